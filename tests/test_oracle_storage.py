@@ -1,0 +1,68 @@
+"""Pins of the oracle's storage roundings (BF16 and FP8 E4M3 with a per-brick
+scale) against torch's CPU conversions and closed forms."""
+import numpy as np
+import torch
+
+import oracle
+
+
+def _probe_values():
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(20000) * 10, rng.standard_normal(2000) * 1e-38,
+                        rng.uniform(-500, 500, 5000), [0.0, 1.0, 1.5, -2.75, 3.0e38]])
+    return x.astype(np.float32)
+
+
+def test_bf16_matches_torch_rne():
+    x = _probe_values()
+    ref = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
+    assert np.array_equal(oracle.bf16_round(x), ref)
+
+
+def test_bf16_ties_to_even():
+    # 1 + 2^-8 lies half-way between 1 and 1 + 2^-7: even mantissa is 1
+    x = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8], np.float32)
+    assert list(oracle.bf16_round(x)) == [1.0, 1 + 2 ** -6]
+
+
+def test_e4m3_matches_torch_in_range():
+    x = _probe_values()
+    x = x[np.abs(x) < 464]
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).float().numpy().astype(np.float64)
+    got = oracle.e4m3_round(x)
+    assert np.array_equal(got, ref)
+
+
+def test_e4m3_saturates_and_closed_forms():
+    x = np.array([448, 460, 500, 1e6, -1e6, 2 ** -9, 2 ** -10, 1.5 * 2 ** -9, 240, 232], np.float32)
+    got = oracle.e4m3_round(x)
+    assert list(got) == [448, 448, 448, 448, -448, 2 ** -9, 0, 2 ** -8, 240, 224]
+    # every finite E4M3 value is a fixed point
+    codes = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).float().numpy()
+    codes = codes[np.isfinite(codes)]
+    assert np.array_equal(oracle.e4m3_round(codes), codes.astype(np.float64))
+
+
+def test_fp8_brick_scale_and_dequant():
+    rng = np.random.default_rng(5)
+    v = (rng.standard_normal((12, 10, 9)) * 7).astype(np.float32)
+    B = 4
+    s = oracle.brick_scales(v, B)
+    assert s.size == 3 * 3 * 3
+    # the brick whose stored region (with halo) holds the absolute maximum maps it
+    # to exactly +-448 * scale
+    k, j, i = np.unravel_index(np.argmax(np.abs(v)), v.shape)
+    d = oracle.dequantize(v, "fp8", B, s)
+    b = ((k // B) * 3 + (j // B)) * 3 + (i // B)
+    assert np.float32(np.abs(v).max()) / s[b] == np.float32(448) or abs(np.abs(v).max() / s[b] - 448) < 1e-4
+    # dequantised values: e4m3(x / s) * s in binary32, errors bounded by the spacing
+    rel = np.abs(d - v) / np.maximum(np.abs(v), 1e-30)
+    small = np.abs(v) < 1e-2
+    assert np.all(rel[~small] <= 2 ** -4 + 1e-7)
+
+
+def test_bf16_dequant_is_per_voxel():
+    rng = np.random.default_rng(6)
+    v = rng.standard_normal((5, 6, 7)).astype(np.float32)
+    d = oracle.dequantize(v, "bf16", 4)
+    assert np.array_equal(d, torch.from_numpy(v).to(torch.bfloat16).float().numpy())
