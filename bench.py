@@ -1,0 +1,346 @@
+"""Benchmark: ray samples/s of the cube ray-casting path on B300.
+
+Default workload ("dvr1024"): a 1024^3 float32 cube (N(0,1) noise + 2000
+Gaussian sources, seed 2; 256^3 bricks), one step = fused statistics with a
+4096-bin histogram + front-to-back DVR of a 32-view orbit at 1920x1080,
+step 0.5 voxel, trilinear sampling, 256-entry transfer function, early
+termination at alpha 0.99, all 32 views in one persistent launch.  Inputs are
+seeded and synthetic (the paper's spectral cubes are not available).
+
+Prints one JSON line.  `--impl reference` times the CPU oracle on the same
+workload instead (bounded pixel sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+# Algorithmic work per DVR sample (trilinear + transfer function + over):
+# trilinear 7 lerps (2 flops each) = 14, TF index 3 + lerp 4x2 = 11, over 8,
+# position 6, t_k 3  -> 42 flops; 8 voxel reads + 2 TF reads.
+DVR_FLOPS_PER_SAMPLE = 42
+MIP_TRI_FLOPS_PER_SAMPLE = 14 + 6 + 3 + 1
+
+
+def workload(name: str) -> dict:
+    if name == "dvr1024":
+        return dict(name="dvr1024", dims=(1024, 1024, 1024), n_sources=2000, seed=2, brick=256, views=32,
+                    W=1920, H=1080, step=0.5, tf="sparse", term=0.99, nbins=4096, storage="f32")
+    if name == "small128":
+        return dict(name="small128", dims=(128, 128, 128), n_sources=8, seed=1, brick=128, views=1,
+                    W=256, H=256, step=1.0, tf="sparse", term=0.99, nbins=256, storage="f32", ortho=True)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_inputs(w: dict):
+    import cubegen
+    v = cubegen.generate(w["dims"], w["n_sources"], w["seed"])
+    if w.get("ortho"):
+        cams = [cubegen.ortho_z_camera(w["dims"])]
+    else:
+        cams = cubegen.orbit_cameras(w["dims"], w["views"])
+    tf = cubegen.tf_sparse() if w["tf"] == "sparse" else cubegen.tf_dense()
+    return v, cams, tf
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(v, cams, tf, w, vmin, vmax, budget_s: float, seed: int = 0):
+    """Time the CPU oracle (as it stands) on random pixels of the views until
+    about budget_s seconds of wall time; returns samples/s and the sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    npix_total = w["W"] * w["H"]
+    done_samples = 0
+    done_pix = 0
+    t0 = time.perf_counter()
+    batch = 256
+    views_used = set()
+    while True:
+        vi = int(rng.integers(0, len(cams)))
+        pix = rng.choice(npix_total, size=batch, replace=False)
+        r = oracle.render(v, cams[vi], w["W"], w["H"], w["step"], "trilinear", "dvr", tf=tf, vmin=vmin, vmax=vmax,
+                          term=w["term"], pixels=pix)
+        done_samples += int(r["nsamp"].sum())
+        done_pix += batch
+        views_used.add(vi)
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+        batch = min(batch * 2, 8192)
+    return done_samples / el, done_pix, done_samples, el, len(views_used)
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    v, cams, tf = make_inputs(w)
+    ref = oracle.stats(v) if v.size <= 2 ** 27 else None
+    vmin = float(v.min()) if ref is None else ref["min"]
+    vmax = float(v.max()) if ref is None else ref["max"]
+    cores = os.cpu_count()
+    budget = float(os.environ.get("VRC_REF_STEP_S", "8"))
+    for _ in range(args.warmup):
+        oracle_rate(v, cams, tf, w, vmin, vmax, 0.5)
+    rates, pix_total = [], 0
+    t_all = time.perf_counter()
+    for s in range(args.steps):
+        rate, npix, nsamp, el, nv = oracle_rate(v, cams, tf, w, vmin, vmax, budget, seed=s + 1)
+        rates.append(rate)
+        pix_total += npix
+    elapsed = time.perf_counter() - t_all
+    value = float(np.mean(rates))
+    line = {"metric": "ray samples/s (DVR, trilinear)", "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w["name"], "dims": list(w["dims"]), "views": w["views"],
+                       "image": [w["W"], w["H"]], "step": w["step"], "storage": w["storage"]},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{pix_total} random pixels over {args.steps} steps, ~{budget:.0f} s each"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, w):
+    import torch
+
+    import paper_1111_6661_b300 as vrc
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    v, cams, tf = make_inputs(w)
+    ctx = vrc.Context(local)
+    st = torch.cuda.current_stream()
+    cid = ctx.cube_upload(v, w["storage"], brick=w["brick"])
+    info = ctx.cube_info(cid)
+    rc = vrc.raycfg(w["W"], w["H"], w["step"], "trilinear")
+    out = torch.empty((len(cams), w["H"], w["W"], 4), dtype=torch.float32, device=dev)
+    dstats = torch.empty(8, dtype=torch.float64, device=dev)
+    dhist = torch.empty(w["nbins"], dtype=torch.int64, device=dev)
+
+    def step():
+        ctx.cube_stats_async(cid, w["nbins"], dstats, dhist)
+        ctx.render_dvr(cid, cams, rc, tf, w["term"], out=out)
+
+    # warm-up (also fixes the sample count of one step: it is deterministic)
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        step()
+    torch.cuda.synchronize()
+    samples_per_step = ctx.last_render_samples()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = Clocks(local)
+    launches0 = ctx.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(st)
+    for i in range(args.steps):
+        ev[i][0].record(st)
+        ctx.cube_stats_async(cid, w["nbins"], dstats, dhist)
+        ev[i][1].record(st)
+        ctx.render_dvr(cid, cams, rc, tf, w["term"], out=out)
+        ev[i][2].record(st)
+    t_end.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(ws)
+    launches = ctx.launch_count() - launches0
+    ms = t_start.elapsed_time(t_end)
+    ms = barrier_max(ms, ws)
+    stats_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    render_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    value = ws * samples_per_step * args.steps / (ms / 1e3)
+
+    pk, pk_kind = peaks()
+    sm_max = pk.get("sm_max_mhz", 2032.0)
+    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved_tflops = samples_per_step * DVR_FLOPS_PER_SAMPLE / (render_ms / 1e3) / 1e12
+    stats_bytes = info["dims"][0] * info["dims"][1] * info["dims"][2] * (4 if w["storage"] == "f32" else 2)
+    stats_gbs = stats_bytes / (stats_ms / 1e3) / 1e9
+
+    # end to end through the public API with host buffers: upload from pinned
+    # host memory, statistics to host, render, images back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        vt = torch.from_numpy(v).pin_memory()
+        host_img = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+        e2e_steps = max(1, min(args.steps, 3))
+        ctx.cube_free(cid)
+        cid = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            c2 = ctx.cube_upload(vt, w["storage"], brick=w["brick"])
+            s, h = ctx.cube_stats(c2, w["nbins"])
+            ctx.render_dvr(c2, cams, rc, tf, w["term"], out=out)
+            host_img.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            ctx.cube_free(c2)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s = barrier_max(e2e_s, ws)
+        e2e = {"value": ws * samples_per_step / e2e_s, "unit": "samples/s",
+               "h2d_bytes_per_step": int(v.nbytes + 4096 + 48 * len(cams)),
+               "d2h_bytes_per_step": int(host_img.numel() * 4 + 8 * w["nbins"] + 48),
+               "ms_per_step": 1e3 * e2e_s}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, npix, nsamp, el, nv = oracle_rate(v, cams, tf, w, info["vmin"], info["vmax"], args.cpu_seconds)
+        cpu = {"value": rate, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{npix} random pixels of {nv} views ({nsamp} samples, {el:.1f} s), FP64 oracle, OpenMP"}
+
+    if rank == 0:
+        line = {"metric": "ray samples/s (DVR, trilinear)", "value": value, "unit": "samples/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": w["name"], "dims": list(w["dims"]), "sources": w["n_sources"],
+                           "brick": w["brick"], "storage": w["storage"], "views": len(cams),
+                           "image": [w["W"], w["H"]], "step": w["step"], "sampling": "trilinear",
+                           "tf": w["tf"], "term_alpha": w["term"], "hist_bins": w["nbins"],
+                           "samples_per_step": samples_per_step, "parallelism": f"replicas{ws}",
+                           "l2": "inputs larger than L2 (cube bricks %.1f GB > 126 MB)" % (info["bytes"] / 1e9)},
+                "roofline": {"bound": "alu", "kernel": "k_render_fused (DVR)", "achieved": achieved_tflops,
+                             "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp32_peak_tflops,
+                             "traffic": None, "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
+                             "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz"},
+                "kernels": {"render_ms": render_ms, "stats_ms": stats_ms,
+                            "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
+                            "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind},
+                "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if cid is not None:
+        ctx.cube_free(cid)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dvr1024")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    w = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

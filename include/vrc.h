@@ -1,0 +1,364 @@
+/*
+ * vrc.h -- C ABI of the B300 cube ray-casting and statistics library.
+ *
+ * The paper (Hassan, Fluke, Barnes) offers, as a service, analysis and
+ * visualisation of spectral data cubes larger than one machine's memory:
+ * minimum/maximum and histograms (Abstract), standard deviation and median as
+ * global multi-pass tasks (Sec. 3), and interactive volume rendering of cubes
+ * split into sub-cubes whose partial images are gathered (Sec. 2, Table 1),
+ * with CUDA streams overlapping computation and I/O (Sec. 2) and multi-user
+ * on-demand sharing (Abstract, Sec. 3).  This library is the single-GPU hot
+ * path of that service.  All work runs in hand-written CUDA kernels for
+ * sm_103a; the host side only validates, plans and launches.
+ *
+ * Conventions used by every entry point
+ *   - A cube has dims (nx, ny, nz), x fastest: voxel (i, j, k) is element
+ *     (k*ny + j)*nx + i of a linear source array and has its centre at
+ *     (i+0.5, j+0.5, k+0.5) in the continuous domain [0,nx]x[0,ny]x[0,nz].
+ *   - Images are row-major, row 0 at the top: pixel (px, py) of view v is
+ *     element (v*H + py)*W + px (MIP: one float; DVR: four floats, RGBA,
+ *     premultiplied).
+ *   - Device pointers are plain CUDA device addresses in the context's device;
+ *     streams are cudaStream_t values passed as void* (NULL = legacy stream).
+ *   - No call aborts, throws or exits: every failure is a negative status.
+ *     Arguments are validated before anything is launched; on an error return
+ *     caller-owned outputs are left unspecified.
+ *   - Ownership: the library owns cube storage, brick pools and scratch; the
+ *     caller owns every output buffer it passes in.
+ *   - Thread safety: one context may be used from one thread at a time, except
+ *     vrc_submit / vrc_poll, which may be called from any thread.
+ */
+#ifndef VRC_H
+#define VRC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vrc_status;
+#define VRC_OK            0
+#define VRC_PENDING       1   /* vrc_poll: request not finished yet */
+#define VRC_E_INVAL      -1   /* bad argument (null pointer, size, enum, unknown flag) */
+#define VRC_E_NOMEM      -2   /* HBM budget exceeded or allocation failed */
+#define VRC_E_CUDA       -3   /* a CUDA runtime call failed; vrc_last_error() has text */
+#define VRC_E_TIMEOUT    -4   /* vrc_poll timed out (request is still pending) */
+#define VRC_E_BADID      -5   /* unknown cube id, ticket or graph handle */
+#define VRC_E_BUSY       -6   /* cube still referenced by queued or running requests */
+#define VRC_E_NONFINITE  -7   /* statistic undefined: the cube has no finite voxel */
+#define VRC_E_INJECTED   -8   /* failure produced by vrc_debug_inject (tests) */
+#define VRC_E_UNSUPPORTED -9  /* operation not available for this cube kind / dtype */
+
+typedef enum { VRC_F32 = 0, VRC_BF16 = 1, VRC_FP8E4M3 = 2 } vrc_dtype;
+
+typedef struct vrc_ctx vrc_ctx;
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    int32_t n_streams;         /* serving: streams requests are spread over (0 = 4) */
+    int32_t max_inflight;      /* serving: requests on the GPU at once (0 = 32) */
+    int32_t reserved0;
+    int64_t hbm_budget_bytes;  /* cube storage + scratch cap; 0 = 90% of free memory */
+} vrc_config;
+
+/* Statistics of the finite voxel values (stored values for BF16/FP8 cubes). */
+typedef struct {
+    double min, max, mean, std;  /* std is the population deviation (divide by n) */
+    uint64_t n, n_nonfinite;
+} vrc_stats;
+
+#define VRC_CAM_ORTHO 0
+#define VRC_CAM_PERSP 1
+typedef struct {
+    int32_t kind;              /* VRC_CAM_ORTHO or VRC_CAM_PERSP */
+    float eye[3], center[3], up[3];
+    float fovy_deg;            /* perspective: full vertical field of view (degrees) */
+    float ortho_height;        /* orthographic: image-plane height (voxel units) */
+} vrc_camera;
+
+#define VRC_NEAREST   0
+#define VRC_TRILINEAR 1
+#define VRC_PATH_FUSED    0    /* one thread per ray walks every brick in ray order */
+#define VRC_PATH_SORTLAST 1    /* per-brick partial images, composited in visibility order */
+typedef struct {
+    int32_t width, height;     /* image size in pixels (1..16384) */
+    float step;                /* sample spacing along the unit ray, voxel units (> 0) */
+    int32_t sampling;          /* VRC_NEAREST or VRC_TRILINEAR */
+    int32_t opacity_correction;/* DVR: 0 = alpha as in the transfer function,
+                                  1 = 1-(1-alpha)^step */
+    int32_t path;              /* VRC_PATH_FUSED or VRC_PATH_SORTLAST (resident cubes) */
+    int32_t tile_w, tile_h;    /* ray tile; 0,0 = tuned default.  tile_w*tile_h = 256,
+                                  tile_w in {8,16,32} */
+} vrc_raycfg;
+
+/*
+ * Ray geometry (both renderers; the fixed formula makes sample positions,
+ * sample counts and voxel choices reproducible).  From the camera, in binary64
+ * and then rounded to binary32:
+ *   w = normalise(center - eye); r = normalise(w x up); u = r x w; asp = W/H
+ *   perspective:  h = tan(fovy/2);      O0 = eye,  D0 = w - (h asp) r + h u
+ *   orthographic: h = ortho_height/2;  O0 = eye - (h asp) r + h u,  D0 = w
+ *   DX = (2 h asp / W) r,  DY = (-2 h / H) u
+ * Per pixel, in binary32 with every operation rounded (no FMA):
+ *   fx = px + 0.5, fy = py + 0.5
+ *   perspective:  o = O0, q = (D0 + fx DX) + fy DY, d = q / sqrt((qx qx + qy qy) + qz qz)
+ *   orthographic: o = (O0 + fx DX) + fy DY, d = D0
+ *   slab test against [0,nx]x[0,ny]x[0,nz] from lo = 0, hi = +inf, using
+ *   t0 = (0 - o_a)/d_a and t1 = (n_a - o_a)/d_a per axis with d_a != 0;
+ *   sample k at t_k = t_entry + (k + 0.5) step while t_k < t_exit,
+ *   position p = o + t_k d.
+ * Sampling: nearest reads voxel floor(p) (clamped); trilinear uses q = p - 0.5,
+ * i0 = floor(q), f = q - i0, clamp-to-edge neighbours.  A sample belongs to the
+ * brick that contains voxel floor(p).
+ * MIP: maximum sample (rays without samples give -FLT_MAX; NaN samples ignored).
+ * DVR: transfer function tf_rgba[256][4] (colour not premultiplied) indexed by
+ * u = clamp((s - min)/(max - min), 0, 1) * 255 with linear interpolation between
+ * entries; front-to-back C += (1-A) a c, A += (1-A) a, stopping after the first
+ * sample with A >= term_alpha; background (0,0,0,0); NaN samples transparent.
+ */
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on cfg->device (cfg may be NULL for defaults).  *out is set
+ * on success.  Errors: VRC_E_INVAL, VRC_E_CUDA, VRC_E_NOMEM. */
+vrc_status vrc_create(vrc_ctx **out, const vrc_config *cfg);
+
+/* Finish every queued serving request, stop the serving thread, free every
+ * cube, graph-independent scratch buffer and stream, and destroy the context.
+ * Graphs created on the context must be destroyed first. */
+vrc_status vrc_destroy(vrc_ctx *ctx);
+
+/* Text of a status code (static storage). */
+const char *vrc_status_str(vrc_status s);
+
+/* Last error message recorded on this context (valid until the next call). */
+const char *vrc_last_error(vrc_ctx *ctx);
+
+/* Bytes currently charged against the HBM budget, and the budget itself. */
+vrc_status vrc_memory(vrc_ctx *ctx, int64_t *used_bytes, int64_t *budget_bytes);
+
+/* ------------------------------------------------------------------ cubes */
+
+/*
+ * Upload a float32 cube and keep it resident in bricks (Sec. 2: the cube is
+ * split into sub-cubes).  src holds nx*ny*nz floats, x fastest, on the host
+ * (src_on_device = 0; any host memory) or on the device (1).  storage selects
+ * the stored type: VRC_F32, VRC_BF16 (round to nearest even) or VRC_FP8E4M3
+ * (per-brick scale = absmax/448 over the brick and its halo, codes =
+ * e4m3(x/scale) rounded to nearest even, saturating).  brick is the brick edge
+ * B (a power of two in 16..512; 0 = 256, or the smallest power of two >= the
+ * largest dimension when that is smaller); each
+ * brick keeps a one-voxel clamp-to-edge halo.  The call records per-brick
+ * min/max and returns when the cube is resident; src may then be reused.
+ * Errors: VRC_E_INVAL (dims <= 0, bad storage/brick), VRC_E_NOMEM (over budget).
+ */
+vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device, int64_t nx, int64_t ny,
+                           int64_t nz, int32_t storage, int32_t brick, void *stream, int64_t *cube_id);
+
+/*
+ * Out-of-core cube (Sec. 2: larger-than-memory cubes; streams overlap I/O):
+ * bricks live in pinned host memory and are streamed to the device on side
+ * streams while rendering.  n_host_bricks pinned brick slots are allocated;
+ * logical brick b uses slot b % n_host_bricks (n_host_bricks < number of
+ * bricks aliases bricks, for benchmarking links when host memory is short).
+ * ring_bricks device slots are charged to the budget (0 = 8).  float32 only.
+ * Errors: VRC_E_INVAL, VRC_E_NOMEM (pinned or device allocation failed).
+ */
+vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_t nz, int32_t brick,
+                                    int64_t n_host_bricks, int32_t ring_bricks, int64_t *cube_id);
+
+/*
+ * Fill host slot `slot` of a streamed cube with one brick given as
+ * (B+2)^3 floats, x fastest, covering voxels [b*B-1, b*B+B] of each axis with
+ * clamp-to-edge values outside the cube.  Host memory, copied; records the
+ * slot's min/max.  Errors: VRC_E_BADID, VRC_E_INVAL.
+ */
+vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const float *brick_with_halo);
+
+/* Release a cube.  VRC_E_BUSY while serving requests still reference it. */
+vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id);
+
+/* dims, brick edge, storage dtype, brick count, stored bytes and the stored
+ * min/max recorded at upload (any output pointer may be NULL). */
+vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t *brick, int32_t *storage,
+                         int64_t *n_bricks, int64_t *bytes, float *vmin, float *vmax);
+
+/* ------------------------------------------------------------- statistics */
+
+/*
+ * Global statistics in one fused pass over the resident bricks (Abstract:
+ * min/max and histogram; Sec. 3: standard deviation): min and max (recorded at
+ * upload), n, mean and population std (binary64 block partials, fixed-order
+ * final merge), n_nonfinite, and, when nbins > 0, hist[nbins] counts over
+ * [min, max] with the binary32 bin formula
+ *   range = fl(max - min), scale = fl(nbins / range),
+ *   bin = trunc(fl(fl(x - min) * scale)) clamped to [0, nbins-1]
+ *   (range == 0: every value in bin 0).
+ * out and hist are HOST memory; the call waits for `stream`.  nbins <= 65536.
+ * Errors: VRC_E_BADID, VRC_E_INVAL, VRC_E_NONFINITE (no finite voxel).
+ */
+vrc_status vrc_cube_stats(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stats *out, uint64_t *hist,
+                          void *stream);
+
+/*
+ * Asynchronous form: writes a vrc_stats record to DEVICE memory dev_out and
+ * counts to DEVICE memory dev_hist[nbins] (may be NULL when nbins == 0),
+ * stream-ordered; nothing waits.  dev_out->n == 0 flags a cube without finite
+ * voxels.
+ */
+vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stats *dev_out,
+                                uint64_t *dev_hist, void *stream);
+
+/*
+ * Median of the finite stored values (Sec. 3: a global task needing all data):
+ * the lower median, value of rank floor((n-1)/2) in ascending order.  Exact:
+ * a 65536-bin histogram on the ordered bit patterns of the values selects the
+ * bin holding the rank, a second pass refines it.  *out is HOST memory; waits
+ * for `stream`.  Errors: VRC_E_BADID, VRC_E_NONFINITE.
+ */
+vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *stream);
+
+/* -------------------------------------------------------------- rendering */
+
+/*
+ * Maximum-intensity projection of n_views views in one persistent launch
+ * (batched (view, ray tile) work items).  cams: HOST array of n_views cameras.
+ * out: DEVICE float[n_views*H*W].  Stream-ordered; returns after launching.
+ * Streamed cubes always take the sort-last path with brick streaming.
+ * Errors: VRC_E_BADID, VRC_E_INVAL.
+ */
+vrc_status vrc_render_mip(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                          const vrc_raycfg *rc, float *out, void *stream);
+
+/*
+ * Front-to-back transfer-function compositing with early termination
+ * (term_alpha in (0, 1]; > 1 disables termination).  tf_rgba: HOST float[1024].
+ * The transfer-function range is the cube's stored [min, max].
+ * out: DEVICE float[n_views*H*W*4].  Stream-ordered.
+ * Errors: VRC_E_BADID, VRC_E_INVAL.
+ */
+vrc_status vrc_render_dvr(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                          const vrc_raycfg *rc, const float *tf_rgba, float term_alpha, float *out,
+                          void *stream);
+
+/*
+ * Ray samples taken by the most recent vrc_render_mip / vrc_render_dvr call on
+ * this context (samples inside the cube that were composited, i.e. before early
+ * termination).  Waits for that render to finish.  *out is HOST memory.
+ */
+vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *out);
+
+/*
+ * Sort-last combination of two image buffers (Sec. 2: gathered partial
+ * images): mode 0 (MIP) out = max(front, back); mode 1 (DVR) out = front +
+ * (1 - front.A) * back per channel.  All DEVICE float arrays of n_pixels
+ * (x4 for DVR); out may alias front or back.  Stream-ordered.
+ */
+vrc_status vrc_composite(vrc_ctx *ctx, const float *front, const float *back, float *out, int64_t n_pixels,
+                         int32_t mode, void *stream);
+
+/* -------------------------------------------------- batching: graphs, tuning */
+
+typedef struct vrc_graph vrc_graph;
+
+/*
+ * Capture one multi-view render (MIP when tf_rgba is NULL, else DVR) of a
+ * resident cube into a CUDA graph: camera data are uploaded once, the graph
+ * resets the work counter and runs the persistent kernel.  out (DEVICE) is
+ * baked into the graph.  Errors: VRC_E_BADID, VRC_E_INVAL, VRC_E_CUDA.
+ */
+vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                            const vrc_raycfg *rc, const float *tf_rgba, float term_alpha, float *out,
+                            vrc_graph **graph);
+vrc_status vrc_graph_launch(vrc_graph *graph, void *stream);
+vrc_status vrc_graph_destroy(vrc_graph *graph);
+
+typedef struct {
+    int32_t tile_w, tile_h;      /* chosen ray tile */
+    int32_t ctas_per_sm;         /* chosen persistent-grid occupancy */
+    int32_t reserved;
+    double best_ms, default_ms;  /* time of the chosen and of the default configuration */
+} vrc_tuning;
+
+/*
+ * Autotuner: times the candidate ray tiles (8x32, 16x16, 32x8) and persistent
+ * grid sizes for this cube and workload with CUDA events and stores the best
+ * as the cube's default (used when rc->tile_w == 0).  The step is never
+ * changed.  Runs the render several times into `out` (DEVICE, as for the
+ * render call); waits for `stream`.
+ */
+vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                        const vrc_raycfg *rc, const float *tf_rgba, float term_alpha, float *out, void *stream,
+                        vrc_tuning *result);
+
+/* ---------------------------------------------------------------- serving */
+
+#define VRC_REQ_MIP   0
+#define VRC_REQ_DVR   1
+#define VRC_REQ_STATS 2
+typedef struct {
+    int32_t kind;          /* VRC_REQ_MIP, VRC_REQ_DVR or VRC_REQ_STATS */
+    int32_t nbins;         /* stats: histogram bins (0..65536) */
+    int64_t cube_id;
+    vrc_camera cam;        /* render: one view */
+    vrc_raycfg rc;
+    float tf_rgba[1024];   /* DVR */
+    float term_alpha;      /* DVR */
+    int32_t reserved;
+    void *out;             /* render: DEVICE image (float[H*W] or float[H*W*4]);
+                              stats: DEVICE uint64[nbins] or NULL */
+} vrc_request;
+
+typedef struct {
+    vrc_status status;     /* VRC_OK or the request's error */
+    int32_t reserved;
+    vrc_stats stats;       /* stats requests */
+    double queue_ms;       /* submit -> launch */
+    double latency_ms;     /* submit -> completion observed */
+    uint64_t samples;      /* render: ray samples taken */
+} vrc_result;
+
+/*
+ * Serving loop (Abstract, Sec. 3: analysis and visualisation as a shared,
+ * on-demand service).  vrc_submit copies the request, queues it and returns a
+ * ticket at once.  A background thread admits queued requests while the
+ * number on the GPU is below max_inflight and their scratch fits the budget,
+ * groups every admitted render into one heterogeneous persistent launch (each
+ * request keeps its own cube, camera, image size and transfer function) on one
+ * of n_streams streams, and runs statistics requests on the next stream, so
+ * new arrivals overlap work already on the GPU.  The cube must stay allocated
+ * until the request completes (vrc_cube_free returns VRC_E_BUSY before).
+ * Errors at submit: VRC_E_BADID, VRC_E_INVAL; later errors arrive in
+ * vrc_result.status.
+ */
+vrc_status vrc_submit(vrc_ctx *ctx, const vrc_request *req, uint64_t *ticket);
+
+/*
+ * Wait up to timeout_ms (0 = just check, < 0 = forever) for a ticket.
+ * Returns VRC_OK and fills *res (the ticket is then retired), VRC_PENDING when
+ * timeout_ms == 0 and it is not done, VRC_E_TIMEOUT when the wait expired,
+ * VRC_E_BADID for an unknown or retired ticket.
+ */
+vrc_status vrc_poll(vrc_ctx *ctx, uint64_t ticket, vrc_result *res, int32_t timeout_ms);
+
+/* ------------------------------------------------------ failure injection */
+
+#define VRC_INJECT_NONE        0
+#define VRC_INJECT_ALLOC       1  /* the nth device/pinned allocation fails (VRC_E_NOMEM) */
+#define VRC_INJECT_H2D         2  /* the nth host->device brick copy fails (VRC_E_INJECTED) */
+#define VRC_INJECT_DROP_REQ    3  /* the nth admitted serving request fails (VRC_E_INJECTED) */
+/*
+ * Host-side fault injection for tests: arm failure `what` to fire on its nth
+ * occurrence from now (n >= 1); VRC_INJECT_NONE disarms.  Nothing is injected
+ * on the GPU.
+ */
+vrc_status vrc_debug_inject(vrc_ctx *ctx, int32_t what, int64_t nth);
+
+/* Kernel launches issued by this context so far (all entry points). */
+uint64_t vrc_launch_count(vrc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VRC_H */

@@ -1,0 +1,424 @@
+// Brick pack + quantise (upload), out-of-core cube registration, cube lifetime.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <float.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "vrc_internal.h"
+
+namespace {
+
+constexpr int kScanSplit = 16;   // blocks per brick in the scan pass
+constexpr int kPackSplit = 32;   // blocks per brick in the pack pass
+
+struct ScanPartial {
+    float mn, mx, absmax;
+    int32_t nonfinite;
+    double sum;   // sum of finite interior source values (for the statistics shift)
+    int64_t cnt;
+};
+
+__device__ __forceinline__ int64_t clamp64(int64_t i, int64_t n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// Pass 1: per brick, min/max of finite interior source values, absmax of finite
+// values over the stored region (interior + halo, clamp-to-edge), count of
+// non-finite interior voxels.
+__global__ void __launch_bounds__(256) k_brick_scan(const float *__restrict__ src, BrickGeom g,
+                                                    ScanPartial *__restrict__ part)
+{
+    const int64_t b = blockIdx.x;
+    const int split = blockIdx.y;
+    const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    float mn = FLT_MAX, mx = -FLT_MAX, am = 0.f;
+    int nnf = 0, cnt = 0;
+    float sum = 0.f;
+    const int R = g.R;
+    for (int row = split * (blockDim.x / 32) + threadIdx.x / 32; row < R * R; row += kScanSplit * (blockDim.x / 32)) {
+        const int ly = row % R - 1, lz = row / R - 1;
+        const int64_t gy = (int64_t)by * g.B + ly, gz = (int64_t)bz * g.B + lz;
+        const bool yz_in = ly >= 0 && ly < g.B && lz >= 0 && lz < g.B && gy < g.dims[1] && gz < g.dims[2];
+        const float *rowp = src + (clamp64(gz, g.dims[2]) * g.dims[1] + clamp64(gy, g.dims[1])) * g.dims[0];
+        for (int lx = (int)(threadIdx.x % 32) - 1; lx <= g.B; lx += 32) {
+            const int64_t gx = (int64_t)bx * g.B + lx;
+            const float x = rowp[clamp64(gx, g.dims[0])];
+            const bool fin = fabsf(x) <= FLT_MAX;
+            if (fin) am = fmaxf(am, fabsf(x));
+            if (yz_in && lx >= 0 && lx < g.B && gx < g.dims[0]) {
+                if (fin) {
+                    mn = fminf(mn, x);
+                    mx = fmaxf(mx, x);
+                    sum += x;
+                    ++cnt;
+                } else {
+                    ++nnf;
+                }
+            }
+        }
+    }
+    double dsum = sum;
+    for (int o = 16; o; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+        nnf += __shfl_xor_sync(0xffffffffu, nnf, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    }
+    __shared__ ScanPartial sp[8];
+    if ((threadIdx.x & 31) == 0) sp[threadIdx.x / 32] = ScanPartial{mn, mx, am, nnf, dsum, cnt};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ScanPartial r = sp[0];
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) {
+            r.mn = fminf(r.mn, sp[w].mn);
+            r.mx = fmaxf(r.mx, sp[w].mx);
+            r.absmax = fmaxf(r.absmax, sp[w].absmax);
+            r.nonfinite += sp[w].nonfinite;
+            r.sum += sp[w].sum;
+            r.cnt += sp[w].cnt;
+        }
+        part[b * kScanSplit + split] = r;
+    }
+}
+
+__device__ __forceinline__ float fp8_round_trip(float x, float scale)
+{
+    const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn(x, scale), __NV_SATFINITE, __NV_E4M3);
+    const __half h = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+    return __fmul_rn(__half2float(h), scale);
+}
+
+__device__ __forceinline__ float stored_value(float x, int dtype, float scale)
+{
+    if (dtype == VRC_BF16) return __bfloat162float(__float2bfloat16_rn(x));
+    if (dtype == VRC_FP8E4M3) return fp8_round_trip(x, scale);
+    return x;
+}
+
+// Per brick: reduce the scan partials, derive the FP8 scale and the stored
+// min/max (rounding is monotone, so stored(min) is the stored minimum).
+__global__ void k_brick_finish(const ScanPartial *__restrict__ part, BrickGeom g, float *scales, float *bmin,
+                               float *bmax, int32_t *bnonfinite, double *bsum)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= g.nbricks) return;
+    ScanPartial r = part[b * kScanSplit];
+    for (int s = 1; s < kScanSplit; ++s) {
+        const ScanPartial p = part[b * kScanSplit + s];
+        r.mn = fminf(r.mn, p.mn);
+        r.mx = fmaxf(r.mx, p.mx);
+        r.absmax = fmaxf(r.absmax, p.absmax);
+        r.nonfinite += p.nonfinite;
+        r.sum += p.sum;
+        r.cnt += p.cnt;
+    }
+    bsum[2 * b] = r.sum;
+    bsum[2 * b + 1] = (double)r.cnt;
+    float scale = 1.f;
+    if (g.dtype == VRC_FP8E4M3 && r.absmax > 0.f) scale = __fdiv_rn(r.absmax, 448.f);
+    scales[b] = scale;
+    const bool any = r.mn <= r.mx;
+    bmin[b] = any ? stored_value(r.mn, g.dtype, scale) : FLT_MAX;
+    bmax[b] = any ? stored_value(r.mx, g.dtype, scale) : -FLT_MAX;
+    bnonfinite[b] = r.nonfinite;
+}
+
+template <int DT>
+__device__ __forceinline__ void store_elem(void *base, int64_t i, float x, float scale)
+{
+    if (DT == VRC_F32) {
+        reinterpret_cast<float *>(base)[i] = x;
+    } else if (DT == VRC_BF16) {
+        reinterpret_cast<__nv_bfloat16 *>(base)[i] = __float2bfloat16_rn(x);
+    } else {
+        reinterpret_cast<__nv_fp8_storage_t *>(base)[i] =
+            __nv_cvt_float_to_fp8(__fdiv_rn(x, scale), __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+// Pass 2: write every stored element of every brick (halo = clamp-to-edge,
+// row padding = 0).
+template <int DT>
+__global__ void __launch_bounds__(256) k_brick_pack(const float *__restrict__ src, BrickGeom g,
+                                                    const float *__restrict__ scales, void *pool)
+{
+    const int64_t b = blockIdx.x;
+    const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    const float scale = scales[b];
+    char *bp = reinterpret_cast<char *>(pool) + b * g.brick_bytes;
+    const int R = g.R;
+    for (int row = blockIdx.y * (blockDim.x / 32) + threadIdx.x / 32; row < R * R; row += kPackSplit * (blockDim.x / 32)) {
+        const int ly = row % R - 1, lz = row / R - 1;
+        const int64_t gy = clamp64((int64_t)by * g.B + ly, g.dims[1]), gz = clamp64((int64_t)bz * g.B + lz, g.dims[2]);
+        const float *rowp = src + (gz * g.dims[1] + gy) * g.dims[0];
+        const int64_t rowbase = (int64_t)row * g.P;
+        for (int sx = threadIdx.x % 32; sx < g.P; sx += 32) {
+            const int lx = sx - g.O;
+            float x = 0.f;
+            if (lx >= -1 && lx <= g.B) x = rowp[clamp64((int64_t)bx * g.B + lx, g.dims[0])];
+            store_elem<DT>(bp, rowbase + sx, x, scale);
+        }
+    }
+}
+
+vrc_status finish_metadata(vrc_ctx *ctx, Cube *c, cudaStream_t st, const double *dbsum)
+{
+    const BrickGeom &g = c->g;
+    std::vector<double> bsum(2 * g.nbricks);
+    VRC_CK(ctx, cudaMemcpyAsync(bsum.data(), dbsum, g.nbricks * 16, cudaMemcpyDeviceToHost, st));
+    c->h_bmin.resize(g.nbricks);
+    c->h_bmax.resize(g.nbricks);
+    c->h_bnonfinite.resize(g.nbricks);
+    VRC_CK(ctx, cudaMemcpyAsync(c->h_bmin.data(), c->bmin, g.nbricks * 4, cudaMemcpyDeviceToHost, st));
+    VRC_CK(ctx, cudaMemcpyAsync(c->h_bmax.data(), c->bmax, g.nbricks * 4, cudaMemcpyDeviceToHost, st));
+    VRC_CK(ctx, cudaMemcpyAsync(c->h_bnonfinite.data(), c->bnonfinite, g.nbricks * 4, cudaMemcpyDeviceToHost, st));
+    VRC_CK(ctx, cudaStreamSynchronize(st));
+    float mn = FLT_MAX, mx = -FLT_MAX;
+    bool any = false;
+    for (int64_t b = 0; b < g.nbricks; ++b) {
+        if (c->h_bmin[b] <= c->h_bmax[b]) {
+            any = true;
+            mn = std::fmin(mn, c->h_bmin[b]);
+            mx = std::fmax(mx, c->h_bmax[b]);
+        }
+    }
+    c->has_finite = any;
+    c->vmin = any ? mn : 0.f;
+    c->vmax = any ? mx : 0.f;
+    double tot = 0, cnt = 0;
+    for (int64_t b = 0; b < g.nbricks; ++b) {
+        tot += bsum[2 * b];
+        cnt += bsum[2 * b + 1];
+    }
+    c->shift = cnt > 0 ? (float)(tot / cnt) : 0.f;
+    if (!std::isfinite(c->shift)) c->shift = c->vmin;
+    return VRC_OK;
+}
+
+void release_cube(vrc_ctx *ctx, Cube *c)
+{
+    const BrickGeom &g = c->g;
+    if (c->pool) dev_free(ctx, c->pool, g.nbricks * g.brick_bytes);
+    if (c->ring_pool) dev_free(ctx, c->ring_pool, (size_t)c->ring * g.brick_bytes);
+    if (c->scales) dev_free(ctx, c->scales, g.nbricks * 4);
+    if (c->bmin) dev_free(ctx, c->bmin, g.nbricks * 4);
+    if (c->bmax) dev_free(ctx, c->bmax, g.nbricks * 4);
+    if (c->bnonfinite) dev_free(ctx, c->bnonfinite, g.nbricks * 4);
+    if (c->host_pool) cudaFreeHost(c->host_pool);
+    delete c;
+}
+
+vrc_status alloc_meta(vrc_ctx *ctx, Cube *c)
+{
+    const int64_t n = c->g.nbricks;
+    vrc_status s;
+    if ((s = dev_alloc(ctx, (void **)&c->scales, n * 4)) != VRC_OK) return s;
+    if ((s = dev_alloc(ctx, (void **)&c->bmin, n * 4)) != VRC_OK) return s;
+    if ((s = dev_alloc(ctx, (void **)&c->bmax, n * 4)) != VRC_OK) return s;
+    if ((s = dev_alloc(ctx, (void **)&c->bnonfinite, n * 4)) != VRC_OK) return s;
+    return VRC_OK;
+}
+
+int64_t register_cube(vrc_ctx *ctx, Cube *c)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    c->id = ctx->next_id++;
+    ctx->cubes[c->id] = c;
+    return c->id;
+}
+
+}  // namespace
+
+extern "C" {
+
+vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device, int64_t nx, int64_t ny,
+                           int64_t nz, int32_t storage, int32_t brick, void *stream, int64_t *cube_id)
+{
+    if (!ctx || !src || !cube_id) return VRC_E_INVAL;
+    if (src_on_device != 0 && src_on_device != 1) return set_err(ctx, VRC_E_INVAL, "src_on_device must be 0 or 1");
+    BrickGeom g;
+    if (!make_geom(nx, ny, nz, brick, storage, &g))
+        return set_err(ctx, VRC_E_INVAL, "bad dims/storage/brick (%lld %lld %lld, %d, %d)", (long long)nx,
+                       (long long)ny, (long long)nz, storage, brick);
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Cube *c = new (std::nothrow) Cube();
+    if (!c) return VRC_E_NOMEM;
+    c->g = g;
+    vrc_status s = dev_alloc(ctx, &c->pool, g.nbricks * g.brick_bytes);
+    if (s == VRC_OK) s = alloc_meta(ctx, c);
+    const float *dsrc = src;
+    void *staging = nullptr;
+    const size_t src_bytes = (size_t)(nx * ny * nz) * 4;
+    if (s == VRC_OK && !src_on_device) {
+        s = dev_alloc(ctx, &staging, src_bytes);
+        if (s == VRC_OK) {
+            cudaError_t e = cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) s = cuda_err(ctx, e, "cube upload H2D");
+            dsrc = (const float *)staging;
+        }
+    }
+    ScanPartial *part = nullptr;
+    const size_t part_bytes = g.nbricks * (kScanSplit * sizeof(ScanPartial) + 16);
+    if (s == VRC_OK) s = dev_alloc(ctx, (void **)&part, part_bytes);
+    double *dbsum = part ? reinterpret_cast<double *>(part + g.nbricks * kScanSplit) : nullptr;
+    if (s == VRC_OK) {
+        k_brick_scan<<<dim3((unsigned)g.nbricks, kScanSplit), 256, 0, st>>>(dsrc, g, part);
+        k_brick_finish<<<(unsigned)((g.nbricks + 127) / 128), 128, 0, st>>>(part, g, c->scales, c->bmin, c->bmax,
+                                                                            c->bnonfinite, dbsum);
+        dim3 grid((unsigned)g.nbricks, kPackSplit);
+        if (storage == VRC_F32) k_brick_pack<VRC_F32><<<grid, 256, 0, st>>>(dsrc, g, c->scales, c->pool);
+        else if (storage == VRC_BF16) k_brick_pack<VRC_BF16><<<grid, 256, 0, st>>>(dsrc, g, c->scales, c->pool);
+        else k_brick_pack<VRC_FP8E4M3><<<grid, 256, 0, st>>>(dsrc, g, c->scales, c->pool);
+        count_launch(ctx, 3);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_err(ctx, e, "brick pack launch");
+    }
+    if (s == VRC_OK) s = finish_metadata(ctx, c, st, dbsum);
+    if (part) {
+        cudaStreamSynchronize(st);
+        dev_free(ctx, part, part_bytes);
+    }
+    if (staging) {
+        cudaStreamSynchronize(st);
+        dev_free(ctx, staging, src_bytes);
+    }
+    if (s != VRC_OK) {
+        release_cube(ctx, c);
+        return s;
+    }
+    c->charged = g.nbricks * g.brick_bytes + 16 * g.nbricks;
+    *cube_id = register_cube(ctx, c);
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_t nz, int32_t brick,
+                                    int64_t n_host_bricks, int32_t ring_bricks, int64_t *cube_id)
+{
+    if (!ctx || !cube_id) return VRC_E_INVAL;
+    BrickGeom g;
+    if (!make_geom(nx, ny, nz, brick, VRC_F32, &g)) return set_err(ctx, VRC_E_INVAL, "bad dims/brick");
+    if (n_host_bricks <= 0 || n_host_bricks > g.nbricks) return set_err(ctx, VRC_E_INVAL, "bad n_host_bricks");
+    if (ring_bricks < 0 || ring_bricks > 4096) return set_err(ctx, VRC_E_INVAL, "bad ring_bricks");
+    if (ring_bricks == 0) ring_bricks = 8;
+    if (ring_bricks < 2) return set_err(ctx, VRC_E_INVAL, "ring needs at least 2 bricks");
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    Cube *c = new (std::nothrow) Cube();
+    if (!c) return VRC_E_NOMEM;
+    c->g = g;
+    c->streamed = true;
+    c->n_host = n_host_bricks;
+    c->ring = ring_bricks;
+    vrc_status s = VRC_OK;
+    if (inject_fire(ctx, VRC_INJECT_ALLOC)) s = set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
+    if (s == VRC_OK) {
+        cudaError_t e = cudaHostAlloc(&c->host_pool, (size_t)n_host_bricks * g.brick_bytes, cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            c->host_pool = nullptr;
+            s = cuda_err(ctx, e, "cudaHostAlloc (pinned brick store)");
+            if (s == VRC_E_CUDA) s = VRC_E_NOMEM;
+        }
+    }
+    if (s == VRC_OK) s = dev_alloc(ctx, &c->ring_pool, (size_t)ring_bricks * g.brick_bytes);
+    if (s == VRC_OK) s = alloc_meta(ctx, c);
+    if (s != VRC_OK) {
+        release_cube(ctx, c);
+        return s;
+    }
+    c->host_filled.assign(n_host_bricks, 0);
+    c->h_bmin.assign(g.nbricks, FLT_MAX);
+    c->h_bmax.assign(g.nbricks, -FLT_MAX);
+    c->h_bnonfinite.assign(g.nbricks, 0);
+    std::vector<float> ones(g.nbricks, 1.f);
+    cudaMemcpy(c->scales, ones.data(), g.nbricks * 4, cudaMemcpyHostToDevice);
+    c->charged = (int64_t)ring_bricks * g.brick_bytes;
+    *cube_id = register_cube(ctx, c);
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const float *bw)
+{
+    if (!ctx || !bw) return VRC_E_INVAL;
+    Cube *c = find_cube(ctx, cube_id);
+    if (!c) return VRC_E_BADID;
+    if (!c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "cube is resident, not streamed");
+    if (slot < 0 || slot >= c->n_host) return set_err(ctx, VRC_E_INVAL, "slot out of range");
+    const BrickGeom &g = c->g;
+    const int R = g.R;
+    float *dst = reinterpret_cast<float *>((char *)c->host_pool + slot * g.brick_bytes);
+    float mn = FLT_MAX, mx = -FLT_MAX;
+    int32_t nnf = 0;
+    for (int zr = 0; zr < R; ++zr)
+        for (int yr = 0; yr < R; ++yr) {
+            float *row = dst + ((int64_t)zr * R + yr) * g.P;
+            const float *in = bw + ((int64_t)zr * R + yr) * R;
+            std::memset(row, 0, sizeof(float) * g.P);
+            std::memcpy(row + g.O - 1, in, sizeof(float) * R);
+            if (zr >= 1 && zr <= g.B && yr >= 1 && yr <= g.B)
+                for (int x = 1; x <= g.B; ++x) {
+                    float v = in[x];
+                    if (std::isfinite(v)) {
+                        mn = std::fmin(mn, v);
+                        mx = std::fmax(mx, v);
+                    } else {
+                        ++nnf;
+                    }
+                }
+        }
+    c->host_filled[slot] = 1;
+    // every logical brick aliased to this slot gets its extrema
+    for (int64_t b = slot; b < g.nbricks; b += c->n_host) {
+        c->h_bmin[b] = mn;
+        c->h_bmax[b] = mx;
+        c->h_bnonfinite[b] = nnf;
+    }
+    float vmn = FLT_MAX, vmx = -FLT_MAX;
+    for (int64_t b = 0; b < g.nbricks; ++b) {
+        if (c->h_bmin[b] <= c->h_bmax[b]) {
+            vmn = std::fmin(vmn, c->h_bmin[b]);
+            vmx = std::fmax(vmx, c->h_bmax[b]);
+        }
+    }
+    c->has_finite = vmn <= vmx;
+    c->vmin = c->has_finite ? vmn : 0.f;
+    c->vmax = c->has_finite ? vmx : 0.f;
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id)
+{
+    if (!ctx) return VRC_E_INVAL;
+    Cube *c = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->cubes.find(cube_id);
+        if (it == ctx->cubes.end()) return VRC_E_BADID;
+        if (it->second->refs.load() > 0) return set_err(ctx, VRC_E_BUSY, "cube referenced by serving requests");
+        c = it->second;
+        ctx->cubes.erase(it);
+    }
+    cudaDeviceSynchronize();
+    release_cube(ctx, c);
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t *brick, int32_t *storage,
+                         int64_t *n_bricks, int64_t *bytes, float *vmin, float *vmax)
+{
+    if (!ctx) return VRC_E_INVAL;
+    Cube *c = find_cube(ctx, cube_id);
+    if (!c) return VRC_E_BADID;
+    if (dims)
+        for (int a = 0; a < 3; ++a) dims[a] = c->g.dims[a];
+    if (brick) *brick = c->g.B;
+    if (storage) *storage = c->g.dtype;
+    if (n_bricks) *n_bricks = c->g.nbricks;
+    if (bytes) *bytes = c->streamed ? (int64_t)c->ring * c->g.brick_bytes : c->g.nbricks * c->g.brick_bytes;
+    if (vmin) *vmin = c->vmin;
+    if (vmax) *vmax = c->vmax;
+    return VRC_OK;
+}
+
+}  // extern "C"

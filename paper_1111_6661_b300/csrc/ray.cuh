@@ -1,0 +1,187 @@
+// Device-side ray set-up, sampling and compositing shared by the render kernels.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <float.h>
+
+#include "vrc_internal.h"
+
+// Cube storage as seen by the kernels.
+struct CubeView {
+    const uint8_t *pool;      // brick b at pool + b * brick_bytes (resident)
+    const float *scales;      // FP8 per-brick scale
+    int64_t brick_bytes;
+    int32_t B, logB, P, O, R;
+    int32_t nb[3];
+    int32_t dims[3];
+    float fdims[3];
+    int32_t dtype;
+};
+
+// One render inside a (possibly heterogeneous) launch.
+struct JobDesc {
+    CubeView cv;
+    ViewParams vp;
+    float step, term, vmin, inv_range;   // TF index u = (s - vmin) * inv_range
+    int32_t opacity_correction;
+    int32_t tile_w, tile_h, tiles_x, tiles_y;
+    int64_t item_begin;                  // first work item of this job
+    const float4 *tf;                    // device [256] (DVR)
+    float *out;                          // image of this job (view)
+    unsigned long long *samples;         // sample counter of this job (may be shared or null)
+};
+
+// Binary32 ray of pixel (px, py), exactly as stated in vrc.h (every operation
+// rounded, no contraction).  Returns false when the ray misses the cube.
+__device__ __forceinline__ bool ray_setup(const ViewParams &v, const float fd[3], int px, int py, float o[3],
+                                          float d[3], float &tin, float &tout)
+{
+    const float fx = __fadd_rn((float)px, 0.5f), fy = __fadd_rn((float)py, 0.5f);
+    if (v.kind == VRC_CAM_PERSP) {
+        float q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = v.O0[a];
+            q[a] = __fadd_rn(__fadd_rn(v.D0[a], __fmul_rn(fx, v.DX[a])), __fmul_rn(fy, v.DY[a]));
+        }
+        const float n = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(q[0], q[0]), __fmul_rn(q[1], q[1])),
+                                             __fmul_rn(q[2], q[2])));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[a] = __fdiv_rn(q[a], n);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            o[a] = __fadd_rn(__fadd_rn(v.O0[a], __fmul_rn(fx, v.DX[a])), __fmul_rn(fy, v.DY[a]));
+            d[a] = v.D0[a];
+        }
+    }
+    float lo = 0.f, hi = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.f) {
+            if (o[a] < 0.f || o[a] > fd[a]) return false;
+            continue;
+        }
+        float t0 = __fdiv_rn(__fsub_rn(0.f, o[a]), d[a]);
+        float t1 = __fdiv_rn(__fsub_rn(fd[a], o[a]), d[a]);
+        if (t0 > t1) {
+            const float tmp = t0;
+            t0 = t1;
+            t1 = tmp;
+        }
+        if (t0 > lo) lo = t0;
+        if (t1 < hi) hi = t1;
+    }
+    tin = lo;
+    tout = hi;
+    return lo < hi;
+}
+
+__device__ __forceinline__ float sample_t(float tin, int k, float step)
+{
+    return __fadd_rn(tin, __fmul_rn(__fadd_rn((float)k, 0.5f), step));
+}
+
+template <int DT>
+__device__ __forceinline__ float raw_voxel(const uint8_t *brick, int64_t e)
+{
+    if (DT == VRC_F32) return __ldg(reinterpret_cast<const float *>(brick) + e);
+    if (DT == VRC_BF16)
+        return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short *>(brick) + e) << 16);
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)__ldg(brick + e), __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+// Per-axis trilinear set-up of one coordinate: q = p - 0.5, i0 = floor(q),
+// f = q - i0; the voxel floor(p) is i0 + (f >= 0.5) (exact because p - 0.5 is
+// exact for p >= 0.5; for p < 0.5 both choices clamp to voxel 0).
+struct AxisT {
+    int i0, ip;
+    float f;
+};
+__device__ __forceinline__ AxisT axis_tri(float p, int n)
+{
+    const float q = __fsub_rn(p, 0.5f);
+    const float fl = floorf(q);
+    AxisT r;
+    r.f = __fsub_rn(q, fl);
+    r.i0 = (int)fl;
+    r.ip = min(max(r.i0 + (r.f >= 0.5f ? 1 : 0), 0), n - 1);
+    return r;
+}
+
+__device__ __forceinline__ int brick_index(const CubeView &cv, int bx, int by, int bz)
+{
+    return (bz * cv.nb[1] + by) * cv.nb[0] + bx;
+}
+
+// Trilinear sample from brick storage `bp` whose local origin is (ox, oy, oz)
+// voxels; needs i0 - o in [-1, B-1] on each axis (guaranteed when the brick
+// contains voxel floor(p)).
+template <int DT>
+__device__ __forceinline__ float tri_in_brick(const CubeView &cv, const uint8_t *bp, const AxisT &ax, const AxisT &ay,
+                                              const AxisT &az, int ox, int oy, int oz, float scale)
+{
+    const int lx = ax.i0 - ox, ly = ay.i0 - oy, lz = az.i0 - oz;
+    const int64_t e = ((int64_t)(lz + 1) * cv.R + (ly + 1)) * cv.P + (lx + cv.O);
+    const int64_t S = (int64_t)cv.P * cv.R;
+    const float v000 = raw_voxel<DT>(bp, e), v100 = raw_voxel<DT>(bp, e + 1);
+    const float v010 = raw_voxel<DT>(bp, e + cv.P), v110 = raw_voxel<DT>(bp, e + cv.P + 1);
+    const float v001 = raw_voxel<DT>(bp, e + S), v101 = raw_voxel<DT>(bp, e + S + 1);
+    const float v011 = raw_voxel<DT>(bp, e + S + cv.P), v111 = raw_voxel<DT>(bp, e + S + cv.P + 1);
+    const float c00 = fmaf(ax.f, v100 - v000, v000), c10 = fmaf(ax.f, v110 - v010, v010);
+    const float c01 = fmaf(ax.f, v101 - v001, v001), c11 = fmaf(ax.f, v111 - v011, v011);
+    const float c0 = fmaf(ay.f, c10 - c00, c00), c1 = fmaf(ay.f, c11 - c01, c01);
+    const float v = fmaf(az.f, c1 - c0, c0);
+    return DT == VRC_FP8E4M3 ? v * scale : v;
+}
+
+template <int DT>
+__device__ __forceinline__ float nearest_in_brick(const CubeView &cv, const uint8_t *bp, int ix, int iy, int iz, int ox,
+                                                  int oy, int oz, float scale)
+{
+    const int64_t e = ((int64_t)(iz - oz + 1) * cv.R + (iy - oy + 1)) * cv.P + (ix - ox + cv.O);
+    const float v = raw_voxel<DT>(bp, e);
+    return DT == VRC_FP8E4M3 ? __fmul_rn(v, scale) : v;
+}
+
+// Sample at p from the resident brick that contains voxel floor(p).
+template <int SAMPLING, int DT>
+__device__ __forceinline__ float sample_resident(const CubeView &cv, float px, float py, float pz)
+{
+    if (SAMPLING == VRC_NEAREST) {
+        const int ix = min(max((int)floorf(px), 0), cv.dims[0] - 1);
+        const int iy = min(max((int)floorf(py), 0), cv.dims[1] - 1);
+        const int iz = min(max((int)floorf(pz), 0), cv.dims[2] - 1);
+        const int bx = ix >> cv.logB, by = iy >> cv.logB, bz = iz >> cv.logB;
+        const int b = brick_index(cv, bx, by, bz);
+        const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
+        return nearest_in_brick<DT>(cv, cv.pool + (int64_t)b * cv.brick_bytes, ix, iy, iz, bx << cv.logB,
+                                    by << cv.logB, bz << cv.logB, scale);
+    } else {
+        const AxisT ax = axis_tri(px, cv.dims[0]), ay = axis_tri(py, cv.dims[1]), az = axis_tri(pz, cv.dims[2]);
+        const int bx = ax.ip >> cv.logB, by = ay.ip >> cv.logB, bz = az.ip >> cv.logB;
+        const int b = brick_index(cv, bx, by, bz);
+        const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
+        return tri_in_brick<DT>(cv, cv.pool + (int64_t)b * cv.brick_bytes, ax, ay, az, bx << cv.logB, by << cv.logB,
+                                bz << cv.logB, scale);
+    }
+}
+
+// Transfer function: 256 RGBA entries, linear between entries.
+__device__ __forceinline__ float4 classify(const float4 *tf, float s, float vmin, float inv_range)
+{
+    float u = (s - vmin) * inv_range;
+    u = fminf(fmaxf(u, 0.f), 1.f);
+    const float x = u * 255.f;
+    const int j = min((int)x, 254);
+    const float f = x - (float)j;
+    const float4 a = tf[j], b = tf[j + 1];
+    return make_float4(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y), fmaf(f, b.z - a.z, a.z),
+                       fmaf(f, b.w - a.w, a.w));
+}
+
+__device__ __forceinline__ float opacity(float a, float step, int correct)
+{
+    return correct ? 1.f - __powf(fmaxf(1.f - a, 0.f), step) : a;
+}

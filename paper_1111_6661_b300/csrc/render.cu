@@ -1,0 +1,1155 @@
+// Ray casting: fused persistent multi-view kernel, sort-last brick kernel with
+// partial images, composite kernel, out-of-core streaming, graphs, autotuner.
+#include <float.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ray.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------------ kernels
+
+// Thread -> pixel inside a tile_w x tile_h tile: warps cover 8 x 4 pixel blocks.
+__device__ __forceinline__ void tile_pixel(int tile_w, int &lx, int &ly)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wx = tile_w >> 3;
+    lx = (warp % wx) * 8 + (lane & 7);
+    ly = (warp / wx) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ int find_job(const JobDesc *jobs, int n_jobs, int64_t item)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item_begin <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void warp_count(unsigned long long *counter, uint32_t n)
+{
+    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(counter, (unsigned long long)n);
+}
+
+// Fused path: one thread per ray walks all its samples in ray order, reading
+// each from the brick that contains it (sort-last compositing of per-brick
+// segments happens in registers).  Persistent: CTAs pull (job, tile) items
+// from an atomic counter.
+template <int MODE, int SAMPLING, int DT>
+__global__ void __launch_bounds__(kThreads) k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs,
+                                                           int64_t total_items, int *counter)
+{
+    __shared__ float4 s_tf[256];
+    __shared__ int64_t s_item;
+    __shared__ int s_job;
+    int loaded = -1;
+    uint32_t nsamp = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(counter, 1);
+            s_job = s_item < total_items ? find_job(jobs, n_jobs, s_item) : -1;
+        }
+        __syncthreads();
+        const int64_t item = s_item;
+        const int jid = s_job;
+        if (item >= total_items) break;
+        const JobDesc &J = jobs[jid];
+        if (MODE == 1 && jid != loaded) {
+            s_tf[threadIdx.x] = J.tf[threadIdx.x];
+            __syncthreads();
+            loaded = jid;
+        }
+        const int64_t t = item - J.item_begin;
+        const int tx = (int)(t % J.tiles_x), ty = (int)(t / J.tiles_x);
+        int lx, ly;
+        tile_pixel(J.tile_w, lx, ly);
+        const int px = tx * J.tile_w + lx, py = ty * J.tile_h + ly;
+        if (px < J.vp.W && py < J.vp.H) {
+            float o[3], d[3], tin, tout;
+            const bool hit = ray_setup(J.vp, J.cv.fdims, px, py, o, d, tin, tout);
+            const int64_t pix = (int64_t)py * J.vp.W + px;
+            if (MODE == 0) {
+                float m = -FLT_MAX;
+                if (hit) {
+                    for (int k = 0;; ++k) {
+                        const float tk = sample_t(tin, k, J.step);
+                        if (!(tk < tout)) break;
+                        const float s = sample_resident<SAMPLING, DT>(J.cv, __fadd_rn(o[0], __fmul_rn(tk, d[0])),
+                                                                      __fadd_rn(o[1], __fmul_rn(tk, d[1])),
+                                                                      __fadd_rn(o[2], __fmul_rn(tk, d[2])));
+                        m = fmaxf(m, s);
+                        ++nsamp;
+                    }
+                }
+                J.out[pix] = m;
+            } else {
+                float cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+                if (hit) {
+                    for (int k = 0;; ++k) {
+                        const float tk = sample_t(tin, k, J.step);
+                        if (!(tk < tout)) break;
+                        const float s = sample_resident<SAMPLING, DT>(J.cv, __fadd_rn(o[0], __fmul_rn(tk, d[0])),
+                                                                      __fadd_rn(o[1], __fmul_rn(tk, d[1])),
+                                                                      __fadd_rn(o[2], __fmul_rn(tk, d[2])));
+                        ++nsamp;
+                        if (s == s) {
+                            const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
+                            const float a = opacity(c.w, J.step, J.opacity_correction);
+                            const float w = (1.f - A) * a;
+                            cr = fmaf(w, c.x, cr);
+                            cg = fmaf(w, c.y, cg);
+                            cb = fmaf(w, c.z, cb);
+                            A += w;
+                        }
+                        if (A >= J.term) break;
+                    }
+                }
+                reinterpret_cast<float4 *>(J.out)[pix] = make_float4(cr, cg, cb, A);
+            }
+        }
+        if (J.samples) warp_count(J.samples, nsamp);   // one atomic per warp and item
+        nsamp = 0;
+        __syncthreads();
+    }
+}
+
+// Sort-last work item: one screen tile of one brick of one view.
+struct BrickItem {
+    int32_t job;
+    int32_t brick;     // brick index in the cube's grid
+    int32_t slot;      // storage slot: resident pool index or streaming ring slot
+    int16_t tx, ty;    // tile origin / tile size
+};
+
+__device__ __forceinline__ bool member(const CubeView &cv, const float o[3], const float d[3], float tk, int bx,
+                                       int by, int bz, float p[3])
+{
+    int ib[3];
+    const int bc[3] = {bx, by, bz};
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p[a] = __fadd_rn(o[a], __fmul_rn(tk, d[a]));
+        ib[a] = min(max((int)floorf(p[a]), 0), cv.dims[a] - 1) >> cv.logB;
+        in = in && ib[a] == bc[a];
+    }
+    return in;
+}
+
+__device__ __forceinline__ int brick_key_of(const CubeView &cv, const ViewParams &vp, const float p[3])
+{
+    int key = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = min(max((int)floorf(p[a]), 0), cv.dims[a] - 1) >> cv.logB;
+        key += abs(b - vp.ec[a]);
+    }
+    return key;
+}
+
+// Sort-last path: per item, the rays of one tile sample only their segment in
+// one brick, starting from zero (DVR: premultiplied partial RGBA, stopping when
+// the total alpha A_front + (1 - A_front) A_partial reaches term, A_front read
+// from the running image), and write the brick's partial image.  Bricks of one
+// wavefront (equal visibility key) never share a ray, so their partials are
+// disjoint.  `slots` maps item.slot to brick storage.
+template <int MODE, int SAMPLING, int DT>
+__global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__restrict__ jobs,
+                                                            const BrickItem *__restrict__ items, int64_t n_items,
+                                                            const uint8_t *slot_base, int64_t slot_bytes,
+                                                            const float *__restrict__ running,
+                                                            float *__restrict__ partial,
+                                                            unsigned long long *samples)
+{
+    __shared__ float4 s_tf[256];
+    const int64_t item_id = blockIdx.x;
+    if (item_id >= n_items) return;
+    const BrickItem it = items[item_id];
+    const JobDesc &J = jobs[it.job];
+    if (MODE == 1) {
+        s_tf[threadIdx.x] = J.tf[threadIdx.x];
+        __syncthreads();
+    }
+    const CubeView &cv = J.cv;
+    int lx, ly;
+    tile_pixel(J.tile_w, lx, ly);
+    const int px = it.tx + lx, py = it.ty + ly;
+    uint32_t nsamp = 0;
+    if (px < J.vp.W && py < J.vp.H) {
+        const int bx = it.brick % cv.nb[0], by = (it.brick / cv.nb[0]) % cv.nb[1], bz = it.brick / (cv.nb[0] * cv.nb[1]);
+        const int ox = bx << cv.logB, oy = by << cv.logB, oz = bz << cv.logB;
+        const uint8_t *bp = slot_base + (int64_t)it.slot * slot_bytes;
+        const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + it.brick) : 1.f;
+        const int bkey = abs(bx - J.vp.ec[0]) + abs(by - J.vp.ec[1]) + abs(bz - J.vp.ec[2]);
+        float o[3], d[3], tin, tout;
+        const int64_t pix = (int64_t)py * J.vp.W + px;
+        const int64_t gpix = J.vp.out_offset + pix;
+        float afront = 0.f;
+        if (MODE == 1) afront = running[4 * gpix + 3];
+        if (ray_setup(J.vp, cv.fdims, px, py, o, d, tin, tout) && !(MODE == 1 && afront >= J.term)) {
+            // estimate the first sample inside the brick box from a slab test
+            float lo = tin, hi = tout;
+            const int oc[3] = {ox, oy, oz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (d[a] == 0.f) continue;
+                const float b0 = (float)oc[a], b1 = fminf((float)(oc[a] + cv.B), cv.fdims[a]);
+                float t0 = (b0 - o[a]) / d[a], t1 = (b1 - o[a]) / d[a];
+                if (t0 > t1) {
+                    const float tmp = t0;
+                    t0 = t1;
+                    t1 = tmp;
+                }
+                lo = fmaxf(lo, t0);
+                hi = fminf(hi, t1);
+            }
+            int k = max(0, (int)ceilf((lo - tin) / J.step - 0.5f) - 1);
+            float p[3];
+            bool found = false;
+            // walk to the first sample whose voxel lies in this brick: keys grow along the ray
+            for (int it2 = 0; it2 < 8 && lo <= hi + 1.f; ++it2) {
+                const float tk = sample_t(tin, k, J.step);
+                if (!(tk < tout)) {
+                    if (k == 0) break;
+                    --k;
+                    continue;
+                }
+                if (member(cv, o, d, tk, bx, by, bz, p)) {
+                    found = true;
+                    break;
+                }
+                const int key = brick_key_of(cv, J.vp, p);
+                if (key < bkey) ++k;
+                else if (key > bkey && k > 0) --k;
+                else break;
+            }
+            if (found) {
+                while (k > 0 && member(cv, o, d, sample_t(tin, k - 1, J.step), bx, by, bz, p)) --k;
+                float m = -FLT_MAX, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+                for (;; ++k) {
+                    const float tk = sample_t(tin, k, J.step);
+                    if (!(tk < tout)) break;
+                    if (!member(cv, o, d, tk, bx, by, bz, p)) break;
+                    float s;
+                    if (SAMPLING == VRC_NEAREST) {
+                        s = nearest_in_brick<DT>(cv, bp, min(max((int)floorf(p[0]), 0), cv.dims[0] - 1),
+                                                 min(max((int)floorf(p[1]), 0), cv.dims[1] - 1),
+                                                 min(max((int)floorf(p[2]), 0), cv.dims[2] - 1), ox, oy, oz, scale);
+                    } else {
+                        s = tri_in_brick<DT>(cv, bp, axis_tri(p[0], cv.dims[0]), axis_tri(p[1], cv.dims[1]),
+                                             axis_tri(p[2], cv.dims[2]), ox, oy, oz, scale);
+                    }
+                    ++nsamp;
+                    if (MODE == 0) {
+                        m = fmaxf(m, s);
+                    } else {
+                        if (s == s) {
+                            const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
+                            const float a = opacity(c.w, J.step, J.opacity_correction);
+                            const float w = (1.f - A) * a;
+                            cr = fmaf(w, c.x, cr);
+                            cg = fmaf(w, c.y, cg);
+                            cb = fmaf(w, c.z, cb);
+                            A += w;
+                        }
+                        if (fmaf(1.f - afront, A, afront) >= J.term) break;
+                    }
+                }
+                if (MODE == 0) partial[gpix] = m;
+                else reinterpret_cast<float4 *>(partial)[gpix] = make_float4(cr, cg, cb, A);
+            }
+        }
+    }
+    if (samples) warp_count(samples, nsamp);
+}
+
+// Sort-last composite of a partial image into the running image (DVR: over,
+// running = running + (1 - running.A) * partial; MIP: max), then reset the
+// partial (DVR 0, MIP -FLT_MAX) when `reset` is set.
+template <int MODE>
+__global__ void k_composite(float *running, float *partial, const float *front, const float *back, float *out,
+                            int64_t n, int reset)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (MODE == 0) {
+            if (running) {
+                running[i] = fmaxf(running[i], partial[i]);
+                if (reset) partial[i] = -FLT_MAX;
+            } else {
+                out[i] = fmaxf(front[i], back[i]);
+            }
+        } else {
+            float4 f, b;
+            if (running) {
+                f = reinterpret_cast<float4 *>(running)[i];
+                b = reinterpret_cast<float4 *>(partial)[i];
+            } else {
+                f = reinterpret_cast<const float4 *>(front)[i];
+                b = reinterpret_cast<const float4 *>(back)[i];
+            }
+            const float t = 1.f - f.w;
+            const float4 r = make_float4(fmaf(t, b.x, f.x), fmaf(t, b.y, f.y), fmaf(t, b.z, f.z), fmaf(t, b.w, f.w));
+            if (running) {
+                reinterpret_cast<float4 *>(running)[i] = r;
+                if (reset) reinterpret_cast<float4 *>(partial)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                reinterpret_cast<float4 *>(out)[i] = r;
+            }
+        }
+    }
+}
+
+template <int MODE>
+__global__ void k_fill(float *img, int64_t n, float v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        img[i] = v;
+}
+
+// ------------------------------------------------------------------ host side
+
+CubeView cube_view(const Cube *c)
+{
+    CubeView v;
+    const BrickGeom &g = c->g;
+    v.pool = (const uint8_t *)c->pool;
+    v.scales = c->scales;
+    v.brick_bytes = g.brick_bytes;
+    v.B = g.B;
+    v.logB = g.logB;
+    v.P = g.P;
+    v.O = g.O;
+    v.R = g.R;
+    for (int a = 0; a < 3; ++a) {
+        v.nb[a] = g.nb[a];
+        v.dims[a] = (int32_t)g.dims[a];
+        v.fdims[a] = (float)g.dims[a];
+    }
+    v.dtype = g.dtype;
+    return v;
+}
+
+ViewParams view_params(const vrc_camera &cam, const BrickGeom &g, int W, int H, int64_t out_offset)
+{
+    ViewParams vp;
+    float basis[12];
+    camera_basis(cam, W, H, basis);
+    for (int a = 0; a < 3; ++a) {
+        vp.O0[a] = basis[a];
+        vp.D0[a] = basis[3 + a];
+        vp.DX[a] = basis[6 + a];
+        vp.DY[a] = basis[9 + a];
+    }
+    vp.kind = cam.kind;
+    vp.W = W;
+    vp.H = H;
+    for (int a = 0; a < 3; ++a) {
+        if (cam.kind == VRC_CAM_PERSP) {
+            double f = std::floor((double)cam.eye[a] / (double)g.B);
+            f = std::min(std::max(f, -1.0), (double)g.nb[a]);
+            vp.ec[a] = (int32_t)f;
+        } else {
+            vp.ec[a] = vp.D0[a] > 0 ? -1 : (vp.D0[a] < 0 ? g.nb[a] : 0);
+        }
+    }
+    vp.out_offset = out_offset;
+    return vp;
+}
+
+bool valid_cam(const vrc_camera &c)
+{
+    if (c.kind != VRC_CAM_ORTHO && c.kind != VRC_CAM_PERSP) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(c.eye[a]) || !std::isfinite(c.center[a]) || !std::isfinite(c.up[a])) return false;
+    double w[3], cr[3];
+    for (int a = 0; a < 3; ++a) w[a] = (double)c.center[a] - c.eye[a];
+    cr[0] = w[1] * c.up[2] - w[2] * c.up[1];
+    cr[1] = w[2] * c.up[0] - w[0] * c.up[2];
+    cr[2] = w[0] * c.up[1] - w[1] * c.up[0];
+    if (cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2] == 0.0) return false;  // up parallel to view / eye == center
+    if (c.kind == VRC_CAM_PERSP && !(c.fovy_deg > 0.f && c.fovy_deg < 179.f)) return false;
+    if (c.kind == VRC_CAM_ORTHO && !(c.ortho_height > 0.f && std::isfinite(c.ortho_height))) return false;
+    return true;
+}
+
+vrc_status check_rc(vrc_ctx *ctx, const vrc_raycfg *rc)
+{
+    if (!rc) return set_err(ctx, VRC_E_INVAL, "null raycfg");
+    if (rc->width < 1 || rc->height < 1 || rc->width > 16384 || rc->height > 16384)
+        return set_err(ctx, VRC_E_INVAL, "image size out of range");
+    if (!(rc->step > 0.f) || !std::isfinite(rc->step) || rc->step < 1e-3f)
+        return set_err(ctx, VRC_E_INVAL, "step must be >= 1e-3");
+    if (rc->sampling != VRC_NEAREST && rc->sampling != VRC_TRILINEAR) return set_err(ctx, VRC_E_INVAL, "bad sampling");
+    if (rc->opacity_correction != 0 && rc->opacity_correction != 1) return set_err(ctx, VRC_E_INVAL, "bad opacity flag");
+    if (rc->path != VRC_PATH_FUSED && rc->path != VRC_PATH_SORTLAST) return set_err(ctx, VRC_E_INVAL, "bad path");
+    const bool tile0 = rc->tile_w == 0 && rc->tile_h == 0;
+    const bool tile_ok = (rc->tile_w == 8 || rc->tile_w == 16 || rc->tile_w == 32) && rc->tile_w * rc->tile_h == 256;
+    if (!tile0 && !tile_ok) return set_err(ctx, VRC_E_INVAL, "tile must be 8x32, 16x16 or 32x8");
+    return VRC_OK;
+}
+
+void pick_tile(const Cube *c, const vrc_raycfg &rc, int &tw, int &th)
+{
+    if (rc.tile_w) {
+        tw = rc.tile_w;
+        th = rc.tile_h;
+    } else if (c->tile_w) {
+        tw = c->tile_w;
+        th = c->tile_h;
+    } else {
+        tw = 16;
+        th = 16;
+    }
+}
+
+JobDesc make_job(const Cube *c, const vrc_camera &cam, const vrc_raycfg &rc, int mode, float term, const float4 *dtf,
+                 float *out, int64_t out_offset, int tw, int th)
+{
+    JobDesc j;
+    j.cv = cube_view(c);
+    j.vp = view_params(cam, c->g, rc.width, rc.height, out_offset);
+    j.step = rc.step;
+    j.term = term;
+    j.vmin = c->vmin;
+    const float range = c->vmax - c->vmin;
+    j.inv_range = range > 0.f ? 1.f / range : 0.f;
+    j.opacity_correction = rc.opacity_correction;
+    j.tile_w = tw;
+    j.tile_h = th;
+    j.tiles_x = (rc.width + tw - 1) / tw;
+    j.tiles_y = (rc.height + th - 1) / th;
+    j.item_begin = 0;
+    j.tf = dtf;
+    j.out = out + (mode == 0 ? 1 : 4) * out_offset;
+    j.samples = nullptr;
+    (void)mode;
+    return j;
+}
+
+template <int MODE, int SAMPLING, int DT>
+int fused_occupancy()
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fused<MODE, SAMPLING, DT>, kThreads, 0);
+    return n > 0 ? n : 1;
+}
+
+template <int MODE, int SAMPLING, int DT>
+void launch_fused_t(int grid, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total, int *counter)
+{
+    k_render_fused<MODE, SAMPLING, DT><<<grid, kThreads, 0, st>>>(jobs, n_jobs, total, counter);
+}
+
+typedef void (*fused_fn)(int, cudaStream_t, const JobDesc *, int, int64_t, int *);
+typedef int (*occ_fn)();
+
+template <int MODE>
+fused_fn pick_fused2(int sampling, int dt)
+{
+    if (sampling == VRC_NEAREST) {
+        if (dt == VRC_F32) return launch_fused_t<MODE, VRC_NEAREST, VRC_F32>;
+        if (dt == VRC_BF16) return launch_fused_t<MODE, VRC_NEAREST, VRC_BF16>;
+        return launch_fused_t<MODE, VRC_NEAREST, VRC_FP8E4M3>;
+    }
+    if (dt == VRC_F32) return launch_fused_t<MODE, VRC_TRILINEAR, VRC_F32>;
+    if (dt == VRC_BF16) return launch_fused_t<MODE, VRC_TRILINEAR, VRC_BF16>;
+    return launch_fused_t<MODE, VRC_TRILINEAR, VRC_FP8E4M3>;
+}
+fused_fn pick_fused(int mode, int sampling, int dt)
+{
+    return mode == 0 ? pick_fused2<0>(sampling, dt) : pick_fused2<1>(sampling, dt);
+}
+template <int MODE>
+occ_fn pick_occ2(int sampling, int dt)
+{
+    if (sampling == VRC_NEAREST) {
+        if (dt == VRC_F32) return fused_occupancy<MODE, VRC_NEAREST, VRC_F32>;
+        if (dt == VRC_BF16) return fused_occupancy<MODE, VRC_NEAREST, VRC_BF16>;
+        return fused_occupancy<MODE, VRC_NEAREST, VRC_FP8E4M3>;
+    }
+    if (dt == VRC_F32) return fused_occupancy<MODE, VRC_TRILINEAR, VRC_F32>;
+    if (dt == VRC_BF16) return fused_occupancy<MODE, VRC_TRILINEAR, VRC_BF16>;
+    return fused_occupancy<MODE, VRC_TRILINEAR, VRC_FP8E4M3>;
+}
+int occupancy(int mode, int sampling, int dt) { return mode == 0 ? pick_occ2<0>(sampling, dt)() : pick_occ2<1>(sampling, dt)(); }
+
+template <int MODE, int SAMPLING, int DT>
+void launch_bricks_t(int64_t n, cudaStream_t st, const JobDesc *jobs, const BrickItem *items, const uint8_t *slot_base,
+                     int64_t slot_bytes, const float *running, float *partial, unsigned long long *samples)
+{
+    k_render_bricks<MODE, SAMPLING, DT><<<(unsigned)n, kThreads, 0, st>>>(jobs, items, n, slot_base, slot_bytes,
+                                                                         running, partial, samples);
+}
+typedef void (*bricks_fn)(int64_t, cudaStream_t, const JobDesc *, const BrickItem *, const uint8_t *, int64_t,
+                          const float *, float *, unsigned long long *);
+template <int MODE>
+bricks_fn pick_bricks2(int sampling, int dt)
+{
+    if (sampling == VRC_NEAREST) {
+        if (dt == VRC_F32) return launch_bricks_t<MODE, VRC_NEAREST, VRC_F32>;
+        if (dt == VRC_BF16) return launch_bricks_t<MODE, VRC_NEAREST, VRC_BF16>;
+        return launch_bricks_t<MODE, VRC_NEAREST, VRC_FP8E4M3>;
+    }
+    if (dt == VRC_F32) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_F32>;
+    if (dt == VRC_BF16) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_BF16>;
+    return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_FP8E4M3>;
+}
+bricks_fn pick_bricks(int mode, int sampling, int dt)
+{
+    return mode == 0 ? pick_bricks2<0>(sampling, dt) : pick_bricks2<1>(sampling, dt);
+}
+
+// Scratch layout helpers: [counter | samples | tf | jobs | items ...]
+struct Arena {
+    char *base;
+    size_t off, cap;
+    template <class T>
+    T *take(size_t n)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += sizeof(T) * n;
+        return p;
+    }
+};
+
+// ----------------------------------------------------- brick screen footprints
+
+// Pixel bounding box of brick b (conservative; full image if the brick reaches
+// behind the eye).  Returns false if it is entirely off screen.
+bool brick_bbox(const vrc_camera &cam, const BrickGeom &g, int W, int H, int b, int box[4])
+{
+    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+    double lo[3] = {(double)bx * g.B, (double)by * g.B, (double)bz * g.B};
+    double hi[3] = {std::min((double)(bx + 1) * g.B, (double)g.dims[0]), std::min((double)(by + 1) * g.B, (double)g.dims[1]),
+                    std::min((double)(bz + 1) * g.B, (double)g.dims[2])};
+    for (int a = 0; a < 3; ++a) {
+        lo[a] -= 1.0;
+        hi[a] += 1.0;
+    }
+    double e[3], w[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) {
+        e[a] = cam.eye[a];
+        w[a] = (double)cam.center[a] - cam.eye[a];
+    }
+    double lw = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    for (int a = 0; a < 3; ++a) w[a] /= lw;
+    r[0] = w[1] * cam.up[2] - w[2] * cam.up[1];
+    r[1] = w[2] * cam.up[0] - w[0] * cam.up[2];
+    r[2] = w[0] * cam.up[1] - w[1] * cam.up[0];
+    double lr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) r[a] /= lr;
+    u[0] = r[1] * w[2] - r[2] * w[1];
+    u[1] = r[2] * w[0] - r[0] * w[2];
+    u[2] = r[0] * w[1] - r[1] * w[0];
+    const double asp = (double)W / H;
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int c = 0; c < 8; ++c) {
+        double p[3] = {(c & 1) ? hi[0] : lo[0], (c & 2) ? hi[1] : lo[1], (c & 4) ? hi[2] : lo[2]};
+        double dv[3] = {p[0] - e[0], p[1] - e[1], p[2] - e[2]};
+        double zc = dv[0] * w[0] + dv[1] * w[1] + dv[2] * w[2];
+        double xc = dv[0] * r[0] + dv[1] * r[1] + dv[2] * r[2];
+        double yc = dv[0] * u[0] + dv[1] * u[1] + dv[2] * u[2];
+        double xn, yn;
+        if (cam.kind == VRC_CAM_PERSP) {
+            if (zc <= 1e-6) {
+                box[0] = 0;
+                box[1] = 0;
+                box[2] = W;
+                box[3] = H;
+                return true;
+            }
+            const double h = std::tan((double)cam.fovy_deg * 3.14159265358979323846 / 360.0);
+            xn = xc / (zc * h * asp);
+            yn = yc / (zc * h);
+        } else {
+            const double h = 0.5 * cam.ortho_height;
+            xn = xc / (h * asp);
+            yn = yc / h;
+        }
+        const double pxf = (xn + 1.0) * 0.5 * W - 0.5, pyf = (1.0 - yn) * 0.5 * H - 0.5;
+        xmin = std::min(xmin, pxf);
+        xmax = std::max(xmax, pxf);
+        ymin = std::min(ymin, pyf);
+        ymax = std::max(ymax, pyf);
+    }
+    const double x0 = std::floor(xmin) - 2, x1 = std::ceil(xmax) + 3, y0 = std::floor(ymin) - 2, y1 = std::ceil(ymax) + 3;
+    if (x1 <= 0 || y1 <= 0 || x0 >= W || y0 >= H) return false;
+    box[0] = (int)std::max(0.0, x0);
+    box[1] = (int)std::max(0.0, y0);
+    box[2] = (int)std::min((double)W, x1);
+    box[3] = (int)std::min((double)H, y1);
+    return box[0] < box[2] && box[1] < box[3];
+}
+
+struct Wave {
+    int key;
+    std::vector<int> bricks;  // bricks of this wavefront that some view sees
+};
+
+// Sort-last plan: wavefronts (equal Manhattan distance of the brick from the
+// eye's brick cell) in front-to-back order, with per-(view, brick) tiles.
+struct SortLastPlan {
+    std::vector<int> wave_key;                 // per wavefront
+    std::vector<std::vector<int>> wave_bricks; // distinct bricks per wavefront
+    std::vector<BrickItem> items;              // grouped by wavefront, then brick
+    std::vector<int64_t> brick_item_begin;     // per (wavefront, brick) entry
+    std::vector<int64_t> wave_item_begin;      // per wavefront (+ end)
+};
+
+void plan_sortlast(const Cube *c, const std::vector<JobDesc> &jobs, const std::vector<vrc_camera> &cams,
+                   SortLastPlan &plan)
+{
+    const BrickGeom &g = c->g;
+    const int nb = (int)g.nbricks;
+    // keys per view; wavefront index = key (0 .. max) is a valid order for every view
+    int maxkey = 0;
+    std::vector<std::vector<int>> key(jobs.size(), std::vector<int>(nb));
+    for (size_t v = 0; v < jobs.size(); ++v)
+        for (int b = 0; b < nb; ++b) {
+            const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+            const int k = std::abs(bx - jobs[v].vp.ec[0]) + std::abs(by - jobs[v].vp.ec[1]) + std::abs(bz - jobs[v].vp.ec[2]);
+            key[v][b] = k;
+            maxkey = std::max(maxkey, k);
+        }
+    plan.items.clear();
+    plan.wave_key.clear();
+    plan.wave_bricks.clear();
+    plan.wave_item_begin.clear();
+    plan.brick_item_begin.clear();
+    for (int k = 0; k <= maxkey; ++k) {
+        std::vector<int> bricks;
+        const int64_t wbeg = (int64_t)plan.items.size();
+        for (int b = 0; b < nb; ++b) {
+            const int64_t bbeg = (int64_t)plan.items.size();
+            for (size_t v = 0; v < jobs.size(); ++v) {
+                if (key[v][b] != k) continue;
+                int box[4];
+                if (!brick_bbox(cams[v], g, jobs[v].vp.W, jobs[v].vp.H, b, box)) continue;
+                const int tw = jobs[v].tile_w, th = jobs[v].tile_h;
+                for (int y = (box[1] / th) * th; y < box[3]; y += th)
+                    for (int x = (box[0] / tw) * tw; x < box[2]; x += tw)
+                        plan.items.push_back(BrickItem{(int32_t)v, b, b, (int16_t)x, (int16_t)y});
+            }
+            if ((int64_t)plan.items.size() > bbeg) {
+                bricks.push_back(b);
+                plan.brick_item_begin.push_back(bbeg);
+            }
+        }
+        if ((int64_t)plan.items.size() > wbeg) {
+            plan.wave_key.push_back(k);
+            plan.wave_bricks.push_back(bricks);
+            plan.wave_item_begin.push_back(wbeg);
+        }
+    }
+    plan.wave_item_begin.push_back((int64_t)plan.items.size());
+    plan.brick_item_begin.push_back((int64_t)plan.items.size());
+}
+
+int grid_for(int64_t n, int cap) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, cap)); }
+
+vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                         const vrc_raycfg *rc, const float *tf_rgba, float term, float *out, cudaStream_t st, int mode,
+                         int ctas_override, unsigned long long *samples_out, bool host_sync_samples);
+
+}  // namespace
+
+// ------------------------------------------------------------------ render entry
+
+namespace {
+
+vrc_status validate_render(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg *rc,
+                           const float *tf, float term, float *out, int mode, Cube **cube)
+{
+    if (!ctx) return VRC_E_INVAL;
+    if (!cams || !out || n_views < 1 || n_views > 4096) return set_err(ctx, VRC_E_INVAL, "bad cams/out/n_views");
+    vrc_status s = check_rc(ctx, rc);
+    if (s != VRC_OK) return s;
+    if (mode == 1 && (!tf || !(term > 0.f) || std::isnan(term))) return set_err(ctx, VRC_E_INVAL, "bad tf/term");
+    if (mode == 1)
+        for (int i = 0; i < 1024; ++i)
+            if (!std::isfinite(tf[i])) return set_err(ctx, VRC_E_INVAL, "tf has non-finite entries");
+    for (int v = 0; v < n_views; ++v)
+        if (!valid_cam(cams[v])) return set_err(ctx, VRC_E_INVAL, "bad camera %d", v);
+    Cube *c = find_cube(ctx, cube_id);
+    if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    *cube = c;
+    return VRC_OK;
+}
+
+vrc_status render_streamed(vrc_ctx *ctx, Cube *c, const std::vector<JobDesc> &jobs_in,
+                           const std::vector<vrc_camera> &cams, const vrc_raycfg &rc, float *out, int64_t npix_total,
+                           int mode, cudaStream_t st, unsigned long long *dsamples, Arena &ar, const float4 *dtf,
+                           const JobDesc *djobs);
+
+vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg *rc,
+                         const float *tf_rgba, float term, float *out, cudaStream_t st, int mode, int ctas_override,
+                         unsigned long long *samples_out, bool host_sync_samples)
+{
+    Cube *c = nullptr;
+    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term, out, mode, &c);
+    if (s != VRC_OK) return s;
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    int tw, th;
+    pick_tile(c, *rc, tw, th);
+    const int64_t npix = (int64_t)rc->width * rc->height;
+    std::vector<JobDesc> jobs(n_views);
+    std::vector<vrc_camera> camv(cams, cams + n_views);
+    int64_t total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        jobs[v] = make_job(c, cams[v], *rc, mode, term, nullptr, out, v * npix, tw, th);
+        jobs[v].item_begin = total;
+        total += (int64_t)jobs[v].tiles_x * jobs[v].tiles_y;
+    }
+    const bool sortlast = c->streamed || rc->path == VRC_PATH_SORTLAST;
+    SortLastPlan plan;
+    if (sortlast) plan_sortlast(c, jobs, camv, plan);
+    const size_t img_floats = (size_t)n_views * npix * (mode == 0 ? 1 : 4);
+    size_t need = 4096 + 1024 * 4 + sizeof(JobDesc) * n_views + 256 * 4;
+    if (sortlast) need += sizeof(BrickItem) * plan.items.size() + sizeof(float) * img_floats + 1024;
+    void *scr = nullptr;
+    if ((s = scratch_get(ctx, need, &scr)) != VRC_OK) return s;
+    Arena ar{(char *)scr, 0, need};
+    int *counter = ar.take<int>(1);
+    unsigned long long *dsamples = ar.take<unsigned long long>(1);
+    float4 *dtf = ar.take<float4>(256);
+    JobDesc *djobs = ar.take<JobDesc>(n_views);
+    for (auto &j : jobs) {
+        if (mode == 1) j.tf = dtf;
+        j.samples = dsamples;
+    }
+    VRC_CK(ctx, cudaMemsetAsync(dsamples, 0, sizeof(unsigned long long), st));
+    if (mode == 1) VRC_CK(ctx, cudaMemcpyAsync(dtf, tf_rgba, 1024 * 4, cudaMemcpyHostToDevice, st));
+    VRC_CK(ctx, cudaMemcpyAsync(djobs, jobs.data(), sizeof(JobDesc) * n_views, cudaMemcpyHostToDevice, st));
+    if (!sortlast) {
+        VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
+        int per_sm = ctas_override > 0 ? ctas_override : (c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype));
+        const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
+        pick_fused(mode, rc->sampling, c->g.dtype)(grid, st, djobs, n_views, total, counter);
+        count_launch(ctx);
+        VRC_CK(ctx, cudaGetLastError());
+    } else if (!c->streamed) {
+        BrickItem *ditems = ar.take<BrickItem>(std::max<size_t>(1, plan.items.size()));
+        float *partial = ar.take<float>(img_floats);
+        if (!plan.items.empty())
+            VRC_CK(ctx, cudaMemcpyAsync(ditems, plan.items.data(), sizeof(BrickItem) * plan.items.size(),
+                                        cudaMemcpyHostToDevice, st));
+        const int64_t n = (int64_t)img_floats;
+        const int g = grid_for(n, ctx->sm_count * 8);
+        if (mode == 0) {
+            k_fill<0><<<g, 256, 0, st>>>(out, n, -FLT_MAX);
+            k_fill<0><<<g, 256, 0, st>>>(partial, n, -FLT_MAX);
+        } else {
+            VRC_CK(ctx, cudaMemsetAsync(out, 0, sizeof(float) * n, st));
+            VRC_CK(ctx, cudaMemsetAsync(partial, 0, sizeof(float) * n, st));
+        }
+        count_launch(ctx, mode == 0 ? 2 : 0);
+        bricks_fn bf = pick_bricks(mode, rc->sampling, c->g.dtype);
+        const int64_t npx = (int64_t)n_views * npix;
+        for (size_t w = 0; w + 1 < plan.wave_item_begin.size(); ++w) {
+            const int64_t b0 = plan.wave_item_begin[w], b1 = plan.wave_item_begin[w + 1];
+            if (b1 <= b0) continue;
+            bf(b1 - b0, st, djobs, ditems + b0, (const uint8_t *)c->pool, c->g.brick_bytes, out, partial, dsamples);
+            const int gc = grid_for(npx, ctx->sm_count * 8);
+            if (mode == 0) k_composite<0><<<gc, 256, 0, st>>>(out, partial, nullptr, nullptr, nullptr, npx, 1);
+            else k_composite<1><<<gc, 256, 0, st>>>(out, partial, nullptr, nullptr, nullptr, npx, 1);
+            count_launch(ctx, 2);
+        }
+        VRC_CK(ctx, cudaGetLastError());
+    } else {
+        s = render_streamed(ctx, c, jobs, camv, *rc, out, (int64_t)n_views * npix, mode, st, dsamples, ar, dtf, djobs);
+        if (s != VRC_OK) return s;
+    }
+    if (samples_out) {
+        VRC_CK(ctx, cudaMemcpyAsync(samples_out, dsamples, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        if (host_sync_samples) VRC_CK(ctx, cudaStreamSynchronize(st));
+    } else {
+        VRC_CK(ctx, cudaMemcpyAsync(ctx->h_samples, dsamples, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        VRC_CK(ctx, cudaEventRecord(ctx->ev_samples, st));
+    }
+    return VRC_OK;
+}
+
+// Out-of-core: bricks of a streamed cube are copied from pinned host slots to a
+// device ring on a side stream, in wavefront order, in chunks of half the ring;
+// chunk i renders while chunk i+1 copies.  Each wavefront's partial image is
+// composited after its last chunk.
+vrc_status render_streamed(vrc_ctx *ctx, Cube *c, const std::vector<JobDesc> &jobs_in,
+                           const std::vector<vrc_camera> &cams, const vrc_raycfg &rc, float *out, int64_t npx,
+                           int mode, cudaStream_t st, unsigned long long *dsamples, Arena &ar, const float4 *dtf,
+                           const JobDesc *djobs)
+{
+    (void)dtf;
+    const BrickGeom &g = c->g;
+    SortLastPlan plan;
+    plan_sortlast(c, jobs_in, cams, plan);
+    // chunks: runs of consecutive bricks inside one wavefront, at most half the ring
+    const int half = c->ring / 2;
+    struct Chunk {
+        int64_t item_b, item_e;
+        std::vector<int> bricks;
+        bool wave_end;
+        int parity;
+    };
+    std::vector<Chunk> chunks;
+    size_t bi = 0;  // index into plan.brick_item_begin
+    for (size_t w = 0; w < plan.wave_bricks.size(); ++w) {
+        const auto &wb = plan.wave_bricks[w];
+        for (size_t k = 0; k < wb.size(); k += half) {
+            Chunk ch;
+            ch.item_b = plan.brick_item_begin[bi];
+            const size_t n = std::min<size_t>(half, wb.size() - k);
+            for (size_t q = 0; q < n; ++q) ch.bricks.push_back(wb[k + q]);
+            bi += n;
+            ch.item_e = plan.brick_item_begin[bi];
+            ch.wave_end = k + n == wb.size();
+            ch.parity = (int)(chunks.size() & 1);
+            chunks.push_back(ch);
+        }
+    }
+    // ring slot of each item: parity half + position of its brick in the chunk
+    for (const Chunk &ch : chunks)
+        for (int64_t it = ch.item_b; it < ch.item_e; ++it) {
+            const int pos = (int)(std::find(ch.bricks.begin(), ch.bricks.end(), plan.items[it].brick) - ch.bricks.begin());
+            plan.items[it].slot = ch.parity * half + pos;
+        }
+    const int64_t img_floats = npx * (mode == 0 ? 1 : 4);
+    BrickItem *ditems = ar.take<BrickItem>(std::max<size_t>(1, plan.items.size()));
+    float *partial = ar.take<float>(img_floats);
+    if (!plan.items.empty())
+        VRC_CK(ctx, cudaMemcpyAsync(ditems, plan.items.data(), sizeof(BrickItem) * plan.items.size(),
+                                    cudaMemcpyHostToDevice, st));
+    const int gfill = grid_for(img_floats, ctx->sm_count * 8);
+    if (mode == 0) {
+        k_fill<0><<<gfill, 256, 0, st>>>(out, img_floats, -FLT_MAX);
+        k_fill<0><<<gfill, 256, 0, st>>>(partial, img_floats, -FLT_MAX);
+        count_launch(ctx, 2);
+    } else {
+        VRC_CK(ctx, cudaMemsetAsync(out, 0, sizeof(float) * img_floats, st));
+        VRC_CK(ctx, cudaMemsetAsync(partial, 0, sizeof(float) * img_floats, st));
+    }
+    cudaStream_t cs;
+    VRC_CK(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    std::vector<cudaEvent_t> ready(chunks.size()), consumed(chunks.size());
+    cudaEvent_t entry;
+    cudaEventCreateWithFlags(&entry, cudaEventDisableTiming);
+    cudaEventRecord(entry, st);             // earlier work on `st` may still use the ring
+    cudaStreamWaitEvent(cs, entry, 0);
+    vrc_status status = VRC_OK;
+    bricks_fn bf = pick_bricks(mode, rc.sampling, VRC_F32);
+    size_t made = 0;
+    for (size_t i = 0; i < chunks.size() && status == VRC_OK; ++i) {
+        const Chunk &ch = chunks[i];
+        cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&consumed[i], cudaEventDisableTiming);
+        made = i + 1;
+        if (i >= 2) cudaStreamWaitEvent(cs, consumed[i - 2], 0);   // slots of this parity are free again
+        for (size_t q = 0; q < ch.bricks.size(); ++q) {
+            if (inject_fire(ctx, VRC_INJECT_H2D)) {
+                status = set_err(ctx, VRC_E_INJECTED, "injected host-to-device brick copy failure");
+                break;
+            }
+            const int64_t hslot = ch.bricks[q] % c->n_host;
+            const char *src = (const char *)c->host_pool + hslot * g.brick_bytes;
+            char *dst = (char *)c->ring_pool + (int64_t)(ch.parity * half + q) * g.brick_bytes;
+            cudaError_t e = cudaMemcpyAsync(dst, src, g.brick_bytes, cudaMemcpyHostToDevice, cs);
+            if (e != cudaSuccess) {
+                status = cuda_err(ctx, e, "brick H2D");
+                break;
+            }
+        }
+        if (status != VRC_OK) break;
+        cudaEventRecord(ready[i], cs);
+        cudaStreamWaitEvent(st, ready[i], 0);
+        if (ch.item_e > ch.item_b)
+            bf(ch.item_e - ch.item_b, st, djobs, ditems + ch.item_b, (const uint8_t *)c->ring_pool, g.brick_bytes,
+               out, partial, dsamples);
+        count_launch(ctx);
+        cudaEventRecord(consumed[i], st);
+        if (ch.wave_end) {
+            const int gc = grid_for(npx, ctx->sm_count * 8);
+            if (mode == 0) k_composite<0><<<gc, 256, 0, st>>>(out, partial, nullptr, nullptr, nullptr, npx, 1);
+            else k_composite<1><<<gc, 256, 0, st>>>(out, partial, nullptr, nullptr, nullptr, npx, 1);
+            count_launch(ctx);
+        }
+    }
+    // the copy stream must not outlive pending copies unnoticed: join it into `st`
+    cudaEvent_t tail;
+    cudaEventCreateWithFlags(&tail, cudaEventDisableTiming);
+    cudaEventRecord(tail, cs);
+    cudaStreamWaitEvent(st, tail, 0);
+    cudaEventDestroy(tail);
+    cudaEventDestroy(entry);
+    for (size_t i = 0; i < made; ++i) {
+        cudaEventDestroy(ready[i]);
+        cudaEventDestroy(consumed[i]);
+    }
+    cudaStreamDestroy(cs);
+    if (status != VRC_OK) return status;
+    VRC_CK(ctx, cudaGetLastError());
+    return VRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vrc_status vrc_render_mip(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg *rc,
+                          float *out, void *stream)
+{
+    return render_common(ctx, cube_id, cams, n_views, rc, nullptr, 0.f, out, (cudaStream_t)stream, 0, 0, nullptr, false);
+}
+
+vrc_status vrc_render_dvr(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg *rc,
+                          const float *tf_rgba, float term_alpha, float *out, void *stream)
+{
+    return render_common(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, (cudaStream_t)stream, 1, 0, nullptr,
+                         false);
+}
+
+vrc_status vrc_composite(vrc_ctx *ctx, const float *front, const float *back, float *out, int64_t n_pixels, int32_t mode,
+                         void *stream)
+{
+    if (!ctx || !front || !back || !out || n_pixels < 0 || (mode != 0 && mode != 1)) return VRC_E_INVAL;
+    if (n_pixels == 0) return VRC_OK;
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int g = grid_for(n_pixels, ctx->sm_count * 8);
+    if (mode == 0) k_composite<0><<<g, 256, 0, st>>>(nullptr, nullptr, front, back, out, n_pixels, 0);
+    else k_composite<1><<<g, 256, 0, st>>>(nullptr, nullptr, front, back, out, n_pixels, 0);
+    count_launch(ctx);
+    VRC_CK(ctx, cudaGetLastError());
+    return VRC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ graphs
+
+struct vrc_graph {
+    vrc_ctx *ctx;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    void *mem;
+    size_t mem_bytes;
+};
+
+extern "C" {
+
+vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                            const vrc_raycfg *rc, const float *tf_rgba, float term_alpha, float *out,
+                            vrc_graph **graph)
+{
+    if (!graph) return VRC_E_INVAL;
+    *graph = nullptr;
+    const int mode = tf_rgba ? 1 : 0;
+    Cube *c = nullptr;
+    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c);
+    if (s != VRC_OK) return s;
+    if (c->streamed || rc->path != VRC_PATH_FUSED)
+        return set_err(ctx, VRC_E_UNSUPPORTED, "graphs capture the fused path of resident cubes");
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    int tw, th;
+    pick_tile(c, *rc, tw, th);
+    const int64_t npix = (int64_t)rc->width * rc->height;
+    std::vector<JobDesc> jobs(n_views);
+    int64_t total = 0;
+    const size_t bytes = 4096 + 4096 + sizeof(JobDesc) * n_views + 1024;
+    void *mem = nullptr;
+    if ((s = dev_alloc(ctx, &mem, bytes)) != VRC_OK) return s;
+    Arena ar{(char *)mem, 0, bytes};
+    int *counter = ar.take<int>(1);
+    unsigned long long *dsamples = ar.take<unsigned long long>(1);
+    float4 *dtf = ar.take<float4>(256);
+    JobDesc *djobs = ar.take<JobDesc>(n_views);
+    for (int v = 0; v < n_views; ++v) {
+        jobs[v] = make_job(c, cams[v], *rc, mode, term_alpha, mode ? dtf : nullptr, out, v * npix, tw, th);
+        jobs[v].samples = dsamples;
+        jobs[v].item_begin = total;
+        total += (int64_t)jobs[v].tiles_x * jobs[v].tiles_y;
+    }
+    cudaError_t e = cudaSuccess;
+    if (mode) e = cudaMemcpy(dtf, tf_rgba, 4096, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(djobs, jobs.data(), sizeof(JobDesc) * n_views, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dev_free(ctx, mem, bytes);
+        return cuda_err(ctx, e, "graph upload");
+    }
+    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype);
+    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
+    cudaStream_t cs;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+        dev_free(ctx, mem, bytes);
+        return cuda_err(ctx, e, "graph stream");
+    }
+    vrc_graph *gph = new vrc_graph{ctx, nullptr, nullptr, mem, bytes};
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(counter, 0, sizeof(int), cs);
+        cudaMemsetAsync(dsamples, 0, sizeof(unsigned long long), cs);
+        pick_fused(mode, rc->sampling, c->g.dtype)(grid, cs, djobs, n_views, total, counter);
+        e = cudaStreamEndCapture(cs, &gph->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gph->exec, gph->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (gph->graph) cudaGraphDestroy(gph->graph);
+        dev_free(ctx, mem, bytes);
+        delete gph;
+        return cuda_err(ctx, e, "graph capture");
+    }
+    *graph = gph;
+    return VRC_OK;
+}
+
+vrc_status vrc_graph_launch(vrc_graph *g, void *stream)
+{
+    if (!g) return VRC_E_INVAL;
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_err(g->ctx, e, "cudaGraphLaunch");
+    count_launch(g->ctx);
+    return VRC_OK;
+}
+
+vrc_status vrc_graph_destroy(vrc_graph *g)
+{
+    if (!g) return VRC_E_INVAL;
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    dev_free(g->ctx, g->mem, g->mem_bytes);
+    delete g;
+    return VRC_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg *rc,
+                        const float *tf_rgba, float term_alpha, float *out, void *stream, vrc_tuning *result)
+{
+    const int mode = tf_rgba ? 1 : 0;
+    Cube *c = nullptr;
+    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c);
+    if (s != VRC_OK) return s;
+    if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "autotuning needs a resident cube");
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tiles[3][2] = {{8, 32}, {16, 16}, {32, 8}};
+    const int occ = occupancy(mode, rc->sampling, c->g.dtype);
+    cudaEvent_t e0, e1;
+    VRC_CK(ctx, cudaEventCreate(&e0));
+    VRC_CK(ctx, cudaEventCreate(&e1));
+    const int old_w = c->tile_w, old_h = c->tile_h, old_c = c->ctas_per_sm;
+    c->tile_w = c->tile_h = c->ctas_per_sm = 0;
+    double best = 1e300, dflt = 0;
+    int bw = 16, bh = 16, bc = occ;
+    for (int t = 0; t < 3; ++t)
+        for (int per_sm = 1; per_sm <= occ; ++per_sm) {
+            vrc_raycfg r = *rc;
+            r.path = VRC_PATH_FUSED;
+            r.tile_w = tiles[t][0];
+            r.tile_h = tiles[t][1];
+            double ms_best = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, st);
+                s = render_common(ctx, cube_id, cams, n_views, &r, tf_rgba, term_alpha, out, st, mode, per_sm, nullptr,
+                                  false);
+                cudaEventRecord(e1, st);
+                if (s != VRC_OK) break;
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_best = std::min(ms_best, (double)ms);
+            }
+            if (s != VRC_OK) break;
+            if (tiles[t][0] == 16 && per_sm == occ) dflt = ms_best;
+            if (ms_best < best) {
+                best = ms_best;
+                bw = tiles[t][0];
+                bh = tiles[t][1];
+                bc = per_sm;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != VRC_OK) {
+        c->tile_w = old_w;
+        c->tile_h = old_h;
+        c->ctas_per_sm = old_c;
+        return s;
+    }
+    c->tile_w = bw;
+    c->tile_h = bh;
+    c->ctas_per_sm = bc;
+    if (result) {
+        result->tile_w = bw;
+        result->tile_h = bh;
+        result->ctas_per_sm = bc;
+        result->reserved = 0;
+        result->best_ms = best;
+        result->default_ms = dflt;
+    }
+    return VRC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- serving helper
+
+size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs)
+{
+    return 1024 + 4096 * jobs.size() + sizeof(JobDesc) * jobs.size() + 1024;
+}
+
+size_t render_hetero_stage_bytes(size_t n_jobs) { return 4096 * n_jobs + sizeof(JobDesc) * n_jobs + 256; }
+
+// One persistent launch over renders of different cubes, image sizes, cameras
+// and transfer functions (all with the same mode/sampling/dtype).  Job i counts
+// its samples into dev_samples[i] (zeroed here).  host_stage: pinned host memory
+// of render_hetero_stage_bytes() used to upload the job table without waiting.
+vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream_t st, void *scratch,
+                         size_t scratch_bytes, unsigned long long *dev_samples, void *host_stage)
+{
+    if (hj.empty()) return VRC_OK;
+    const int mode = hj[0].mode, sampling = hj[0].rc.sampling, dt = hj[0].cube->g.dtype;
+    Arena ar{(char *)scratch, 0, scratch_bytes};
+    int *counter = ar.take<int>(1);
+    float4 *dtf = ar.take<float4>(256 * hj.size());
+    JobDesc *djobs = ar.take<JobDesc>(hj.size());
+    float *htf = (float *)host_stage;
+    JobDesc *hjobs = (JobDesc *)((char *)host_stage + 4096 * hj.size());
+    int64_t total = 0;
+    for (size_t i = 0; i < hj.size(); ++i) {
+        const HetJob &h = hj[i];
+        int tw, th;
+        pick_tile(h.cube, h.rc, tw, th);
+        hjobs[i] = make_job(h.cube, h.cam, h.rc, mode, h.term, mode ? dtf + 256 * i : nullptr, h.out, 0, tw, th);
+        hjobs[i].samples = dev_samples + i;
+        hjobs[i].item_begin = total;
+        total += (int64_t)hjobs[i].tiles_x * hjobs[i].tiles_y;
+        if (mode) std::memcpy(htf + 1024 * i, h.tf_host, 4096);
+    }
+    VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
+    VRC_CK(ctx, cudaMemsetAsync(dev_samples, 0, sizeof(unsigned long long) * hj.size(), st));
+    if (mode) VRC_CK(ctx, cudaMemcpyAsync(dtf, htf, 4096 * hj.size(), cudaMemcpyHostToDevice, st));
+    VRC_CK(ctx, cudaMemcpyAsync(djobs, hjobs, sizeof(JobDesc) * hj.size(), cudaMemcpyHostToDevice, st));
+    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt), total);
+    pick_fused(mode, sampling, dt)(grid, st, djobs, (int)hj.size(), total, counter);
+    count_launch(ctx);
+    VRC_CK(ctx, cudaGetLastError());
+    return VRC_OK;
+}
+
+vrc_status validate_raycfg(vrc_ctx *ctx, const vrc_raycfg *rc) { return check_rc(ctx, rc); }
+bool camera_is_valid(const vrc_camera &c) { return valid_cam(c); }

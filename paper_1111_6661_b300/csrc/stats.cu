@@ -1,0 +1,540 @@
+// Fused global statistics over resident bricks (min/max, mean, std, histogram)
+// and exact median by two-level radix selection.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <float.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "vrc_internal.h"
+
+namespace {
+
+constexpr int kStatsThreads = 256;
+constexpr int kSmemBinsMax = 16384;   // 64 KB of shared-memory counters
+
+struct StatPartial {
+    double s1, s2;                 // sum of d and d^2, d = x - shift
+    unsigned long long n, nnf;
+};
+
+struct StatsArgs {
+    const uint8_t *pool;
+    BrickGeom g;
+    const float *scales;
+    const int32_t *bnonfinite;     // per brick: non-finite interior voxels
+    float vmin, hscale;            // histogram: bin = trunc(fl(fl(x - vmin) * hscale))
+    float shift;                   // c: moments use d = (x - c) * dscale (c has 8 significant bits)
+    float dscale;                  // power of two keeping d^2 finite in binary32
+    float kq;                      // power of two >= max d^2: seed of the Fast2Sum accumulator
+    int nbins;
+    unsigned long long *hist;      // device [nbins], zeroed by the caller
+    StatPartial *partials;         // device [gridDim.x]
+};
+
+// Error-free transformation (Knuth TwoSum): hi + lo tracks the exact running sum.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    const float t = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    hi = t;
+    lo = __fadd_rn(lo, err);
+}
+
+template <int DT>
+__device__ __forceinline__ void decode16(const uint4 &raw, float scale, float *x)
+{
+    if (DT == VRC_F32) {
+        x[0] = __uint_as_float(raw.x);
+        x[1] = __uint_as_float(raw.y);
+        x[2] = __uint_as_float(raw.z);
+        x[3] = __uint_as_float(raw.w);
+    } else if (DT == VRC_BF16) {
+        const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = __uint_as_float(w[i] << 16);
+            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    } else {
+        const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xffffu), __NV_E4M3);
+            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+            x[4 * i + 0] = __fmul_rn(a.x, scale);
+            x[4 * i + 1] = __fmul_rn(a.y, scale);
+            x[4 * i + 2] = __fmul_rn(b.x, scale);
+            x[4 * i + 3] = __fmul_rn(b.y, scale);
+        }
+    }
+}
+
+constexpr int kVecPerLane = 4;                 // 16-byte vectors in flight per lane
+constexpr int kLogChunk = 7;                   // 128 vectors per warp iteration
+
+struct Acc {
+    float2 s_hi, s_lo;                         // TwoSum accumulation of d (two lanes of f32x2)
+    float2 q_hi, q_lo;                         // Fast2Sum accumulation of d^2
+    uint32_t n = 0, nnf = 0;
+};
+
+// One 16-byte vector of VE values.  CHECK: mask element e by `nvalid` and
+// finiteness; otherwise every element is a finite voxel inside the cube.
+// Every accumulation is error-free per element: d by TwoSum, d^2 = P - En by
+// TwoProd and a Fast2Sum into q_hi (seeded with kq >= every P), so repeated
+// values (quantised cubes) cannot bias the sums.
+template <int VE, int HIST, bool CHECK>
+__device__ __forceinline__ void accumulate(const float *x, int nvalid, const StatsArgs &a, uint32_t *sh, Acc &acc)
+{
+    const float2 s2 = make_float2(a.dscale, a.dscale), ns2 = make_float2(-a.dscale, -a.dscale);
+    const float cs = __fmul_rn(a.shift, a.dscale);
+    const float2 cs2 = make_float2(cs, cs), ncs2 = make_float2(-cs, -cs);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 nvmin2 = make_float2(-a.vmin, -a.vmin), hs2 = make_float2(a.hscale, a.hscale);
+#pragma unroll
+    for (int e = 0; e < VE; e += 2) {
+        float2 X = make_float2(x[e], x[e + 1]);
+        bool v0 = true, v1 = true;
+        if (CHECK) {
+            v0 = e < nvalid && fabsf(X.x) <= FLT_MAX;
+            v1 = e + 1 < nvalid && fabsf(X.y) <= FLT_MAX;
+            acc.nnf += (e < nvalid && !v0 ? 1u : 0u) + (e + 1 < nvalid && !v1 ? 1u : 0u);
+            acc.n += (v0 ? 1u : 0u) + (v1 ? 1u : 0u);
+            if (!v0) X.x = a.shift;           // contributes d = 0
+            if (!v1) X.y = a.shift;
+        }
+        // d = fl(x - c) * s, computed as fl((x - c) s): scaling by 2^k commutes with rounding
+        const float2 D = __ffma2_rn(X, s2, ncs2);
+        const float2 Dn = __ffma2_rn(X, ns2, cs2);
+        // TwoSum of d into s_hi + s_lo
+        const float2 T1 = __fadd2_rn(acc.s_hi, D);
+        const float2 BP = __ffma2_rn(acc.s_hi, m1, T1);
+        const float2 AP = __ffma2_rn(BP, m1, T1);
+        const float2 E1 = __ffma2_rn(AP, m1, acc.s_hi);
+        const float2 E2 = __ffma2_rn(BP, m1, D);
+        acc.s_hi = T1;
+        acc.s_lo = __fadd2_rn(acc.s_lo, __fadd2_rn(E1, E2));
+        // exact square d^2 = P - En; Fast2Sum of P into q_hi (q_hi >= kq >= P)
+        const float2 P = __fmul2_rn(D, D);
+        const float2 En = __ffma2_rn(Dn, D, P);
+        const float2 T = __fadd2_rn(acc.q_hi, P);
+        const float2 Z = __ffma2_rn(acc.q_hi, m1, T);
+        const float2 Er = __ffma2_rn(Z, m1, P);
+        acc.q_hi = T;
+        acc.q_lo = __fadd2_rn(acc.q_lo, __ffma2_rn(En, m1, Er));
+        if (HIST) {
+            const float2 Tb = __fmul2_rn(__fadd2_rn(X, nvmin2), hs2);
+            const int nbm1 = a.nbins - 1;
+            const int b0 = min((int)Tb.x, nbm1), b1 = min((int)Tb.y, nbm1);
+            if (!CHECK || v0) {
+                if (HIST == 1) atomicAdd(&sh[b0], 1u);
+                else atomicAdd(&a.hist[b0], 1ull);
+            }
+            if (!CHECK || v1) {
+                if (HIST == 1) atomicAdd(&sh[b1], 1u);
+                else atomicAdd(&a.hist[b1], 1ull);
+            }
+        }
+    }
+    if (!CHECK) acc.n += VE;
+}
+
+// One pass over the interior of every brick.  A warp takes 128 16-byte vectors
+// (whole interior rows of one brick) per iteration, 4 per lane in flight.
+// Moments: d = (x - c) s with c ~ the mean (8 significant bits, so x - c is exact
+// for every voxel not far below |c|; c = 0 for FP8 cubes, whose values repeat);
+// d summed by TwoSum, d^2 exactly (TwoProd) into a Fast2Sum accumulator seeded
+// with a power of two kq >= every square; binary32 pairs (f32x2) throughout;
+// binary64 per block.  Histogram: the stated binary32 bin formula into shared-memory
+// counters (HIST 1) or global counters (HIST 2), flushed once per block.
+template <int DT, int HIST>
+__global__ void __launch_bounds__(kStatsThreads) k_stats(StatsArgs a)
+{
+    extern __shared__ uint32_t sh_hist[];
+    constexpr int VE = DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 8 : 16);
+    constexpr int LOG_VE = DT == VRC_F32 ? 2 : (DT == VRC_BF16 ? 3 : 4);
+    const BrickGeom &g = a.g;
+    if (HIST == 1) {
+        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) sh_hist[i] = 0;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int logVPR = g.logB - LOG_VE;
+    const int logRPC = kLogChunk - logVPR;     // rows per chunk (divides B*B)
+    const int64_t total_chunks = (g.nbricks << (2 * g.logB)) >> logRPC;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    Acc acc;
+    acc.s_hi = make_float2(0.f, 0.f);
+    acc.s_lo = make_float2(0.f, 0.f);
+    acc.q_hi = make_float2(a.kq, a.kq);
+    acc.q_lo = make_float2(0.f, 0.f);
+    for (int64_t ch = warp0; ch < total_chunks; ch += nwarps) {
+        const int64_t r0 = ch << logRPC;
+        const int64_t b = r0 >> (2 * g.logB);
+        const int lr0 = (int)(r0 & (((int64_t)1 << (2 * g.logB)) - 1));
+        const int bxi = (int)(b % g.nb[0]);
+        const int byz = (int)(b / g.nb[0]);
+        const int byi = byz % g.nb[1], bzi = byz / g.nb[1];
+        const int64_t ox = (int64_t)bxi << g.logB, oy = (int64_t)byi << g.logB, oz = (int64_t)bzi << g.logB;
+        const bool full = ox + g.B <= g.dims[0] && oy + g.B <= g.dims[1] && oz + g.B <= g.dims[2];
+        const bool clean = full && __ldg(a.bnonfinite + b) == 0;
+        const uint8_t *bp = a.pool + b * g.brick_bytes;
+        const float scale = DT == VRC_FP8E4M3 ? __ldg(a.scales + b) : 1.f;
+        uint4 raw[kVecPerLane];
+        int lys[kVecPerLane], lzs[kVecPerLane], cols[kVecPerLane];
+#pragma unroll
+        for (int i = 0; i < kVecPerLane; ++i) {
+            const int j = lane + 32 * i;
+            const int lr = lr0 + (j >> logVPR);
+            cols[i] = j & ((1 << logVPR) - 1);
+            lys[i] = lr & (g.B - 1);
+            lzs[i] = lr >> g.logB;
+            const int64_t off =
+                (((int64_t)(lzs[i] + 1) * g.R + (lys[i] + 1)) * g.P + g.O + ((int64_t)cols[i] << LOG_VE)) * g.esize;
+            raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + off));
+        }
+#pragma unroll
+        for (int i = 0; i < kVecPerLane; ++i) {
+            float x[VE];
+            decode16<DT>(raw[i], scale, x);
+            if (clean) {
+                accumulate<VE, HIST, false>(x, VE, a, sh_hist, acc);
+            } else {
+                const int64_t gx0 = ox + ((int64_t)cols[i] << LOG_VE);
+                int nvalid = (int)min((int64_t)VE, g.dims[0] - gx0);
+                if (oy + lys[i] >= g.dims[1] || oz + lzs[i] >= g.dims[2] || nvalid < 0) nvalid = 0;
+                accumulate<VE, HIST, true>(x, nvalid, a, sh_hist, acc);
+            }
+        }
+    }
+    double s1 = ((double)acc.s_hi.x + (double)acc.s_lo.x) + ((double)acc.s_hi.y + (double)acc.s_lo.y);
+    double s2 = ((double)acc.q_hi.x - (double)a.kq) + (double)acc.q_lo.x + ((double)acc.q_hi.y - (double)a.kq) +
+                (double)acc.q_lo.y;
+    unsigned long long n64 = acc.n, nnf64 = acc.nnf;
+    for (int o = 16; o; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+        nnf64 += __shfl_xor_sync(0xffffffffu, nnf64, o);
+    }
+    __shared__ StatPartial wp[kStatsThreads / 32];
+    if ((threadIdx.x & 31) == 0) wp[threadIdx.x / 32] = StatPartial{s1, s2, n64, nnf64};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        StatPartial r = wp[0];
+        for (int w = 1; w < kStatsThreads / 32; ++w) {
+            r.s1 += wp[w].s1;
+            r.s2 += wp[w].s2;
+            r.n += wp[w].n;
+            r.nnf += wp[w].nnf;
+        }
+        a.partials[blockIdx.x] = r;
+    }
+    if (HIST == 1) {
+        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+            const uint32_t cnt = sh_hist[i];
+            if (cnt) atomicAdd(&a.hist[i], (unsigned long long)cnt);
+        }
+    }
+}
+
+// Fixed-order merge of the block partials (deterministic for a given grid).
+__global__ void k_stats_final(const StatPartial *__restrict__ p, int nparts, float vmin, float vmax, float shift,
+                              float dscale, vrc_stats *out)
+{
+    __shared__ double s1[256], s2[256];
+    __shared__ unsigned long long nn[256], nf[256];
+    double a = 0, b = 0;
+    unsigned long long c = 0, d = 0;
+    for (int i = threadIdx.x; i < nparts; i += 256) {
+        a += p[i].s1;
+        b += p[i].s2;
+        c += p[i].n;
+        d += p[i].nnf;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    nn[threadIdx.x] = c;
+    nf[threadIdx.x] = d;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+            nn[threadIdx.x] += nn[threadIdx.x + w];
+            nf[threadIdx.x] += nf[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        vrc_stats r;
+        r.n = nn[0];
+        r.n_nonfinite = nf[0];
+        r.min = vmin;
+        r.max = vmax;
+        if (r.n) {
+            const double inv = 1.0 / (double)dscale;     // exact: power of two
+            const double m1 = s1[0] / (double)r.n;
+            const double var = s2[0] / (double)r.n - m1 * m1;
+            r.mean = (double)shift + m1 * inv;
+            r.std = sqrt(var > 0 ? var : 0.0) * inv;
+        } else {
+            r.mean = r.std = nan("");
+        }
+        *out = r;
+    }
+}
+
+// ----------------------------------------------------------------- median
+
+// Order-preserving map from float bits to uint32 (negative values reversed).
+__device__ __forceinline__ uint32_t ord_key(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+struct SelArgs {
+    const uint8_t *pool;
+    BrickGeom g;
+    const float *scales;
+    uint32_t prefix;       // pass 2: only keys whose high 16 bits equal prefix
+    int pass;              // 1: histogram of high 16 bits; 2: of low 16 bits
+    unsigned int *hist;    // device [65536]
+};
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_select_hist(SelArgs a)
+{
+    constexpr int VE = DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 8 : 16);
+    constexpr int LOG_VE = DT == VRC_F32 ? 2 : (DT == VRC_BF16 ? 3 : 4);
+    const BrickGeom &g = a.g;
+    const int logVPR = g.logB - LOG_VE;
+    const int logVPB = 2 * g.logB + logVPR;
+    const int64_t total = g.nbricks << logVPB;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = v >> logVPB;
+        const int r = (int)(v & ((1ll << logVPB) - 1));
+        const int row = r >> logVPR, c = r & ((1 << logVPR) - 1);
+        const int ly = row & (g.B - 1), lz = row >> g.logB;
+        const int bx = (int)(b % g.nb[0]);
+        const int64_t byz = b / g.nb[0];
+        const int by = (int)(byz % g.nb[1]), bz = (int)(byz / g.nb[1]);
+        const int64_t gx0 = ((int64_t)bx << g.logB) + ((int64_t)c << LOG_VE);
+        if (((int64_t)by << g.logB) + ly >= g.dims[1] || ((int64_t)bz << g.logB) + lz >= g.dims[2] || gx0 >= g.dims[0])
+            continue;
+        const int nvalid = (int)min((int64_t)VE, g.dims[0] - gx0);
+        const int64_t off = (((int64_t)(lz + 1) * g.R + (ly + 1)) * g.P + g.O + ((int64_t)c << LOG_VE)) * g.esize;
+        const uint4 raw = __ldcs(reinterpret_cast<const uint4 *>(a.pool + b * g.brick_bytes + off));
+        float x[VE];
+        decode16<DT>(raw, DT == VRC_FP8E4M3 ? __ldg(a.scales + b) : 1.f, x);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) {
+            if (e >= nvalid || !(fabsf(x[e]) <= FLT_MAX)) continue;
+            const uint32_t k = ord_key(x[e] == 0.f ? 0.f : x[e]);   // -0 and +0 are one value
+            if (a.pass == 1) atomicAdd(&a.hist[k >> 16], 1u);
+            else if ((k >> 16) == a.prefix) atomicAdd(&a.hist[k & 0xffffu], 1u);
+        }
+    }
+}
+
+int stats_grid(vrc_ctx *ctx) { return ctx->sm_count * 4; }
+
+// Persistent grid: as many blocks as fit on the SMs (at most grid_cap).
+template <int DT>
+int launch_stats(const StatsArgs &a, int sm_count, int grid_cap, size_t smem, int hist, cudaStream_t st)
+{
+    int occ = 1;
+    if (hist == 1) {
+        cudaFuncSetAttribute(k_stats<DT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stats<DT, 1>, kStatsThreads, smem);
+    } else if (hist == 2) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stats<DT, 2>, kStatsThreads, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stats<DT, 0>, kStatsThreads, 0);
+    }
+    const int grid = std::max(1, std::min(grid_cap, sm_count * std::max(occ, 1)));
+    if (hist == 1) {
+        cudaFuncSetAttribute(k_stats<DT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_stats<DT, 1><<<grid, kStatsThreads, smem, st>>>(a);
+    } else if (hist == 2) {
+        k_stats<DT, 2><<<grid, kStatsThreads, 0, st>>>(a);
+    } else {
+        k_stats<DT, 0><<<grid, kStatsThreads, 0, st>>>(a);
+    }
+    return grid;
+}
+
+}  // namespace
+
+size_t stats_scratch_bytes(vrc_ctx *ctx) { return sizeof(StatPartial) * (size_t)stats_grid(ctx); }
+
+// Launch the fused statistics pass + final merge on `st`.  dev_hist (nbins
+// counters) is zeroed here; partials is scratch of stats_scratch_bytes().
+vrc_status stats_launch_with(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *dev_out, uint64_t *dev_hist,
+                             void *partials, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    const int grid = stats_grid(ctx);
+    StatsArgs a;
+    a.pool = (const uint8_t *)c->pool;
+    a.g = g;
+    a.scales = c->scales;
+    a.vmin = c->vmin;
+    a.bnonfinite = c->bnonfinite;
+    // c: the upload-time mean rounded to 8 significant bits (x - c is then exact
+    // for every voxel not far below |c|); s: power of two keeping d^2 finite;
+    // kq: power of two bounding every d^2, seed of the Fast2Sum accumulator
+    {
+        int e = 0;
+        const double m = std::frexp((double)c->shift, &e);
+        a.shift = (float)std::ldexp(std::nearbyint(std::ldexp(m, 8)), e - 8);
+        if (!(a.shift >= c->vmin && a.shift <= c->vmax)) a.shift = c->vmin;
+        // FP8 values repeat (256 codes per brick): take c = 0 so that d = x is exact
+        if (g.dtype == VRC_FP8E4M3) a.shift = 0.f;
+        const double maxd = std::fmax(std::fabs((double)c->vmax - a.shift), std::fabs((double)a.shift - c->vmin));
+        int k = 0;
+        while (std::ldexp(maxd, -k) > 0x1p60) ++k;
+        a.dscale = (float)std::ldexp(1.0, -k);
+        const double md = std::ldexp(maxd, -k) * (1.0 + 0x1p-20);
+        double kq = 1.0;
+        while (kq < md * md) kq *= 2.0;
+        a.kq = (float)kq;
+    }
+    // histogram scale in binary32: range = fl(max - min), scale = fl(nbins / range)
+    volatile float range = c->vmax - c->vmin;
+    a.hscale = (nbins > 0 && range > 0.f) ? (float)nbins / (float)range : 0.f;
+    a.nbins = nbins;
+    a.hist = (unsigned long long *)dev_hist;
+    a.partials = (StatPartial *)partials;
+    if (nbins > 0) VRC_CK(ctx, cudaMemsetAsync(dev_hist, 0, sizeof(uint64_t) * nbins, st));
+    const int hist = nbins == 0 ? 0 : (nbins <= kSmemBinsMax ? 1 : 2);
+    const size_t smem = hist == 1 ? sizeof(uint32_t) * nbins : 0;
+    int used = 0;
+    if (g.dtype == VRC_F32) used = launch_stats<VRC_F32>(a, ctx->sm_count, grid, smem, hist, st);
+    else if (g.dtype == VRC_BF16) used = launch_stats<VRC_BF16>(a, ctx->sm_count, grid, smem, hist, st);
+    else used = launch_stats<VRC_FP8E4M3>(a, ctx->sm_count, grid, smem, hist, st);
+    k_stats_final<<<1, 256, 0, st>>>(a.partials, used, c->vmin, c->vmax, a.shift, a.dscale, dev_out);
+    count_launch(ctx, 2);
+    VRC_CK(ctx, cudaGetLastError());
+    return VRC_OK;
+}
+
+static vrc_status check_stats_args(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, Cube **out)
+{
+    if (!ctx) return VRC_E_INVAL;
+    if (nbins < 0 || nbins > 65536) return set_err(ctx, VRC_E_INVAL, "nbins must be in [0, 65536]");
+    Cube *c = find_cube(ctx, cube_id);
+    if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "statistics need a resident cube");
+    *out = c;
+    return VRC_OK;
+}
+
+extern "C" {
+
+vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stats *dev_out,
+                                uint64_t *dev_hist, void *stream)
+{
+    Cube *c = nullptr;
+    vrc_status s = check_stats_args(ctx, cube_id, nbins, &c);
+    if (s != VRC_OK) return s;
+    if (!dev_out || (nbins > 0 && !dev_hist)) return set_err(ctx, VRC_E_INVAL, "null output");
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    void *scr = nullptr;
+    if ((s = scratch_get(ctx, stats_scratch_bytes(ctx), &scr)) != VRC_OK) return s;
+    return stats_launch_with(ctx, c, nbins, dev_out, dev_hist, scr, (cudaStream_t)stream);
+}
+
+vrc_status vrc_cube_stats(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stats *out, uint64_t *hist,
+                          void *stream)
+{
+    Cube *c = nullptr;
+    vrc_status s = check_stats_args(ctx, cube_id, nbins, &c);
+    if (s != VRC_OK) return s;
+    if (!out || (nbins > 0 && !hist)) return set_err(ctx, VRC_E_INVAL, "null output");
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t pbytes = (stats_scratch_bytes(ctx) + 255) & ~(size_t)255;
+    const size_t need = pbytes + 256 + sizeof(uint64_t) * (size_t)nbins;
+    void *scr = nullptr;
+    if ((s = scratch_get(ctx, need, &scr)) != VRC_OK) return s;
+    vrc_stats *dout = (vrc_stats *)((char *)scr + pbytes);
+    uint64_t *dhist = (uint64_t *)((char *)scr + pbytes + 256);
+    if ((s = stats_launch_with(ctx, c, nbins, dout, dhist, scr, st)) != VRC_OK) return s;
+    VRC_CK(ctx, cudaMemcpyAsync(out, dout, sizeof(vrc_stats), cudaMemcpyDeviceToHost, st));
+    if (nbins > 0) VRC_CK(ctx, cudaMemcpyAsync(hist, dhist, sizeof(uint64_t) * nbins, cudaMemcpyDeviceToHost, st));
+    VRC_CK(ctx, cudaStreamSynchronize(st));
+    if (out->n == 0) return set_err(ctx, VRC_E_NONFINITE, "cube has no finite voxel");
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *stream)
+{
+    Cube *c = nullptr;
+    vrc_status s = check_stats_args(ctx, cube_id, 0, &c);
+    if (s != VRC_OK) return s;
+    if (!out) return VRC_E_INVAL;
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scr = nullptr;
+    if ((s = scratch_get(ctx, 65536 * sizeof(unsigned int), &scr)) != VRC_OK) return s;
+    unsigned int *dh = (unsigned int *)scr;
+    std::vector<unsigned int> h(65536);
+    SelArgs a;
+    a.pool = (const uint8_t *)c->pool;
+    a.g = c->g;
+    a.scales = c->scales;
+    a.hist = dh;
+    a.prefix = 0;
+    const int grid = stats_grid(ctx);
+    uint64_t rank = 0, total = 0;
+    uint32_t key = 0;
+    for (int pass = 1; pass <= 2; ++pass) {
+        a.pass = pass;
+        VRC_CK(ctx, cudaMemsetAsync(dh, 0, 65536 * sizeof(unsigned int), st));
+        if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, 256, 0, st>>>(a);
+        else if (c->g.dtype == VRC_BF16) k_select_hist<VRC_BF16><<<grid, 256, 0, st>>>(a);
+        else k_select_hist<VRC_FP8E4M3><<<grid, 256, 0, st>>>(a);
+        count_launch(ctx);
+        VRC_CK(ctx, cudaGetLastError());
+        VRC_CK(ctx, cudaMemcpyAsync(h.data(), dh, 65536 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        VRC_CK(ctx, cudaStreamSynchronize(st));
+        if (pass == 1) {
+            for (int i = 0; i < 65536; ++i) total += h[i];
+            if (total == 0) return set_err(ctx, VRC_E_NONFINITE, "cube has no finite voxel");
+            rank = (total - 1) / 2;
+        }
+        uint64_t acc = 0;
+        int sel = -1;
+        for (int i = 0; i < 65536; ++i) {
+            if (acc + h[i] > rank) {
+                sel = i;
+                break;
+            }
+            acc += h[i];
+        }
+        if (sel < 0) return set_err(ctx, VRC_E_CUDA, "median selection inconsistent");
+        rank -= acc;
+        if (pass == 1) {
+            a.prefix = (uint32_t)sel;
+            key = (uint32_t)sel << 16;
+        } else {
+            key |= (uint32_t)sel;
+        }
+    }
+    const uint32_t u = (key & 0x80000000u) ? (key & 0x7fffffffu) : ~key;
+    float f;
+    memcpy(&f, &u, 4);
+    *out = f;
+    return VRC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Internal declarations of the cube ray-casting / statistics library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/vrc.h"
+
+// ------------------------------------------------------------------ brick store
+//
+// A cube of dims (nx, ny, nz) is stored as nb[0] x nb[1] x nb[2] bricks of edge
+// B (power of two).  Brick (bx, by, bz) has index (bz*nb[1] + by)*nb[0] + bx and
+// stores local voxels l in [-1, B] on each axis (a one-voxel halo; positions
+// outside the cube hold the clamp-to-edge value).  Memory layout of one brick,
+// in elements of the stored type (esize bytes):
+//   slice z (R = B+2 slices), row y (R rows per slice), row pitch P elements;
+//   local voxel (lx, ly, lz) sits at ((lz+1)*R + (ly+1))*P + (lx + O),
+//   O = 16/esize, P = B + 2*O, so every interior row starts 16-byte aligned and
+//   the halo voxels lx = -1 and lx = B sit at O-1 and O+B.
+struct BrickGeom {
+    int64_t dims[3];
+    int32_t B, logB, dtype, esize;
+    int32_t nb[3];
+    int64_t nbricks;
+    int32_t O, P, R;
+    int64_t brick_elems, brick_bytes;
+};
+
+bool make_geom(int64_t nx, int64_t ny, int64_t nz, int32_t B, int32_t dtype, BrickGeom *g);
+
+struct vrc_ctx;
+
+struct Cube {
+    int64_t id = 0;
+    BrickGeom g{};
+    bool streamed = false;
+    void *pool = nullptr;         // device bricks (resident cubes)
+    float *scales = nullptr;      // device [nbricks] (1 unless FP8)
+    float *bmin = nullptr;        // device [nbricks] stored interior min (finite values)
+    float *bmax = nullptr;        // device [nbricks] stored interior max
+    int32_t *bnonfinite = nullptr;// device [nbricks] non-finite interior voxels
+    std::vector<float> h_bmin, h_bmax;
+    std::vector<int32_t> h_bnonfinite;
+    float vmin = 0.f, vmax = 0.f; // stored extrema over finite voxels
+    float shift = 0.f;            // approximate mean (upload pass): centres the statistics sums
+    bool has_finite = false;
+    int64_t charged = 0;          // bytes charged to the budget
+    // out-of-core
+    void *host_pool = nullptr;    // pinned, n_host slots of brick_bytes
+    int64_t n_host = 0;
+    int32_t ring = 0;
+    void *ring_pool = nullptr;    // device, ring slots
+    std::vector<uint8_t> host_filled;
+    // tuning (0 = default)
+    int32_t tile_w = 0, tile_h = 0, ctas_per_sm = 0;
+    std::atomic<int> refs{0};
+};
+
+struct Server;  // serving loop (serve.cu)
+
+struct vrc_ctx {
+    int device = 0;
+    vrc_config cfg{};
+    int sm_count = 148;
+    int64_t budget = 0;
+    std::atomic<int64_t> used{0};
+    std::mutex mu;
+    std::map<int64_t, Cube *> cubes;
+    int64_t next_id = 1;
+    std::string last_error;
+    std::mutex err_mu;            // last_error is written by the serving thread too
+    std::atomic<uint64_t> launches{0};
+    // scratch reused by statistics / rendering (grown on demand)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // host fault injection
+    std::mutex inj_mu;
+    int32_t inj_what = VRC_INJECT_NONE;
+    int64_t inj_left = 0;
+    Server *server = nullptr;
+    std::mutex srv_mu;
+    // sample count of the last render (pinned host word + completion event)
+    unsigned long long *h_samples = nullptr;
+    cudaEvent_t ev_samples = nullptr;
+};
+
+// ------------------------------------------------------------------ helpers
+vrc_status set_err(vrc_ctx *ctx, vrc_status s, const char *fmt, ...);
+vrc_status cuda_err(vrc_ctx *ctx, cudaError_t e, const char *what);
+bool inject_fire(vrc_ctx *ctx, int32_t what);
+vrc_status dev_alloc(vrc_ctx *ctx, void **p, size_t bytes);
+void dev_free(vrc_ctx *ctx, void *p, size_t bytes);
+vrc_status scratch_get(vrc_ctx *ctx, size_t bytes, void **p);
+Cube *find_cube(vrc_ctx *ctx, int64_t id);
+inline void count_launch(vrc_ctx *ctx, uint64_t n = 1) { ctx->launches.fetch_add(n); }
+
+#define VRC_CK(ctx, call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------------------ rendering
+// Per-view ray basis (binary32) as defined in vrc.h.
+struct ViewParams {
+    float O0[3], D0[3], DX[3], DY[3];
+    int32_t kind, W, H;
+    int32_t ec[3];          // eye brick cell for the visibility order
+    int64_t out_offset;     // element offset of the view's image (pixels)
+};
+void camera_basis(const vrc_camera &cam, int W, int H, float basis[12]);
+
+// Statistics launch (stats.cu), used by the serving loop too.
+vrc_status stats_launch(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *dev_out, uint64_t *dev_hist,
+                        cudaStream_t st);
+
+// Heterogeneous persistent render launch (render.cu), used by the serving loop.
+struct HetJob {             // one request inside a heterogeneous launch
+    Cube *cube;
+    vrc_camera cam;
+    vrc_raycfg rc;
+    int32_t mode;           // 0 MIP, 1 DVR
+    float term;
+    const float *tf_host;   // 1024 floats (DVR)
+    float *out;             // device image
+};
+vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &jobs, cudaStream_t st, void *scratch,
+                         size_t scratch_bytes, unsigned long long *dev_samples, void *host_stage);
+size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs);
+size_t render_hetero_stage_bytes(size_t n_jobs);
+
+void server_stop(vrc_ctx *ctx);

@@ -1,0 +1,129 @@
+"""Serving loop: continuous batching of mixed requests over resident cubes of
+different sizes and dtypes.  Every result must be identical alone and in the
+mix (no cross-request state; per-pixel work is deterministic)."""
+import numpy as np
+import pytest
+import torch
+
+import cubegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_1111_6661_b300 as vrc
+    ctx = vrc.Context(0, n_streams=3, max_inflight=8)
+    cubes = {}
+    specs = [((64, 64, 64), "f32", 16), ((56, 40, 48), "bf16", 16), ((96, 96, 96), "f32", 32)]
+    for i, (dims, dt, B) in enumerate(specs):
+        v = cubegen.generate(dims, 3, 100 + i)
+        cubes[i] = (ctx.cube_upload(v, dt, brick=B), dims, v)
+    yield vrc, ctx, cubes
+    ctx.close()
+
+
+def make_requests(vrc, cubes, n=24, seed=3):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        cube = int(rng.integers(0, len(cubes)))
+        cid, dims, _ = cubes[cube]
+        kind = ["mip", "dvr", "stats"][int(rng.integers(0, 3))]
+        W, H = [(40, 30), (64, 64), (48, 24)][int(rng.integers(0, 3))]
+        cam = cubegen.random_cameras(dims, 1, int(rng.integers(0, 1 << 30)))[0]
+        sampling = ["nearest", "trilinear"][int(rng.integers(0, 2))]
+        reqs.append(dict(kind=kind, cid=cid, cam=cam, rc=vrc.raycfg(W, H, 0.5, sampling),
+                         tf=cubegen.tf_random(int(rng.integers(0, 1000))), nbins=int(rng.integers(1, 300))))
+    return reqs
+
+
+def out_for(r):
+    if r["kind"] == "stats":
+        return torch.zeros(r["nbins"], dtype=torch.int64, device="cuda")
+    c = 1 if r["kind"] == "mip" else 4
+    return torch.full((r["rc"].height * r["rc"].width * c,), float("nan"), device="cuda")
+
+
+def submit(ctx, r, out):
+    return ctx.submit(r["kind"], r["cid"], cam=r["cam"], rc=r["rc"], tf=r["tf"], nbins=r["nbins"], out=out)
+
+
+def test_alone_equals_mixed(setup):
+    vrc, ctx, cubes = setup
+    reqs = make_requests(vrc, cubes)
+    alone = []
+    for r in reqs:
+        out = out_for(r)
+        res = ctx.poll(submit(ctx, r, out), -1)
+        assert res["status"] == 0, res
+        alone.append((out.cpu(), res))
+    outs = [out_for(r) for r in reqs]
+    tickets = [submit(ctx, r, o) for r, o in zip(reqs, outs)]
+    results = [ctx.poll(t, -1) for t in tickets]
+    for r, o, res, (ao, ares) in zip(reqs, outs, results, alone):
+        assert res["status"] == 0
+        assert torch.equal(o.cpu(), ao), r["kind"]
+        if r["kind"] == "stats":
+            assert res["stats"] == ares["stats"]
+        else:
+            assert res["samples"] == ares["samples"] and res["samples"] > 0
+        assert res["latency_ms"] >= res["queue_ms"] >= 0
+
+
+def test_serving_matches_direct_api(setup):
+    vrc, ctx, cubes = setup
+    cid, dims, v = cubes[2]
+    cam = cubegen.orbit_cameras(dims, 3)[1]
+    rc = vrc.raycfg(50, 40, 0.5)
+    tf = cubegen.tf_dense()
+    direct = ctx.render_dvr(cid, [cam], rc, tf).cpu().reshape(-1)
+    out = torch.zeros(50 * 40 * 4, device="cuda")
+    res = ctx.poll(ctx.submit("dvr", cid, cam=cam, rc=rc, tf=tf, out=out), -1)
+    assert res["status"] == 0 and torch.equal(out.cpu(), direct)
+    s, h = ctx.cube_stats(cid, 64)
+    hist = torch.zeros(64, dtype=torch.int64, device="cuda")
+    res = ctx.poll(ctx.submit("stats", cid, nbins=64, out=hist), -1)
+    assert res["stats"] == s and np.array_equal(hist.cpu().numpy().astype(np.uint64), h)
+
+
+def test_busy_drop_timeout_and_bad_ticket(setup):
+    vrc, ctx, cubes = setup
+    cid, dims, _ = cubes[0]
+    cam = cubegen.orbit_cameras(dims, 1)[0]
+    out = torch.zeros(256 * 256 * 4, device="cuda")
+    rc = vrc.raycfg(256, 256, 0.25)
+    tickets = [ctx.submit("dvr", cid, cam=cam, rc=rc, tf=cubegen.tf_sparse(), out=out) for _ in range(4)]
+    with pytest.raises(vrc.VrcError, match="BUSY"):
+        ctx.cube_free(cid)                  # referenced by pending requests
+    for t in tickets:
+        assert ctx.poll(t, -1)["status"] == 0
+    with pytest.raises(vrc.VrcError, match="BADID"):
+        ctx.poll(tickets[0], 0)             # retired
+    ctx.debug_inject("drop", 1)
+    t = ctx.submit("stats", cid, nbins=8)
+    assert ctx.poll(t, -1)["status"] == -8   # VRC_E_INJECTED
+    t = ctx.submit("stats", cid, nbins=8)
+    assert ctx.poll(t, -1)["status"] == 0    # the next one runs
+    with pytest.raises(vrc.VrcError, match="INVAL"):
+        ctx.submit("dvr", cid, cam=cam, rc=vrc.raycfg(0, 8, 0.5), tf=cubegen.tf_sparse(), out=out)
+    with pytest.raises(vrc.VrcError, match="BADID"):
+        ctx.submit("stats", 999, nbins=8)
+
+
+def test_poll_timeout_reports_pending():
+    import paper_1111_6661_b300 as vrc
+    ctx = vrc.Context(0, max_inflight=1)
+    v = cubegen.generate((128, 128, 128), 8, 1)
+    cid = ctx.cube_upload(v, "f32", brick=64)
+    cam = cubegen.orbit_cameras((128, 128, 128), 1)[0]
+    out = torch.zeros(1024 * 1024 * 4, device="cuda")
+    rc = vrc.raycfg(1024, 1024, 0.05)        # a few hundred ms of work
+    ts = [ctx.submit("dvr", cid, cam=cam, rc=rc, tf=cubegen.tf_sparse(), term_alpha=2.0, out=out) for _ in range(3)]
+    assert ctx.poll(ts[-1], 0) is None        # still queued behind the others
+    with pytest.raises(vrc.VrcError, match="TIMEOUT"):
+        ctx.poll(ts[-1], 1)
+    for t in ts:
+        assert ctx.poll(t, -1)["status"] == 0
+    ctx.cube_free(cid)
+    ctx.close()
