@@ -334,8 +334,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
     args = ap.parse_args()
     w = workload(args.workload)
+    if args.views:
+        w["views"] = args.views
     if args.impl == "reference":
         run_reference(args, w)
     else:
