@@ -309,6 +309,7 @@ def run_gpu(args, w):
                            "image": [w["W"], w["H"]], "step": w["step"], "sampling": "trilinear",
                            "tf": w["tf"], "term_alpha": w["term"], "hist_bins": w["nbins"],
                            "samples_per_step": samples_per_step, "parallelism": f"replicas{ws}",
+                           "render_copy_bytes": info["render_copy_bytes"],
                            "l2": "inputs larger than L2 (cube bricks %.1f GB > 126 MB)" % (info["bytes"] / 1e9)},
                 "roofline": {"bound": "alu", "kernel": "k_render_fused (DVR)", "achieved": achieved_tflops,
                              "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp32_peak_tflops,
@@ -324,6 +325,206 @@ def run_gpu(args, w):
     ctx.close()
 
 
+# ---------------------------------------------------------------- precision form
+def run_precision(args):
+    """BF16 / FP8 storage against fp32 on the 2048x2048x4096 cube: samples/s
+    per dtype and the error of every image and statistic against the FP64
+    oracle, both on the original fp32 cube and on the stored (dequantised) cube."""
+    import torch
+
+    import cubegen
+    import oracle
+    import paper_1111_6661_b300 as vrc
+    dims = tuple(args.dims) if args.dims else (2048, 2048, 4096)
+    nsrc = int(16000 * (dims[0] * dims[1] * dims[2]) / 2 ** 34) or 8
+    t0 = time.perf_counter()
+    v = cubegen.generate(dims, nsrc, 3)
+    gen_s = time.perf_counter() - t0
+    views = args.views or 16
+    cams = cubegen.orbit_cameras(dims, views)
+    W, H = 1920, 1080
+    tf = cubegen.tf_dense()
+    rng = np.random.default_rng(0)
+    pix = rng.choice(W * H, size=args.error_pixels, replace=False)
+    ref_views = list(range(0, views, max(1, views // 2)))[:2]
+    ctx = vrc.Context(0)
+    st_ref = oracle.stats(v)
+    out = {}
+    for dt in ("f32", "bf16", "fp8"):
+        cid = ctx.cube_upload(v, dt, brick=256)
+        info = ctx.cube_info(cid)
+        s, h = ctx.cube_stats(cid, 4096)
+        row = {"stats": {k: s[k] for k in ("min", "max", "mean", "std")}}
+        row["stats_rel_err_vs_fp32_oracle"] = {k: abs(s[k] - st_ref[k]) / max(abs(st_ref[k]), st_ref["std"])
+                                               for k in ("min", "max", "mean", "std")}
+        if dt != "f32":
+            dq = oracle.dequantize(v, dt, 256)
+            sq = oracle.stats(dq)
+            row["stats_rel_err_vs_stored_oracle"] = {k: abs(s[k] - sq[k]) / max(abs(sq[k]), sq["std"])
+                                                     for k in ("min", "max", "mean", "std")}
+            del dq
+        for mode in ("mip", "dvr"):
+            rc = vrc.raycfg(W, H, 0.5, "trilinear")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            img = ctx.render_mip(cid, cams, rc) if mode == "mip" else ctx.render_dvr(cid, cams, rc, tf, 0.99)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            nsamp = ctx.last_render_samples()
+            errs = {"vs_fp32_oracle": [], "vs_stored_oracle": []}
+            for vi in ref_views:
+                got = img[vi].reshape(-1, 1 if mode == "mip" else 4).cpu().numpy().astype(np.float64)[pix]
+                kw = dict(pixels=pix, tf=tf, vmin=info["vmin"], vmax=info["vmax"])
+                r32 = oracle.render(v, cams[vi], W, H, 0.5, "trilinear", mode, **kw)
+                rs = r32 if dt == "f32" else oracle.render(v, cams[vi], W, H, 0.5, "trilinear", mode, dtype=dt,
+                                                           brick=256, **kw)
+                ref32 = r32["out"].reshape(got.shape)
+                refs = rs["out"].reshape(got.shape)
+                hit = (r32["nsamp"] > 0)
+                errs["vs_fp32_oracle"].append(float(np.abs(got - ref32)[hit].max()) if hit.any() else 0.0)
+                errs["vs_stored_oracle"].append(float(np.abs(got - refs)[hit].max()) if hit.any() else 0.0)
+            row[mode] = {"ms": ms, "samples": nsamp, "samples_per_s": nsamp / (ms / 1e3),
+                         "max_abs_err_vs_fp32_oracle": max(errs["vs_fp32_oracle"]),
+                         "max_abs_err_vs_stored_oracle": max(errs["vs_stored_oracle"])}
+            del img
+        row["stored_bytes"] = info["bytes"]
+        out[dt] = row
+        ctx.cube_free(cid)
+        torch.cuda.empty_cache()
+    ctx.close()
+    line = {"metric": "precision form: samples/s and error vs FP64 oracle per storage type", "workload":
+            f"precision{dims[0]}x{dims[1]}x{dims[2]}", "views": views, "image": [W, H], "step": 0.5,
+            "error_sample": f"{args.error_pixels} random pixels of views {ref_views}; stats over all voxels",
+            "generate_s": gen_s, "results": out}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- out-of-core form
+def run_ooc(args):
+    """4096x4096x3072 fp32 cube in 256^3 bricks (+halo) streamed from pinned
+    host memory; host RAM holds an aliased pool of K distinct bricks."""
+    import torch
+
+    import cubegen
+    import paper_1111_6661_b300 as vrc
+    dims = tuple(args.dims) if args.dims else (4096, 4096, 3072)
+    B = 256
+    nb = [(d + B - 1) // B for d in dims]
+    total = nb[0] * nb[1] * nb[2]
+    K = min(total, args.host_bricks)
+    nsrc = max(8, int(96000 * (dims[0] * dims[1] * dims[2]) / (4096 * 4096 * 3072)))
+    ctx = vrc.Context(0)
+    cid = ctx.cube_create_streamed(dims, B, K, args.ring)
+    t0 = time.perf_counter()
+    for slot in range(K):
+        b = slot
+        bx, by, bz = b % nb[0], (b // nb[0]) % nb[1], b // (nb[0] * nb[1])
+        lo = [bx * B - 1, by * B - 1, bz * B - 1]
+        box = [max(0, lo[a]) for a in range(3)]
+        hi = [min(dims[a], lo[a] + B + 2) for a in range(3)]
+        sub = cubegen.generate(dims, nsrc, 4, box=(box[0], box[1], box[2], hi[0] - box[0], hi[1] - box[1],
+                                                    hi[2] - box[2]))
+        pad = [(box[a] - lo[a], lo[a] + B + 2 - hi[a]) for a in (2, 1, 0)]
+        ctx.cube_put_brick(cid, slot, np.pad(sub, pad, mode="edge"))
+    fill_s = time.perf_counter() - t0
+    # host->device link probe: pinned copies of one brick-sized buffer
+    hb = torch.empty(68 << 20, dtype=torch.uint8, pin_memory=True)
+    db = torch.empty_like(hb, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        db.copy_(hb, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    link_gbs = 20 * hb.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    cams = cubegen.orbit_cameras(dims, 1)
+    rc = vrc.raycfg(1920, 1080, 0.5, "trilinear")
+    tf = cubegen.tf_sparse()
+    out = torch.empty((1, 1080, 1920, 4), device="cuda")
+    ctx.render_dvr(cid, cams, rc, tf, 0.99, out=out)   # warm-up
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0.record()
+        ctx.render_dvr(cid, cams, rc, tf, 0.99, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    nsamp = ctx.last_render_samples()
+    info = ctx.cube_info(cid)
+    brick_bytes = (B + 2 * 4) * (B + 2) * (B + 2) * 4
+    frame_ms = float(np.median(times))
+    streamed = total * brick_bytes
+    line = {"metric": "out-of-core DVR frame time", "value": frame_ms, "unit": "ms", "higher_is_better": False,
+            "workload": f"ooc{dims[0]}x{dims[1]}x{dims[2]}", "bricks": total, "host_slots": K,
+            "ring_bricks": args.ring, "brick_bytes": brick_bytes, "bytes_streamed_per_frame": streamed,
+            "achieved_link_gbs": streamed / (frame_ms / 1e3) / 1e9, "pinned_h2d_probe_gbs": link_gbs,
+            "link_bound_frame_ms": streamed / (link_gbs * 1e9) * 1e3, "samples": nsamp,
+            "samples_per_s": nsamp / (frame_ms / 1e3), "host_fill_s": fill_s, "frames": args.steps,
+            "note": "logical brick b reads pinned host slot b % host_slots when host RAM is short"}
+    ctx.cube_free(cid)
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- serving form
+def run_serving(args):
+    import torch
+
+    import cubegen
+    import paper_1111_6661_b300 as vrc
+    wl = cubegen.serving_stream(seed=5, rate_hz=args.rate, duration_s=args.duration, n_cubes=args.n_cubes)
+    ctx = vrc.Context(0, hbm_budget_bytes=int(args.budget_gib * 2 ** 30), n_streams=4, max_inflight=32)
+    ids = []
+    t0 = time.perf_counter()
+    for c in wl["cubes"]:
+        v = cubegen.generate(c["dims"], c["n_sources"], c["seed"])
+        ids.append(ctx.cube_upload(v, c["dtype"], brick=128 if c["dims"][0] <= 512 else 256))
+    load_s = time.perf_counter() - t0
+    used, budget = ctx.memory()
+    outs = {}
+    for (w, h) in [(512, 512), (1024, 1024), (1920, 1080)]:
+        outs[(w, h)] = [torch.empty(w * h * 4, device="cuda") for _ in range(8)]
+    hists = [torch.empty(4096, dtype=torch.int64, device="cuda") for _ in range(8)]
+    reqs = wl["requests"]
+    tickets = []
+    start = time.perf_counter()
+    for i, r in enumerate(reqs):
+        now = time.perf_counter() - start
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        cid = ids[r["cube"]]
+        dims = wl["cubes"][r["cube"]]["dims"]
+        if r["kind"] == "stats":
+            t = ctx.submit("stats", cid, nbins=4096, out=hists[i % 8])
+        else:
+            cam = cubegen.random_cameras(dims, 1, r["view_seed"])[0]
+            rc = vrc.raycfg(r["width"], r["height"], 0.5, "trilinear")
+            tf = cubegen.tf_random(r["tf_seed"] % 1000)
+            t = ctx.submit(r["kind"], cid, cam=cam, rc=rc, tf=tf, out=outs[(r["width"], r["height"])][i % 8])
+        tickets.append((t, r["kind"]))
+    res = [(ctx.poll(t, -1), k) for t, k in tickets]
+    wall = time.perf_counter() - start
+    lat = np.array([r["latency_ms"] for r, _ in res])
+    samples = sum(r["samples"] for r, _ in res)
+    bykind = {}
+    for kind in ("dvr", "mip", "stats"):
+        l = np.array([r["latency_ms"] for r, k in res if k == kind])
+        if l.size:
+            bykind[kind] = {"n": int(l.size), "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99))}
+    line = {"metric": "serving p50/p99 latency and samples/s", "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "samples_per_s": samples / wall, "requests": len(res),
+            "errors": int(sum(1 for r, _ in res if r["status"] != 0)), "rate_hz": args.rate,
+            "duration_s": args.duration, "wall_s": wall, "by_kind": bykind, "cubes": len(ids),
+            "resident_bytes": used, "budget_bytes": budget, "load_s": load_s,
+            "queue_ms_p99": float(np.percentile([r["queue_ms"] for r, _ in res], 99))}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,7 +536,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
+    ap.add_argument("--dims", type=int, nargs=3, default=None, help="precision/ooc: cube dims")
+    ap.add_argument("--error-pixels", type=int, default=4096)
+    ap.add_argument("--host-bricks", type=int, default=512)
+    ap.add_argument("--ring", type=int, default=8)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--n-cubes", type=int, default=64)
+    ap.add_argument("--budget-gib", type=float, default=160.0)
     args = ap.parse_args()
+    if args.workload == "precision":
+        return run_precision(args)
+    if args.workload == "ooc":
+        return run_ooc(args)
+    if args.workload == "serving":
+        return run_serving(args)
     w = workload(args.workload)
     if args.views:
         w["views"] = args.views

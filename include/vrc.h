@@ -79,15 +79,17 @@ typedef struct {
 
 #define VRC_NEAREST   0
 #define VRC_TRILINEAR 1
-#define VRC_PATH_FUSED    0    /* one thread per ray walks every brick in ray order */
+#define VRC_PATH_FUSED    0    /* one thread per ray walks every brick in ray order;
+                                  trilinear samples through texture gathers */
 #define VRC_PATH_SORTLAST 1    /* per-brick partial images, composited in visibility order */
+#define VRC_PATH_FUSED_LDG 2   /* fused, trilinear samples by 8 global loads (no textures) */
 typedef struct {
     int32_t width, height;     /* image size in pixels (1..16384) */
     float step;                /* sample spacing along the unit ray, voxel units (> 0) */
     int32_t sampling;          /* VRC_NEAREST or VRC_TRILINEAR */
     int32_t opacity_correction;/* DVR: 0 = alpha as in the transfer function,
                                   1 = 1-(1-alpha)^step */
-    int32_t path;              /* VRC_PATH_FUSED or VRC_PATH_SORTLAST (resident cubes) */
+    int32_t path;              /* VRC_PATH_FUSED, VRC_PATH_SORTLAST or VRC_PATH_FUSED_LDG */
     int32_t tile_w, tile_h;    /* ray tile; 0,0 = tuned default.  tile_w*tile_h = 256,
                                   tile_w in {8,16,32} */
 } vrc_raycfg;
@@ -179,10 +181,12 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
 /* Release a cube.  VRC_E_BUSY while serving requests still reference it. */
 vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id);
 
-/* dims, brick edge, storage dtype, brick count, stored bytes and the stored
- * min/max recorded at upload (any output pointer may be NULL). */
+/* dims, brick edge, storage dtype, brick count, stored bytes, the stored
+ * min/max recorded at upload, and the bytes of the texture render copies
+ * (0 when the cube has none, e.g. no room in the budget; any output pointer
+ * may be NULL). */
 vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t *brick, int32_t *storage,
-                         int64_t *n_bricks, int64_t *bytes, float *vmin, float *vmax);
+                         int64_t *n_bricks, int64_t *bytes, float *vmin, float *vmax, int64_t *render_copy_bytes);
 
 /* ------------------------------------------------------------- statistics */
 

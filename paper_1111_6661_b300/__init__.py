@@ -136,11 +136,12 @@ class Context:
     def cube_info(self, cube_id: int) -> dict:
         dims = (ctypes.c_int64 * 3)()
         B, st, nb, by = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
-        mn, mx = ctypes.c_float(), ctypes.c_float()
+        mn, mx, tb = ctypes.c_float(), ctypes.c_float(), ctypes.c_int64()
         self._check(self._lib.vrc_cube_info(self.h, cube_id, dims, ctypes.byref(B), ctypes.byref(st),
-                                            ctypes.byref(nb), ctypes.byref(by), ctypes.byref(mn), ctypes.byref(mx)))
+                                            ctypes.byref(nb), ctypes.byref(by), ctypes.byref(mn), ctypes.byref(mx),
+                                            ctypes.byref(tb)))
         return dict(dims=tuple(dims), brick=B.value, storage={v: k for k, v in DTYPES.items()}[st.value],
-                    n_bricks=nb.value, bytes=by.value, vmin=mn.value, vmax=mx.value)
+                    n_bricks=nb.value, bytes=by.value, vmin=mn.value, vmax=mx.value, render_copy_bytes=tb.value)
 
     # ------------------------------------------------------------ statistics
     def cube_stats(self, cube_id: int, nbins: int = 0, stream=None):

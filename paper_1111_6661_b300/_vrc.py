@@ -16,7 +16,7 @@ STATUS = {0: "VRC_OK", 1: "VRC_PENDING", -1: "VRC_E_INVAL", -2: "VRC_E_NOMEM", -
           -9: "VRC_E_UNSUPPORTED"}
 DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
 SAMPLING = {"nearest": 0, "trilinear": 1}
-PATHS = {"fused": 0, "sortlast": 1}
+PATHS = {"fused": 0, "sortlast": 1, "fused_ldg": 2}
 INJECT = {"none": 0, "alloc": 1, "h2d": 2, "drop": 3}
 
 
@@ -67,7 +67,8 @@ PROTOTYPES = {
     "vrc_cube_put_brick": (c_i32, [c_p, c_i64, c_i64, c_p]),
     "vrc_cube_free": (c_i32, [c_p, c_i64]),
     "vrc_cube_info": (c_i32, [c_p, c_i64, c_p, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_i64),
-                              ctypes.POINTER(c_i64), ctypes.POINTER(c_f32), ctypes.POINTER(c_f32)]),
+                              ctypes.POINTER(c_i64), ctypes.POINTER(c_f32), ctypes.POINTER(c_f32),
+                              ctypes.POINTER(c_i64)]),
     "vrc_cube_stats": (c_i32, [c_p, c_i64, c_i32, ctypes.POINTER(vrc_stats), c_p, c_p]),
     "vrc_cube_stats_async": (c_i32, [c_p, c_i64, c_i32, c_p, c_p, c_p]),
     "vrc_cube_median": (c_i32, [c_p, c_i64, ctypes.POINTER(c_f64), c_p]),

@@ -2,8 +2,11 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <float.h>
+#include <stdio.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "vrc_internal.h"
@@ -197,9 +200,92 @@ vrc_status finish_metadata(vrc_ctx *ctx, Cube *c, cudaStream_t st, const double 
     return VRC_OK;
 }
 
+// Copy one packed brick (interior + halo) into its layered CUDA array through
+// a surface: grid.y = layer, threads over the (B+2)^2 texels of the layer.
+template <typename T>
+__global__ void k_fill_array(const uint8_t *__restrict__ brick, BrickGeom g, cudaSurfaceObject_t surf)
+{
+    const int layer = blockIdx.y;
+    const int R = g.R;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R * R; i += gridDim.x * blockDim.x) {
+        const int y = i / R, x = i % R;
+        const T v = reinterpret_cast<const T *>(brick)[((int64_t)layer * R + y) * g.P + (g.O - 1) + x];
+        surf2DLayeredwrite(v, surf, x * (int)sizeof(T), y, layer);
+    }
+}
+
+void release_textures(vrc_ctx *ctx, Cube *c)
+{
+    for (cudaTextureObject_t t : c->tex_objs) cudaDestroyTextureObject(t);
+    for (cudaArray_t a : c->tex_arrays) cudaFreeArray(a);
+    c->tex_objs.clear();
+    c->tex_arrays.clear();
+    if (c->dtex) dev_free(ctx, c->dtex, c->g.nbricks * 8);
+    c->dtex = nullptr;
+    ctx->used.fetch_sub(c->tex_bytes);
+    c->tex_bytes = 0;
+}
+
+// Copy every packed brick (with its halo) into a (B+2)^2 x (B+2)-layer CUDA
+// array and create a point-sampled texture object on it.  Charged to the budget.
+vrc_status build_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    const int64_t per = g.esize * (int64_t)g.R * g.R * g.R;
+    const int64_t want = per * g.nbricks + (1 << 20);
+    if (ctx->used.load() + want > ctx->budget) return set_err(ctx, VRC_E_NOMEM, "budget: no room for texture copies");
+    ctx->used.fetch_add(want);
+    c->tex_bytes = want;
+    vrc_status s = dev_alloc(ctx, (void **)&c->dtex, g.nbricks * 8);
+    if (s != VRC_OK) return s;
+    cudaChannelFormatDesc desc = g.dtype == VRC_F32 ? cudaCreateChannelDesc<float>()
+                               : (g.dtype == VRC_BF16 ? cudaCreateChannelDesc<unsigned short>()
+                                                      : cudaCreateChannelDesc<unsigned char>());
+    for (int64_t b = 0; b < g.nbricks; ++b) {
+        cudaArray_t arr = nullptr;
+        if (inject_fire(ctx, VRC_INJECT_ALLOC)) return set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
+        VRC_CK(ctx, cudaMalloc3DArray(&arr, &desc, make_cudaExtent(g.R, g.R, g.R),
+                                      cudaArrayLayered | cudaArraySurfaceLoadStore));
+        c->tex_arrays.push_back(arr);
+        {
+            cudaResourceDesc sd = {};
+            sd.resType = cudaResourceTypeArray;
+            sd.res.array.array = arr;
+            cudaSurfaceObject_t surf = 0;
+            VRC_CK(ctx, cudaCreateSurfaceObject(&surf, &sd));
+            const uint8_t *src = (const uint8_t *)c->pool + b * g.brick_bytes;
+            dim3 grid((unsigned)std::min<int64_t>((int64_t)g.R * g.R / 256 + 1, 64), (unsigned)g.R);
+            if (g.dtype == VRC_F32) k_fill_array<float><<<grid, 256, 0, st>>>(src, g, surf);
+            else if (g.dtype == VRC_BF16) k_fill_array<unsigned short><<<grid, 256, 0, st>>>(src, g, surf);
+            else k_fill_array<unsigned char><<<grid, 256, 0, st>>>(src, g, surf);
+            count_launch(ctx);
+            cudaError_t e = cudaGetLastError();
+            VRC_CK(ctx, cudaStreamSynchronize(st));
+            cudaDestroySurfaceObject(surf);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "array fill");
+        }
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        cudaTextureObject_t t = 0;
+        VRC_CK(ctx, cudaCreateTextureObject(&t, &rd, &td, nullptr));
+        c->tex_objs.push_back(t);
+    }
+    std::vector<unsigned long long> h(c->tex_objs.begin(), c->tex_objs.end());
+    VRC_CK(ctx, cudaMemcpyAsync(c->dtex, h.data(), 8 * g.nbricks, cudaMemcpyHostToDevice, st));
+    VRC_CK(ctx, cudaStreamSynchronize(st));
+    return VRC_OK;
+}
+
 void release_cube(vrc_ctx *ctx, Cube *c)
 {
     const BrickGeom &g = c->g;
+    release_textures(ctx, c);
     if (c->pool) dev_free(ctx, c->pool, g.nbricks * g.brick_bytes);
     if (c->ring_pool) dev_free(ctx, c->ring_pool, (size_t)c->ring * g.brick_bytes);
     if (c->scales) dev_free(ctx, c->scales, g.nbricks * 4);
@@ -277,6 +363,15 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
         if (e != cudaSuccess) s = cuda_err(ctx, e, "brick pack launch");
     }
     if (s == VRC_OK) s = finish_metadata(ctx, c, st, dbsum);
+    if (s == VRC_OK && getenv("VRC_NO_TEXTURES") == nullptr) {
+        // texture copies are an accelerator: without room for them the cube still renders
+        if (build_textures(ctx, c, st) != VRC_OK) {
+            cudaStreamSynchronize(st);
+            cudaGetLastError();
+            release_textures(ctx, c);
+            fprintf(stderr, "vrc: no texture render copies for this cube (%s)\n", vrc_last_error(ctx));
+        }
+    }
     if (part) {
         cudaStreamSynchronize(st);
         dev_free(ctx, part, part_bytes);
@@ -405,7 +500,7 @@ vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id)
 }
 
 vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t *brick, int32_t *storage,
-                         int64_t *n_bricks, int64_t *bytes, float *vmin, float *vmax)
+                         int64_t *n_bricks, int64_t *bytes, float *vmin, float *vmax, int64_t *render_copy_bytes)
 {
     if (!ctx) return VRC_E_INVAL;
     Cube *c = find_cube(ctx, cube_id);
@@ -418,6 +513,7 @@ vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t
     if (bytes) *bytes = c->streamed ? (int64_t)c->ring * c->g.brick_bytes : c->g.nbricks * c->g.brick_bytes;
     if (vmin) *vmin = c->vmin;
     if (vmax) *vmax = c->vmax;
+    if (render_copy_bytes) *render_copy_bytes = c->tex_bytes;
     return VRC_OK;
 }
 

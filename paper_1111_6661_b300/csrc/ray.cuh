@@ -9,6 +9,7 @@
 // Cube storage as seen by the kernels.
 struct CubeView {
     const uint8_t *pool;      // brick b at pool + b * brick_bytes (resident)
+    const unsigned long long *tex;  // brick b's layered-array texture (null: none)
     const float *scales;      // FP8 per-brick scale
     int64_t brick_bytes;
     int32_t B, logB, P, O, R;
@@ -166,6 +167,64 @@ __device__ __forceinline__ float sample_resident(const CubeView &cv, float px, f
         return tri_in_brick<DT>(cv, cv.pool + (int64_t)b * cv.brick_bytes, ax, ay, az, bx << cv.logB, by << cv.logB,
                                 bz << cv.logB, scale);
     }
+}
+
+// 2x2 texel footprint of layer `layer` of a 2D layered texture, gathered at the
+// integer coordinate (u, v): with point sampling and unnormalised coordinates
+// the footprint is texels (u-1, v-1) .. (u, v) exactly, returned as
+// x = (u-1, v), y = (u, v), z = (u, v-1), w = (u-1, v-1).
+template <int DT>
+__device__ __forceinline__ float4 gather4(unsigned long long tex, int layer, float u, float v)
+{
+    float4 r;
+    if (DT == VRC_F32) {
+        asm volatile("tld4.r.a2d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+                     : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                     : "l"(tex), "r"(layer), "f"(u), "f"(v));
+    } else {
+        uint32_t a, b, c, d;
+        asm volatile("tld4.r.a2d.v4.u32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+                     : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+                     : "l"(tex), "r"(layer), "f"(u), "f"(v));
+        if (DT == VRC_BF16) {
+            r = make_float4(__uint_as_float(a << 16), __uint_as_float(b << 16), __uint_as_float(c << 16),
+                            __uint_as_float(d << 16));
+        } else {
+            auto f8 = [](uint32_t q) {
+                return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
+            };
+            r = make_float4(f8(a), f8(b), f8(c), f8(d));
+        }
+    }
+    return r;
+}
+
+// Trilinear sample through two texture gathers (layers lz and lz+1 of brick b).
+template <int DT>
+__device__ __forceinline__ float tri_tex(const CubeView &cv, int b, const AxisT &ax, const AxisT &ay, const AxisT &az,
+                                         int ox, int oy, int oz, float scale)
+{
+    const unsigned long long t = __ldg(cv.tex + b);
+    // array index of local voxel l is l + 1; footprint (lx, lx+1) sits at u = lx + 2
+    const float u = (float)(ax.i0 - ox + 2), v = (float)(ay.i0 - oy + 2);
+    const int layer = az.i0 - oz + 1;
+    const float4 g0 = gather4<DT>(t, layer, u, v);
+    const float4 g1 = gather4<DT>(t, layer + 1, u, v);
+    const float c00 = fmaf(ax.f, g0.z - g0.w, g0.w), c10 = fmaf(ax.f, g0.y - g0.x, g0.x);
+    const float c01 = fmaf(ax.f, g1.z - g1.w, g1.w), c11 = fmaf(ax.f, g1.y - g1.x, g1.x);
+    const float c0 = fmaf(ay.f, c10 - c00, c00), c1 = fmaf(ay.f, c11 - c01, c01);
+    const float val = fmaf(az.f, c1 - c0, c0);
+    return DT == VRC_FP8E4M3 ? val * scale : val;
+}
+
+template <int DT>
+__device__ __forceinline__ float sample_resident_tex(const CubeView &cv, float px, float py, float pz)
+{
+    const AxisT ax = axis_tri(px, cv.dims[0]), ay = axis_tri(py, cv.dims[1]), az = axis_tri(pz, cv.dims[2]);
+    const int bx = ax.ip >> cv.logB, by = ay.ip >> cv.logB, bz = az.ip >> cv.logB;
+    const int b = brick_index(cv, bx, by, bz);
+    const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
+    return tri_tex<DT>(cv, b, ax, ay, az, bx << cv.logB, by << cv.logB, bz << cv.logB, scale);
 }
 
 // Transfer function: 256 RGBA entries, linear between entries.

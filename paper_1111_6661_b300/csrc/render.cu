@@ -46,7 +46,7 @@ __device__ __forceinline__ void warp_count(unsigned long long *counter, uint32_t
 // each from the brick that contains it (sort-last compositing of per-brick
 // segments happens in registers).  Persistent: CTAs pull (job, tile) items
 // from an atomic counter.
-template <int MODE, int SAMPLING, int DT>
+template <int MODE, int SAMPLING, int DT, bool TEX>
 __global__ void __launch_bounds__(kThreads) k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs,
                                                            int64_t total_items, int *counter)
 {
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_render_fused(const JobDesc *__rest
         int lx, ly;
         tile_pixel(J.tile_w, lx, ly);
         const int px = tx * J.tile_w + lx, py = ty * J.tile_h + ly;
+        const bool use_tex = TEX && J.cv.tex != nullptr;   // uniform per item
         if (px < J.vp.W && py < J.vp.H) {
             float o[3], d[3], tin, tout;
             const bool hit = ray_setup(J.vp, J.cv.fdims, px, py, o, d, tin, tout);
@@ -85,9 +86,11 @@ __global__ void __launch_bounds__(kThreads) k_render_fused(const JobDesc *__rest
                     for (int k = 0;; ++k) {
                         const float tk = sample_t(tin, k, J.step);
                         if (!(tk < tout)) break;
-                        const float s = sample_resident<SAMPLING, DT>(J.cv, __fadd_rn(o[0], __fmul_rn(tk, d[0])),
-                                                                      __fadd_rn(o[1], __fmul_rn(tk, d[1])),
-                                                                      __fadd_rn(o[2], __fmul_rn(tk, d[2])));
+                        const float p0 = __fadd_rn(o[0], __fmul_rn(tk, d[0]));
+                        const float p1 = __fadd_rn(o[1], __fmul_rn(tk, d[1]));
+                        const float p2 = __fadd_rn(o[2], __fmul_rn(tk, d[2]));
+                        const float s = use_tex ? sample_resident_tex<DT>(J.cv, p0, p1, p2)
+                                                : sample_resident<SAMPLING, DT>(J.cv, p0, p1, p2);
                         m = fmaxf(m, s);
                         ++nsamp;
                     }
@@ -99,9 +102,11 @@ __global__ void __launch_bounds__(kThreads) k_render_fused(const JobDesc *__rest
                     for (int k = 0;; ++k) {
                         const float tk = sample_t(tin, k, J.step);
                         if (!(tk < tout)) break;
-                        const float s = sample_resident<SAMPLING, DT>(J.cv, __fadd_rn(o[0], __fmul_rn(tk, d[0])),
-                                                                      __fadd_rn(o[1], __fmul_rn(tk, d[1])),
-                                                                      __fadd_rn(o[2], __fmul_rn(tk, d[2])));
+                        const float p0 = __fadd_rn(o[0], __fmul_rn(tk, d[0]));
+                        const float p1 = __fadd_rn(o[1], __fmul_rn(tk, d[1]));
+                        const float p2 = __fadd_rn(o[2], __fmul_rn(tk, d[2]));
+                        const float s = use_tex ? sample_resident_tex<DT>(J.cv, p0, p1, p2)
+                                                : sample_resident<SAMPLING, DT>(J.cv, p0, p1, p2);
                         ++nsamp;
                         if (s == s) {
                             const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
@@ -324,6 +329,7 @@ CubeView cube_view(const Cube *c)
     CubeView v;
     const BrickGeom &g = c->g;
     v.pool = (const uint8_t *)c->pool;
+    v.tex = c->dtex;
     v.scales = c->scales;
     v.brick_bytes = g.brick_bytes;
     v.B = g.B;
@@ -392,7 +398,8 @@ vrc_status check_rc(vrc_ctx *ctx, const vrc_raycfg *rc)
         return set_err(ctx, VRC_E_INVAL, "step must be >= 1e-3");
     if (rc->sampling != VRC_NEAREST && rc->sampling != VRC_TRILINEAR) return set_err(ctx, VRC_E_INVAL, "bad sampling");
     if (rc->opacity_correction != 0 && rc->opacity_correction != 1) return set_err(ctx, VRC_E_INVAL, "bad opacity flag");
-    if (rc->path != VRC_PATH_FUSED && rc->path != VRC_PATH_SORTLAST) return set_err(ctx, VRC_E_INVAL, "bad path");
+    if (rc->path != VRC_PATH_FUSED && rc->path != VRC_PATH_SORTLAST && rc->path != VRC_PATH_FUSED_LDG)
+        return set_err(ctx, VRC_E_INVAL, "bad path");
     const bool tile0 = rc->tile_w == 0 && rc->tile_h == 0;
     const bool tile_ok = (rc->tile_w == 8 || rc->tile_w == 16 || rc->tile_w == 32) && rc->tile_w * rc->tile_h == 256;
     if (!tile0 && !tile_ok) return set_err(ctx, VRC_E_INVAL, "tile must be 8x32, 16x16 or 32x8");
@@ -437,52 +444,58 @@ JobDesc make_job(const Cube *c, const vrc_camera &cam, const vrc_raycfg &rc, int
     return j;
 }
 
-template <int MODE, int SAMPLING, int DT>
+template <int MODE, int SAMPLING, int DT, bool TEX>
 int fused_occupancy()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fused<MODE, SAMPLING, DT>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fused<MODE, SAMPLING, DT, TEX>, kThreads, 0);
     return n > 0 ? n : 1;
 }
 
-template <int MODE, int SAMPLING, int DT>
+template <int MODE, int SAMPLING, int DT, bool TEX>
 void launch_fused_t(int grid, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total, int *counter)
 {
-    k_render_fused<MODE, SAMPLING, DT><<<grid, kThreads, 0, st>>>(jobs, n_jobs, total, counter);
+    k_render_fused<MODE, SAMPLING, DT, TEX><<<grid, kThreads, 0, st>>>(jobs, n_jobs, total, counter);
 }
 
 typedef void (*fused_fn)(int, cudaStream_t, const JobDesc *, int, int64_t, int *);
 typedef int (*occ_fn)();
 
-template <int MODE>
-fused_fn pick_fused2(int sampling, int dt)
+// Texture gathers serve trilinear sampling only; nearest reads one voxel.
+template <int MODE, int DT>
+fused_fn pick_fused3(int sampling, bool tex)
 {
-    if (sampling == VRC_NEAREST) {
-        if (dt == VRC_F32) return launch_fused_t<MODE, VRC_NEAREST, VRC_F32>;
-        if (dt == VRC_BF16) return launch_fused_t<MODE, VRC_NEAREST, VRC_BF16>;
-        return launch_fused_t<MODE, VRC_NEAREST, VRC_FP8E4M3>;
-    }
-    if (dt == VRC_F32) return launch_fused_t<MODE, VRC_TRILINEAR, VRC_F32>;
-    if (dt == VRC_BF16) return launch_fused_t<MODE, VRC_TRILINEAR, VRC_BF16>;
-    return launch_fused_t<MODE, VRC_TRILINEAR, VRC_FP8E4M3>;
-}
-fused_fn pick_fused(int mode, int sampling, int dt)
-{
-    return mode == 0 ? pick_fused2<0>(sampling, dt) : pick_fused2<1>(sampling, dt);
+    if (sampling == VRC_NEAREST) return launch_fused_t<MODE, VRC_NEAREST, DT, false>;
+    return tex ? launch_fused_t<MODE, VRC_TRILINEAR, DT, true> : launch_fused_t<MODE, VRC_TRILINEAR, DT, false>;
 }
 template <int MODE>
-occ_fn pick_occ2(int sampling, int dt)
+fused_fn pick_fused2(int sampling, int dt, bool tex)
 {
-    if (sampling == VRC_NEAREST) {
-        if (dt == VRC_F32) return fused_occupancy<MODE, VRC_NEAREST, VRC_F32>;
-        if (dt == VRC_BF16) return fused_occupancy<MODE, VRC_NEAREST, VRC_BF16>;
-        return fused_occupancy<MODE, VRC_NEAREST, VRC_FP8E4M3>;
-    }
-    if (dt == VRC_F32) return fused_occupancy<MODE, VRC_TRILINEAR, VRC_F32>;
-    if (dt == VRC_BF16) return fused_occupancy<MODE, VRC_TRILINEAR, VRC_BF16>;
-    return fused_occupancy<MODE, VRC_TRILINEAR, VRC_FP8E4M3>;
+    if (dt == VRC_F32) return pick_fused3<MODE, VRC_F32>(sampling, tex);
+    if (dt == VRC_BF16) return pick_fused3<MODE, VRC_BF16>(sampling, tex);
+    return pick_fused3<MODE, VRC_FP8E4M3>(sampling, tex);
 }
-int occupancy(int mode, int sampling, int dt) { return mode == 0 ? pick_occ2<0>(sampling, dt)() : pick_occ2<1>(sampling, dt)(); }
+fused_fn pick_fused(int mode, int sampling, int dt, bool tex)
+{
+    return mode == 0 ? pick_fused2<0>(sampling, dt, tex) : pick_fused2<1>(sampling, dt, tex);
+}
+template <int MODE, int DT>
+occ_fn pick_occ3(int sampling, bool tex)
+{
+    if (sampling == VRC_NEAREST) return fused_occupancy<MODE, VRC_NEAREST, DT, false>;
+    return tex ? fused_occupancy<MODE, VRC_TRILINEAR, DT, true> : fused_occupancy<MODE, VRC_TRILINEAR, DT, false>;
+}
+template <int MODE>
+occ_fn pick_occ2(int sampling, int dt, bool tex)
+{
+    if (dt == VRC_F32) return pick_occ3<MODE, VRC_F32>(sampling, tex);
+    if (dt == VRC_BF16) return pick_occ3<MODE, VRC_BF16>(sampling, tex);
+    return pick_occ3<MODE, VRC_FP8E4M3>(sampling, tex);
+}
+int occupancy(int mode, int sampling, int dt, bool tex)
+{
+    return mode == 0 ? pick_occ2<0>(sampling, dt, tex)() : pick_occ2<1>(sampling, dt, tex)();
+}
 
 template <int MODE, int SAMPLING, int DT>
 void launch_bricks_t(int64_t n, cudaStream_t st, const JobDesc *jobs, const BrickItem *items, const uint8_t *slot_base,
@@ -713,6 +726,7 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         total += (int64_t)jobs[v].tiles_x * jobs[v].tiles_y;
     }
     const bool sortlast = c->streamed || rc->path == VRC_PATH_SORTLAST;
+    if (!sortlast && !c->pool) return set_err(ctx, VRC_E_UNSUPPORTED, "cube has no resident bricks");
     SortLastPlan plan;
     if (sortlast) plan_sortlast(c, jobs, camv, plan);
     const size_t img_floats = (size_t)n_views * npix * (mode == 0 ? 1 : 4);
@@ -734,9 +748,11 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     VRC_CK(ctx, cudaMemcpyAsync(djobs, jobs.data(), sizeof(JobDesc) * n_views, cudaMemcpyHostToDevice, st));
     if (!sortlast) {
         VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-        int per_sm = ctas_override > 0 ? ctas_override : (c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype));
+        const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
+        int per_sm = ctas_override > 0 ? ctas_override
+                                       : (c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype, tex));
         const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
-        pick_fused(mode, rc->sampling, c->g.dtype)(grid, st, djobs, n_views, total, counter);
+        pick_fused(mode, rc->sampling, c->g.dtype, tex)(grid, st, djobs, n_views, total, counter);
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
     } else if (!c->streamed) {
@@ -957,8 +973,9 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     Cube *c = nullptr;
     vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c);
     if (s != VRC_OK) return s;
-    if (c->streamed || rc->path != VRC_PATH_FUSED)
+    if (c->streamed || rc->path == VRC_PATH_SORTLAST)
         return set_err(ctx, VRC_E_UNSUPPORTED, "graphs capture the fused path of resident cubes");
+    const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
     VRC_CK(ctx, cudaSetDevice(ctx->device));
     int tw, th;
     pick_tile(c, *rc, tw, th);
@@ -986,7 +1003,7 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
         dev_free(ctx, mem, bytes);
         return cuda_err(ctx, e, "graph upload");
     }
-    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype);
+    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype, tex);
     const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
     cudaStream_t cs;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -998,7 +1015,7 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     if (e == cudaSuccess) {
         cudaMemsetAsync(counter, 0, sizeof(int), cs);
         cudaMemsetAsync(dsamples, 0, sizeof(unsigned long long), cs);
-        pick_fused(mode, rc->sampling, c->g.dtype)(grid, cs, djobs, n_views, total, counter);
+        pick_fused(mode, rc->sampling, c->g.dtype, tex)(grid, cs, djobs, n_views, total, counter);
         e = cudaStreamEndCapture(cs, &gph->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gph->exec, gph->graph, 0);
@@ -1046,7 +1063,7 @@ vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, i
     VRC_CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const int tiles[3][2] = {{8, 32}, {16, 16}, {32, 8}};
-    const int occ = occupancy(mode, rc->sampling, c->g.dtype);
+    const int occ = occupancy(mode, rc->sampling, c->g.dtype, rc->path == VRC_PATH_FUSED && c->dtex != nullptr);
     cudaEvent_t e0, e1;
     VRC_CK(ctx, cudaEventCreate(&e0));
     VRC_CK(ctx, cudaEventCreate(&e1));
@@ -1057,7 +1074,7 @@ vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, i
     for (int t = 0; t < 3; ++t)
         for (int per_sm = 1; per_sm <= occ; ++per_sm) {
             vrc_raycfg r = *rc;
-            r.path = VRC_PATH_FUSED;
+            if (r.path == VRC_PATH_SORTLAST) r.path = VRC_PATH_FUSED;
             r.tile_w = tiles[t][0];
             r.tile_h = tiles[t][1];
             double ms_best = 1e300;
@@ -1144,8 +1161,8 @@ vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream
     VRC_CK(ctx, cudaMemsetAsync(dev_samples, 0, sizeof(unsigned long long) * hj.size(), st));
     if (mode) VRC_CK(ctx, cudaMemcpyAsync(dtf, htf, 4096 * hj.size(), cudaMemcpyHostToDevice, st));
     VRC_CK(ctx, cudaMemcpyAsync(djobs, hjobs, sizeof(JobDesc) * hj.size(), cudaMemcpyHostToDevice, st));
-    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt), total);
-    pick_fused(mode, sampling, dt)(grid, st, djobs, (int)hj.size(), total, counter);
+    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt, true), total);
+    pick_fused(mode, sampling, dt, true)(grid, st, djobs, (int)hj.size(), total, counter);
     count_launch(ctx);
     VRC_CK(ctx, cudaGetLastError());
     return VRC_OK;

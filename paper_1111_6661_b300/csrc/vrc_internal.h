@@ -60,6 +60,12 @@ struct Cube {
     int32_t ring = 0;
     void *ring_pool = nullptr;    // device, ring slots
     std::vector<uint8_t> host_filled;
+    // render copies of the bricks as 2D layered CUDA arrays, read by texture
+    // gathers (2x2 texel footprints) in the fused renderer
+    std::vector<cudaArray_t> tex_arrays;
+    std::vector<cudaTextureObject_t> tex_objs;
+    unsigned long long *dtex = nullptr;   // device [nbricks] texture handles
+    int64_t tex_bytes = 0;
     // tuning (0 = default)
     int32_t tile_w = 0, tile_h = 0, ctas_per_sm = 0;
     std::atomic<int> refs{0};

@@ -335,3 +335,25 @@ def test_budget_and_injected_allocation_failure():
     c.cube_free(cid)
     assert c.memory()[0] == 0 or c.memory()[0] > 0  # scratch may stay allocated
     c.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_texture_gather_equals_global_loads(ctx, dtype, cube128):
+    """The fused renderer reads trilinear footprints with 2x2 texture gathers
+    from per-brick layered arrays; the same lerps on the same stored values
+    must reproduce the 8-global-load variant bit for bit."""
+    vrc = vrcmod()
+    v = cube128[:70, :50, :90].copy()
+    dims = (90, 50, 70)
+    cid = ctx.cube_upload(v, dtype, brick=32)
+    assert ctx.cube_info(cid)["render_copy_bytes"] > 0     # the gather path is really taken
+    cams = cubegen.orbit_cameras(dims, 3) + [cubegen.camera("persp", (40.3, 22.1, 31.7), (0, 0, 0), (0, 1, 0),
+                                                            fovy_deg=70)]
+    tf = cubegen.tf_dense()
+    a = ctx.render_dvr(cid, cams, vrc.raycfg(64, 48, 0.5, path="fused"), tf).cpu()
+    b = ctx.render_dvr(cid, cams, vrc.raycfg(64, 48, 0.5, path="fused_ldg"), tf).cpu()
+    assert torch.equal(a, b)
+    a = ctx.render_mip(cid, cams, vrc.raycfg(64, 48, 0.5, path="fused")).cpu()
+    b = ctx.render_mip(cid, cams, vrc.raycfg(64, 48, 0.5, path="fused_ldg")).cpu()
+    assert torch.equal(a, b)
+    ctx.cube_free(cid)
