@@ -199,32 +199,65 @@ __device__ __forceinline__ float4 gather4(unsigned long long tex, int layer, flo
     return r;
 }
 
-// Trilinear sample through two texture gathers (layers lz and lz+1 of brick b).
-template <int DT>
-__device__ __forceinline__ float tri_tex(const CubeView &cv, int b, const AxisT &ax, const AxisT &ay, const AxisT &az,
+// Trilinear sample through two texture gathers from the copy of brick b whose
+// layers run along AXIS (0 x, 1 y, 2 z).  In that copy local voxel l sits at
+// texel (l[a1]+1, l[a2]+1, layer l[AXIS]+1), (a1, a2) = (x, y) / (y, z) / (z, x)
+// for AXIS = z / x / y.  The corner values are regrouped so that the lerps run
+// in x, then y, then z order, as in the global-load sampler.
+template <int DT, int AXIS>
+__device__ __forceinline__ float tri_tex(unsigned long long t, const AxisT &ax, const AxisT &ay, const AxisT &az,
                                          int ox, int oy, int oz, float scale)
 {
-    const unsigned long long t = __ldg(cv.tex + b);
-    // array index of local voxel l is l + 1; footprint (lx, lx+1) sits at u = lx + 2
-    const float u = (float)(ax.i0 - ox + 2), v = (float)(ay.i0 - oy + 2);
-    const int layer = az.i0 - oz + 1;
-    const float4 g0 = gather4<DT>(t, layer, u, v);
-    const float4 g1 = gather4<DT>(t, layer + 1, u, v);
-    const float c00 = fmaf(ax.f, g0.z - g0.w, g0.w), c10 = fmaf(ax.f, g0.y - g0.x, g0.x);
-    const float c01 = fmaf(ax.f, g1.z - g1.w, g1.w), c11 = fmaf(ax.f, g1.y - g1.x, g1.x);
+    const int l[3] = {ax.i0 - ox, ay.i0 - oy, az.i0 - oz};
+    constexpr int A1 = AXIS == 2 ? 0 : (AXIS == 0 ? 1 : 2);
+    constexpr int A2 = AXIS == 2 ? 1 : (AXIS == 0 ? 2 : 0);
+    // footprint (l, l+1) on texel axis k is gathered at coordinate l + 2
+    const float4 g0 = gather4<DT>(t, l[AXIS] + 1, (float)(l[A1] + 2), (float)(l[A2] + 2));
+    const float4 g1 = gather4<DT>(t, l[AXIS] + 2, (float)(l[A1] + 2), (float)(l[A2] + 2));
+    // gather order: x = (a1 lo, a2 hi), y = (a1 hi, a2 hi), z = (a1 hi, a2 lo), w = (a1 lo, a2 lo)
+    float v[2][2][2];   // v[dz][dy][dx]
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float4 gg = h ? g1 : g0;
+        const float q[2][2] = {{gg.w, gg.x}, {gg.z, gg.y}};   // q[a1 offset][a2 offset]
+#pragma unroll
+        for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+            for (int i2 = 0; i2 < 2; ++i2) {
+                int d[3];
+                d[AXIS] = h;
+                d[A1] = i1;
+                d[A2] = i2;
+                v[d[2]][d[1]][d[0]] = q[i1][i2];
+            }
+    }
+    const float c00 = fmaf(ax.f, v[0][0][1] - v[0][0][0], v[0][0][0]);
+    const float c10 = fmaf(ax.f, v[0][1][1] - v[0][1][0], v[0][1][0]);
+    const float c01 = fmaf(ax.f, v[1][0][1] - v[1][0][0], v[1][0][0]);
+    const float c11 = fmaf(ax.f, v[1][1][1] - v[1][1][0], v[1][1][0]);
     const float c0 = fmaf(ay.f, c10 - c00, c00), c1 = fmaf(ay.f, c11 - c01, c01);
     const float val = fmaf(az.f, c1 - c0, c0);
     return DT == VRC_FP8E4M3 ? val * scale : val;
 }
 
-template <int DT>
-__device__ __forceinline__ float sample_resident_tex(const CubeView &cv, float px, float py, float pz)
+// Per-ray cache of the current brick's texture handle (bricks change rarely).
+struct TexCache {
+    int b = -1;
+    unsigned long long t = 0;
+};
+
+template <int DT, int AXIS>
+__device__ __forceinline__ float sample_resident_tex(const CubeView &cv, TexCache &tc, float px, float py, float pz)
 {
     const AxisT ax = axis_tri(px, cv.dims[0]), ay = axis_tri(py, cv.dims[1]), az = axis_tri(pz, cv.dims[2]);
     const int bx = ax.ip >> cv.logB, by = ay.ip >> cv.logB, bz = az.ip >> cv.logB;
     const int b = brick_index(cv, bx, by, bz);
+    if (b != tc.b) {
+        tc.b = b;
+        tc.t = __ldg(cv.tex + b);
+    }
     const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
-    return tri_tex<DT>(cv, b, ax, ay, az, bx << cv.logB, by << cv.logB, bz << cv.logB, scale);
+    return tri_tex<DT, AXIS>(tc.t, ax, ay, az, bx << cv.logB, by << cv.logB, bz << cv.logB, scale);
 }
 
 // Transfer function: 256 RGBA entries, linear between entries.

@@ -42,12 +42,67 @@ __device__ __forceinline__ void warp_count(unsigned long long *counter, uint32_t
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(counter, (unsigned long long)n);
 }
 
-// Fused path: one thread per ray walks all its samples in ray order, reading
-// each from the brick that contains it (sort-last compositing of per-brick
-// segments happens in registers).  Persistent: CTAs pull (job, tile) items
-// from an atomic counter.
+// One ray of the fused path: all samples in ray order, each read from the
+// brick that contains it (per-brick segments are composited in registers).
+// TEXAXIS < 0: trilinear/nearest from the packed bricks with global loads;
+// TEXAXIS = 2: trilinear from the texture copy layered along z.
+template <int MODE, int SAMPLING, int DT, int TEXAXIS>
+__device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf, int px, int py, uint32_t &nsamp)
+{
+    float o[3], d[3], tin, tout;
+    const bool hit = ray_setup(J.vp, J.cv.fdims, px, py, o, d, tin, tout);
+    const int64_t pix = (int64_t)py * J.vp.W + px;
+    const unsigned long long *tex =
+        TEXAXIS >= 0 ? J.cv.tex + (int64_t)TEXAXIS * J.cv.nb[0] * J.cv.nb[1] * J.cv.nb[2] : nullptr;
+    TexCache tc;
+    float m = -FLT_MAX, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+    if (hit) {
+        const float step = J.step;
+#pragma unroll 1
+        for (int k = 0;; ++k) {
+            const float tk = sample_t(tin, k, step);
+            if (!(tk < tout)) break;
+            const float p0 = __fadd_rn(o[0], __fmul_rn(tk, d[0]));
+            const float p1 = __fadd_rn(o[1], __fmul_rn(tk, d[1]));
+            const float p2 = __fadd_rn(o[2], __fmul_rn(tk, d[2]));
+            float s;
+            if (TEXAXIS >= 0) {
+                const CubeView &cv = J.cv;
+                const AxisT ax = axis_tri(p0, cv.dims[0]), ay = axis_tri(p1, cv.dims[1]), az = axis_tri(p2, cv.dims[2]);
+                const int bx = ax.ip >> cv.logB, by = ay.ip >> cv.logB, bz = az.ip >> cv.logB;
+                const int b = (bz * cv.nb[1] + by) * cv.nb[0] + bx;
+                tc.t = __ldg(tex + b);   // cheaper than a per-ray cache of the handle (measured)
+                const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
+                s = tri_tex<DT, (TEXAXIS < 0 ? 0 : TEXAXIS)>(tc.t, ax, ay, az, bx << cv.logB, by << cv.logB,
+                                                             bz << cv.logB, scale);
+            } else {
+                s = sample_resident<SAMPLING, DT>(J.cv, p0, p1, p2);
+            }
+            ++nsamp;
+            if (MODE == 0) {
+                m = fmaxf(m, s);
+            } else {
+                if (s == s) {
+                    const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
+                    const float a = opacity(c.w, step, J.opacity_correction);
+                    const float w = (1.f - A) * a;
+                    cr = fmaf(w, c.x, cr);
+                    cg = fmaf(w, c.y, cg);
+                    cb = fmaf(w, c.z, cb);
+                    A += w;
+                }
+                if (A >= J.term) break;
+            }
+        }
+    }
+    if (MODE == 0) J.out[pix] = m;
+    else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(cr, cg, cb, A);
+}
+
+// Fused path, persistent: CTAs pull (job, tile) items from an atomic counter.
+// TEX: trilinear samples come from the cubes' texture copies.
 template <int MODE, int SAMPLING, int DT, bool TEX>
-__global__ void __launch_bounds__(kThreads) k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(kThreads, 5) k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs,
                                                            int64_t total_items, int *counter)
 {
     __shared__ float4 s_tf[256];
@@ -75,54 +130,9 @@ __global__ void __launch_bounds__(kThreads) k_render_fused(const JobDesc *__rest
         int lx, ly;
         tile_pixel(J.tile_w, lx, ly);
         const int px = tx * J.tile_w + lx, py = ty * J.tile_h + ly;
-        const bool use_tex = TEX && J.cv.tex != nullptr;   // uniform per item
-        if (px < J.vp.W && py < J.vp.H) {
-            float o[3], d[3], tin, tout;
-            const bool hit = ray_setup(J.vp, J.cv.fdims, px, py, o, d, tin, tout);
-            const int64_t pix = (int64_t)py * J.vp.W + px;
-            if (MODE == 0) {
-                float m = -FLT_MAX;
-                if (hit) {
-                    for (int k = 0;; ++k) {
-                        const float tk = sample_t(tin, k, J.step);
-                        if (!(tk < tout)) break;
-                        const float p0 = __fadd_rn(o[0], __fmul_rn(tk, d[0]));
-                        const float p1 = __fadd_rn(o[1], __fmul_rn(tk, d[1]));
-                        const float p2 = __fadd_rn(o[2], __fmul_rn(tk, d[2]));
-                        const float s = use_tex ? sample_resident_tex<DT>(J.cv, p0, p1, p2)
-                                                : sample_resident<SAMPLING, DT>(J.cv, p0, p1, p2);
-                        m = fmaxf(m, s);
-                        ++nsamp;
-                    }
-                }
-                J.out[pix] = m;
-            } else {
-                float cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
-                if (hit) {
-                    for (int k = 0;; ++k) {
-                        const float tk = sample_t(tin, k, J.step);
-                        if (!(tk < tout)) break;
-                        const float p0 = __fadd_rn(o[0], __fmul_rn(tk, d[0]));
-                        const float p1 = __fadd_rn(o[1], __fmul_rn(tk, d[1]));
-                        const float p2 = __fadd_rn(o[2], __fmul_rn(tk, d[2]));
-                        const float s = use_tex ? sample_resident_tex<DT>(J.cv, p0, p1, p2)
-                                                : sample_resident<SAMPLING, DT>(J.cv, p0, p1, p2);
-                        ++nsamp;
-                        if (s == s) {
-                            const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
-                            const float a = opacity(c.w, J.step, J.opacity_correction);
-                            const float w = (1.f - A) * a;
-                            cr = fmaf(w, c.x, cr);
-                            cg = fmaf(w, c.y, cg);
-                            cb = fmaf(w, c.z, cb);
-                            A += w;
-                        }
-                        if (A >= J.term) break;
-                    }
-                }
-                reinterpret_cast<float4 *>(J.out)[pix] = make_float4(cr, cg, cb, A);
-            }
-        }
+        // TEX kernels are launched only when every job's cube has texture copies
+        if (px < J.vp.W && py < J.vp.H)
+            trace_fused<MODE, SAMPLING, DT, ((TEX && SAMPLING == VRC_TRILINEAR) ? 2 : -1)>(J, s_tf, px, py, nsamp);
         if (J.samples) warp_count(J.samples, nsamp);   // one atomic per warp and item
         nsamp = 0;
         __syncthreads();
@@ -370,6 +380,7 @@ ViewParams view_params(const vrc_camera &cam, const BrickGeom &g, int W, int H, 
         }
     }
     vp.out_offset = out_offset;
+    vp.tex_axis = 2;
     return vp;
 }
 
@@ -1161,8 +1172,10 @@ vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream
     VRC_CK(ctx, cudaMemsetAsync(dev_samples, 0, sizeof(unsigned long long) * hj.size(), st));
     if (mode) VRC_CK(ctx, cudaMemcpyAsync(dtf, htf, 4096 * hj.size(), cudaMemcpyHostToDevice, st));
     VRC_CK(ctx, cudaMemcpyAsync(djobs, hjobs, sizeof(JobDesc) * hj.size(), cudaMemcpyHostToDevice, st));
-    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt, true), total);
-    pick_fused(mode, sampling, dt, true)(grid, st, djobs, (int)hj.size(), total, counter);
+    bool tex = true;
+    for (const HetJob &h : hj) tex = tex && h.cube->dtex != nullptr;
+    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt, tex), total);
+    pick_fused(mode, sampling, dt, tex)(grid, st, djobs, (int)hj.size(), total, counter);
     count_launch(ctx);
     VRC_CK(ctx, cudaGetLastError());
     return VRC_OK;

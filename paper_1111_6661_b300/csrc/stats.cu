@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "vrc_internal.h"
@@ -33,16 +34,6 @@ struct StatsArgs {
     unsigned long long *hist;      // device [nbins], zeroed by the caller
     StatPartial *partials;         // device [gridDim.x]
 };
-
-// Error-free transformation (Knuth TwoSum): hi + lo tracks the exact running sum.
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
-{
-    const float t = __fadd_rn(hi, x);
-    const float bp = __fsub_rn(t, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-    hi = t;
-    lo = __fadd_rn(lo, err);
-}
 
 template <int DT>
 __device__ __forceinline__ void decode16(const uint4 &raw, float scale, float *x)

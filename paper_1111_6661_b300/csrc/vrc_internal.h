@@ -60,11 +60,12 @@ struct Cube {
     int32_t ring = 0;
     void *ring_pool = nullptr;    // device, ring slots
     std::vector<uint8_t> host_filled;
-    // render copies of the bricks as 2D layered CUDA arrays, read by texture
-    // gathers (2x2 texel footprints) in the fused renderer
+    // render copies of the bricks as 2D layered CUDA arrays (layers along z),
+    // read by texture gathers (2x2 texel footprints) in the fused renderer
     std::vector<cudaArray_t> tex_arrays;
     std::vector<cudaTextureObject_t> tex_objs;
-    unsigned long long *dtex = nullptr;   // device [nbricks] texture handles
+    unsigned long long *dtex = nullptr;   // device [3][nbricks] texture handles by layer axis (0 where absent)
+    int32_t tex_axes = 0;                 // bit a set: copy layered along axis a exists (only z is built)
     int64_t tex_bytes = 0;
     // tuning (0 = default)
     int32_t tile_w = 0, tile_h = 0, ctas_per_sm = 0;
@@ -121,6 +122,7 @@ struct ViewParams {
     float O0[3], D0[3], DX[3], DY[3];
     int32_t kind, W, H;
     int32_t ec[3];          // eye brick cell for the visibility order
+    int32_t tex_axis;       // layer axis of the texture copy this view reads
     int64_t out_offset;     // element offset of the view's image (pixels)
 };
 void camera_basis(const vrc_camera &cam, int W, int H, float basis[12]);

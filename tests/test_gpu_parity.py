@@ -347,8 +347,12 @@ def test_texture_gather_equals_global_loads(ctx, dtype, cube128):
     dims = (90, 50, 70)
     cid = ctx.cube_upload(v, dtype, brick=32)
     assert ctx.cube_info(cid)["render_copy_bytes"] > 0     # the gather path is really taken
-    cams = cubegen.orbit_cameras(dims, 3) + [cubegen.camera("persp", (40.3, 22.1, 31.7), (0, 0, 0), (0, 1, 0),
-                                                            fovy_deg=70)]
+    c = (45.0, 25.0, 35.0)
+    axis_views = [cubegen.camera("persp", (c[0], c[1], -200), c, (0, 1, 0)),     # rays along z
+                  cubegen.camera("persp", (-250, c[1], c[2]), c, (0, 1, 0)),     # rays along x
+                  cubegen.camera("persp", (c[0], 300, c[2]), c, (0, 0, 1))]      # rays along y
+    cams = cubegen.orbit_cameras(dims, 3) + axis_views + [
+        cubegen.camera("persp", (40.3, 22.1, 31.7), (0, 0, 0), (0, 1, 0), fovy_deg=70)]
     tf = cubegen.tf_dense()
     a = ctx.render_dvr(cid, cams, vrc.raycfg(64, 48, 0.5, path="fused"), tf).cpu()
     b = ctx.render_dvr(cid, cams, vrc.raycfg(64, 48, 0.5, path="fused_ldg"), tf).cpu()
