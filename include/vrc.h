@@ -215,6 +215,25 @@ vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vr
                                 uint64_t *dev_hist, void *stream);
 
 /*
+ * Allocation-free form of vrc_cube_stats_async (the paper has no counterpart;
+ * this serves callers that must not allocate device memory at this point: a
+ * latency-bound interactive or serving loop, where cudaMalloc/cudaFree may
+ * stall the whole device, or a plug-in inside an application that keeps the
+ * device memory in its own pool).  Same inputs, outputs and errors as
+ * vrc_cube_stats_async; the pass's block partials go to one static device
+ * array of 64 KiB that the library holds on every device that loads it, so
+ * the call performs no cudaMalloc, cudaFree or other allocation.  Devices whose
+ * statistics pass needs more scratch than that are refused with VRC_E_NOMEM.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or other host threads) race and give wrong results, so serialise
+ * them (e.g. one stream).  Nothing in the array needs clearing between calls.
+ */
+vrc_status vrc_cube_stats_noalloc(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stats *dev_out,
+                                  uint64_t *dev_hist, void *stream);
+
+/*
  * Median of the finite stored values (Sec. 3: a global task needing all data):
  * the lower median, value of rank floor((n-1)/2) in ascending order.  Exact:
  * a 65536-bin histogram on the ordered bit patterns of the values selects the

@@ -71,6 +71,7 @@ PROTOTYPES = {
                               ctypes.POINTER(c_i64)]),
     "vrc_cube_stats": (c_i32, [c_p, c_i64, c_i32, ctypes.POINTER(vrc_stats), c_p, c_p]),
     "vrc_cube_stats_async": (c_i32, [c_p, c_i64, c_i32, c_p, c_p, c_p]),
+    "vrc_cube_stats_noalloc": (c_i32, [c_p, c_i64, c_i32, c_p, c_p, c_p]),
     "vrc_cube_median": (c_i32, [c_p, c_i64, ctypes.POINTER(c_f64), c_p]),
     "vrc_render_mip": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p, c_p]),
     "vrc_render_dvr": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p, c_f32,
