@@ -268,6 +268,26 @@ def run_gpu(args, w):
     stats_bytes = info["dims"][0] * info["dims"][1] * info["dims"][2] * (4 if w["storage"] == "f32" else 2)
     stats_gbs = stats_bytes / (stats_ms / 1e3) / 1e9
 
+    # the same step with empty-space skipping (identical image): frames/s, and
+    # how many of the lattice samples were actually fetched
+    skip = None
+    if not args.no_skip_variant:
+        rc_s = vrc.raycfg(w["W"], w["H"], w["step"], "trilinear", skip_empty=True)
+        ctx.render_dvr(cid, cams, rc_s, tf, w["term"], out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            ctx.render_dvr(cid, cams, rc_s, tf, w["term"], out=out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sk_ms = e0.elapsed_time(e1) / args.steps
+        lat, ev = ctx.last_render_samples(evaluated=True)
+        skip = {"render_ms": sk_ms, "frames_per_s": len(cams) / (sk_ms / 1e3), "lattice_samples": lat,
+                "evaluated_samples": ev, "evaluated_samples_per_s": ev / (sk_ms / 1e3),
+                "note": "skip_empty=1: samples whose 8^3 macro-cell is transparent under the TF are not fetched; "
+                        "the image is bit-identical"}
+
     # end to end through the public API with host buffers: upload from pinned
     # host memory, statistics to host, render, images back to pinned host memory
     e2e = None
@@ -315,6 +335,7 @@ def run_gpu(args, w):
                              "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp32_peak_tflops,
                              "traffic": None, "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz"},
+                "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms,
                             "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
                             "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind},
@@ -430,16 +451,19 @@ def run_ooc(args):
         ctx.cube_put_brick(cid, slot, np.pad(sub, pad, mode="edge"))
     fill_s = time.perf_counter() - t0
     # host->device link probe: pinned copies of one brick-sized buffer
-    hb = torch.empty(68 << 20, dtype=torch.uint8, pin_memory=True)
-    db = torch.empty_like(hb, device="cuda")
+    hb = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    db = torch.empty(hb.shape, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        db.copy_(hb, non_blocking=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(20):
+    for _ in range(8):
         db.copy_(hb, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    link_gbs = 20 * hb.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    link_gbs = 8 * hb.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del db, hb
     cams = cubegen.orbit_cameras(dims, 1)
     rc = vrc.raycfg(1920, 1080, 0.5, "trilinear")
     tf = cubegen.tf_sparse()
@@ -477,6 +501,9 @@ def run_serving(args):
     import cubegen
     import paper_1111_6661_b300 as vrc
     wl = cubegen.serving_stream(seed=5, rate_hz=args.rate, duration_s=args.duration, n_cubes=args.n_cubes)
+    if args.serving_dtype != "mix":
+        for c in wl["cubes"]:
+            c["dtype"] = args.serving_dtype
     ctx = vrc.Context(0, hbm_budget_bytes=int(args.budget_gib * 2 ** 30), n_streams=4, max_inflight=32)
     ids = []
     t0 = time.perf_counter()
@@ -520,7 +547,8 @@ def run_serving(args):
             "errors": int(sum(1 for r, _ in res if r["status"] != 0)), "rate_hz": args.rate,
             "duration_s": args.duration, "wall_s": wall, "by_kind": bykind, "cubes": len(ids),
             "resident_bytes": used, "budget_bytes": budget, "load_s": load_s,
-            "queue_ms_p99": float(np.percentile([r["queue_ms"] for r, _ in res], 99))}
+            "queue_ms_p99": float(np.percentile([r["queue_ms"] for r, _ in res], 99)),
+            "cube_dtype": args.serving_dtype}
     ctx.close()
     print(json.dumps(line), flush=True)
 
@@ -534,6 +562,7 @@ def main():
     ap.add_argument("--workload", default="dvr1024")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-skip-variant", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
     ap.add_argument("--dims", type=int, nargs=3, default=None, help="precision/ooc: cube dims")
@@ -543,7 +572,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=20.0)
     ap.add_argument("--n-cubes", type=int, default=64)
-    ap.add_argument("--budget-gib", type=float, default=160.0)
+    ap.add_argument("--budget-gib", type=float, default=200.0)
+    ap.add_argument("--serving-dtype", default="mix", choices=["mix", "f32", "bf16", "fp8"])
     args = ap.parse_args()
     if args.workload == "precision":
         return run_precision(args)

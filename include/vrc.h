@@ -92,6 +92,12 @@ typedef struct {
     int32_t path;              /* VRC_PATH_FUSED, VRC_PATH_SORTLAST or VRC_PATH_FUSED_LDG */
     int32_t tile_w, tile_h;    /* ray tile; 0,0 = tuned default.  tile_w*tile_h = 256,
                                   tile_w in {8,16,32} */
+    int32_t skip_empty;        /* fused trilinear path: 1 = skip samples that cannot
+                                  change the image (DVR: the transfer function is
+                                  transparent up to the 8^3 macro-cell's maximum;
+                                  MIP: the cell's maximum cannot raise the ray's max).
+                                  The image is identical; 0 = sample everything */
+    int32_t reserved;          /* must be 0 */
 } vrc_raycfg;
 
 /*
@@ -266,11 +272,13 @@ vrc_status vrc_render_dvr(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams,
                           void *stream);
 
 /*
- * Ray samples taken by the most recent vrc_render_mip / vrc_render_dvr call on
- * this context (samples inside the cube that were composited, i.e. before early
- * termination).  Waits for that render to finish.  *out is HOST memory.
+ * Ray samples of the most recent vrc_render_mip / vrc_render_dvr call on this
+ * context: *samples = lattice samples inside the cube up to early termination
+ * (the work the method defines); *evaluated = samples actually fetched and
+ * composited (smaller only with skip_empty; may be NULL).  Waits for that
+ * render to finish.  Outputs are HOST memory.
  */
-vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *out);
+vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *evaluated);
 
 /*
  * Sort-last combination of two image buffers (Sec. 2: gathered partial

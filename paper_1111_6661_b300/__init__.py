@@ -42,9 +42,9 @@ def camera_struct(cam: dict) -> _vrc.vrc_camera:
 
 
 def raycfg(width: int, height: int, step: float, sampling: str = "trilinear", opacity_correction: bool = False,
-           path: str = "fused", tile=(0, 0)) -> _vrc.vrc_raycfg:
+           path: str = "fused", tile=(0, 0), skip_empty: bool = False) -> _vrc.vrc_raycfg:
     return _vrc.vrc_raycfg(int(width), int(height), float(step), SAMPLING[sampling], int(opacity_correction),
-                           PATHS[path], int(tile[0]), int(tile[1]))
+                           PATHS[path], int(tile[0]), int(tile[1]), int(skip_empty), 0)
 
 
 def _stream_ptr(stream):
@@ -188,10 +188,12 @@ class Context:
                                              ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
-    def last_render_samples(self) -> int:
-        n = ctypes.c_uint64()
-        self._check(self._lib.vrc_last_render_samples(self.h, ctypes.byref(n)))
-        return n.value
+    def last_render_samples(self, evaluated: bool = False):
+        """Lattice samples of the last render (and, with evaluated=True, the
+        samples actually fetched as a second value)."""
+        n, e = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._lib.vrc_last_render_samples(self.h, ctypes.byref(n), ctypes.byref(e)))
+        return (n.value, e.value) if evaluated else n.value
 
     def composite(self, front, back, mode: str = "dvr", out=None, stream=None):
         import torch

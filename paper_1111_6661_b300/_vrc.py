@@ -37,7 +37,8 @@ class vrc_camera(ctypes.Structure):
 
 class vrc_raycfg(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("step", c_f32), ("sampling", c_i32),
-                ("opacity_correction", c_i32), ("path", c_i32), ("tile_w", c_i32), ("tile_h", c_i32)]
+                ("opacity_correction", c_i32), ("path", c_i32), ("tile_w", c_i32), ("tile_h", c_i32),
+                ("skip_empty", c_i32), ("reserved", c_i32)]
 
 
 class vrc_tuning(ctypes.Structure):
@@ -76,7 +77,7 @@ PROTOTYPES = {
     "vrc_render_mip": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p, c_p]),
     "vrc_render_dvr": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p, c_f32,
                                c_p, c_p]),
-    "vrc_last_render_samples": (c_i32, [c_p, ctypes.POINTER(c_u64)]),
+    "vrc_last_render_samples": (c_i32, [c_p, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)]),
     "vrc_composite": (c_i32, [c_p, c_p, c_p, c_p, c_i64, c_i32, c_p]),
     "vrc_graph_create": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p,
                                  c_f32, c_p, ctypes.POINTER(c_p)]),

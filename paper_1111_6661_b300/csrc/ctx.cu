@@ -212,14 +212,14 @@ vrc_status vrc_create(vrc_ctx **out, const vrc_config *cfg)
     ctx->cfg = c;
     ctx->budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : (int64_t)(0.9 * (double)freeb);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, c.device);
-    if (cudaHostAlloc(&ctx->h_samples, sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess ||
+    if (cudaHostAlloc(&ctx->h_samples, 2 * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_samples, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->h_samples) cudaFreeHost(ctx->h_samples);
         delete ctx;
         return VRC_E_CUDA;
     }
-    *ctx->h_samples = 0;
+    ctx->h_samples[0] = ctx->h_samples[1] = 0;
     *out = ctx;
     return VRC_OK;
 }
@@ -262,11 +262,12 @@ vrc_status vrc_debug_inject(vrc_ctx *ctx, int32_t what, int64_t nth)
 
 uint64_t vrc_launch_count(vrc_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
 
-vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *out)
+vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *evaluated)
 {
-    if (!ctx || !out) return VRC_E_INVAL;
+    if (!ctx || !samples) return VRC_E_INVAL;
     VRC_CK(ctx, cudaEventSynchronize(ctx->ev_samples));
-    *out = *ctx->h_samples;
+    *samples = ctx->h_samples[0];
+    if (evaluated) *evaluated = ctx->h_samples[1];
     return VRC_OK;
 }
 

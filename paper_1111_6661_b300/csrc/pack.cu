@@ -220,6 +220,66 @@ __global__ void k_fill_array(const uint8_t *__restrict__ brick, BrickGeom g, int
     }
 }
 
+// Maximum stored value over local voxels [8l-1, 8l+8]^3 of each 8^3 macro-cell
+// l of each brick (the brick's own copy, so FP8 halos use the brick's scale).
+// NaN voxels never raise the maximum.  One thread per cell.
+template <int DT>
+__global__ void k_cell_max(const uint8_t *__restrict__ pool, BrickGeom g, const float *__restrict__ scales,
+                           int ncx, int ncy, int ncz, float *__restrict__ cellmax)
+{
+    const int64_t n = (int64_t)ncx * ncy * ncz;
+    const int cpb = g.B >> 3;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int cx = (int)(i % ncx), cy = (int)((i / ncx) % ncy), cz = (int)(i / ((int64_t)ncx * ncy));
+        const int bx = cx / cpb, by = cy / cpb, bz = cz / cpb;
+        const int64_t b = ((int64_t)bz * g.nb[1] + by) * g.nb[0] + bx;
+        const uint8_t *bp = pool + b * g.brick_bytes;
+        const float scale = scales[b];
+        const int lx0 = (cx % cpb) * 8 - 1, ly0 = (cy % cpb) * 8 - 1, lz0 = (cz % cpb) * 8 - 1;
+        float m = -INFINITY;
+        for (int z = 0; z < 10; ++z)
+            for (int y = 0; y < 10; ++y) {
+                const int64_t row = ((int64_t)(lz0 + z + 1) * g.R + (ly0 + y + 1)) * g.P + g.O + lx0;
+                for (int x = 0; x < 10; ++x) {
+                    float v;
+                    if (DT == VRC_F32) {
+                        v = reinterpret_cast<const float *>(bp)[row + x];
+                    } else if (DT == VRC_BF16) {
+                        v = __uint_as_float((uint32_t)reinterpret_cast<const unsigned short *>(bp)[row + x] << 16);
+                    } else {
+                        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)bp[row + x], __NV_E4M3);
+                        v = __fmul_rn(__half2float(__half(h)), scale);
+                    }
+                    m = fmaxf(m, v);
+                }
+            }
+        cellmax[i] = m;
+    }
+}
+
+vrc_status build_cellmax(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    const int cpb = g.B / 8;
+    for (int a = 0; a < 3; ++a) c->ncell[a] = g.nb[a] * cpb;
+    const int64_t n = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
+    vrc_status s = dev_alloc(ctx, (void **)&c->cellmax, n * 4);
+    if (s != VRC_OK) return s;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 16);
+    if (g.dtype == VRC_F32)
+        k_cell_max<VRC_F32><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0], c->ncell[1],
+                                                  c->ncell[2], c->cellmax);
+    else if (g.dtype == VRC_BF16)
+        k_cell_max<VRC_BF16><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0], c->ncell[1],
+                                                   c->ncell[2], c->cellmax);
+    else
+        k_cell_max<VRC_FP8E4M3><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0],
+                                                      c->ncell[1], c->ncell[2], c->cellmax);
+    count_launch(ctx);
+    VRC_CK(ctx, cudaGetLastError());
+    return VRC_OK;
+}
+
 void release_textures(vrc_ctx *ctx, Cube *c)
 {
     for (cudaTextureObject_t t : c->tex_objs) cudaDestroyTextureObject(t);
@@ -305,6 +365,7 @@ void release_cube(vrc_ctx *ctx, Cube *c)
     if (c->pool) dev_free(ctx, c->pool, g.nbricks * g.brick_bytes);
     if (c->ring_pool) dev_free(ctx, c->ring_pool, (size_t)c->ring * g.brick_bytes);
     if (c->scales) dev_free(ctx, c->scales, g.nbricks * 4);
+    if (c->cellmax) dev_free(ctx, c->cellmax, (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2] * 4);
     if (c->bmin) dev_free(ctx, c->bmin, g.nbricks * 4);
     if (c->bmax) dev_free(ctx, c->bmax, g.nbricks * 4);
     if (c->bnonfinite) dev_free(ctx, c->bnonfinite, g.nbricks * 4);
@@ -379,6 +440,7 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
         if (e != cudaSuccess) s = cuda_err(ctx, e, "brick pack launch");
     }
     if (s == VRC_OK) s = finish_metadata(ctx, c, st, dbsum);
+    if (s == VRC_OK) s = build_cellmax(ctx, c, st);
     if (s == VRC_OK && getenv("VRC_NO_TEXTURES") == nullptr) {
         // texture copies are an accelerator: without room for them the cube still renders
         if (build_textures(ctx, c, st) != VRC_OK) {

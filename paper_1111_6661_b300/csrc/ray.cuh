@@ -26,10 +26,14 @@ struct JobDesc {
     float step, term, vmin, inv_range;   // TF index u = (s - vmin) * inv_range
     int32_t opacity_correction;
     int32_t tile_w, tile_h, tiles_x, tiles_y;
+    int32_t warp_w;                      // a warp covers warp_w x (32 / warp_w) pixels
     int64_t item_begin;                  // first work item of this job
     const float4 *tf;                    // device [256] (DVR)
     float *out;                          // image of this job (view)
-    unsigned long long *samples;         // sample counter of this job (may be shared or null)
+    unsigned long long *samples;         // [lattice, evaluated] sample counters of this job (may be shared or null)
+    const float *cellmax;                // empty-space skipping: macro-cell maxima (null: no skipping)
+    int32_t ncx, ncy;                    // macro-cells per row / per slice
+    float skip_below;                    // DVR: samples whose cell max <= this are transparent
 };
 
 // Binary32 ray of pixel (px, py), exactly as stated in vrc.h (every operation

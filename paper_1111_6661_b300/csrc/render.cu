@@ -16,13 +16,14 @@ constexpr int kThreads = 256;
 
 // ------------------------------------------------------------------ kernels
 
-// Thread -> pixel inside a tile_w x tile_h tile: warps cover 8 x 4 pixel blocks.
-__device__ __forceinline__ void tile_pixel(int tile_w, int &lx, int &ly)
+// Thread -> pixel inside a tile_w x tile_h tile: warps cover ww x (32/ww)
+// pixel blocks (ww a power of two dividing tile_w).
+__device__ __forceinline__ void tile_pixel(int tile_w, int ww, int &lx, int &ly)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wx = tile_w >> 3;
-    lx = (warp % wx) * 8 + (lane & 7);
-    ly = (warp / wx) * 4 + (lane >> 3);
+    const int wx = tile_w / ww, wh = 32 / ww;
+    lx = (warp % wx) * ww + (lane % ww);
+    ly = (warp / wx) * wh + (lane / ww);
 }
 
 __device__ __forceinline__ int find_job(const JobDesc *jobs, int n_jobs, int64_t item)
@@ -36,25 +37,31 @@ __device__ __forceinline__ int find_job(const JobDesc *jobs, int n_jobs, int64_t
     return lo;
 }
 
-__device__ __forceinline__ void warp_count(unsigned long long *counter, uint32_t n)
+__device__ __forceinline__ void warp_count2(unsigned long long *counters, uint32_t lattice, uint32_t evaluated)
 {
-    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if ((threadIdx.x & 31) == 0 && n) atomicAdd(counter, (unsigned long long)n);
+    for (int o = 16; o; o >>= 1) {
+        lattice += __shfl_xor_sync(0xffffffffu, lattice, o);
+        evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lattice) atomicAdd(counters, (unsigned long long)lattice);
+        if (evaluated) atomicAdd(counters + 1, (unsigned long long)evaluated);
+    }
 }
 
 // One ray of the fused path: all samples in ray order, each read from the
 // brick that contains it (per-brick segments are composited in registers).
 // TEXAXIS < 0: trilinear/nearest from the packed bricks with global loads;
 // TEXAXIS = 2: trilinear from the texture copy layered along z.
-template <int MODE, int SAMPLING, int DT, int TEXAXIS>
-__device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf, int px, int py, uint32_t &nsamp)
+template <int MODE, int SAMPLING, int DT, int TEXAXIS, bool SKIP>
+__device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf, int px, int py, uint32_t &nsamp,
+                                            uint32_t &neval)
 {
     float o[3], d[3], tin, tout;
     const bool hit = ray_setup(J.vp, J.cv.fdims, px, py, o, d, tin, tout);
     const int64_t pix = (int64_t)py * J.vp.W + px;
     const unsigned long long *tex =
         TEXAXIS >= 0 ? J.cv.tex + (int64_t)TEXAXIS * J.cv.nb[0] * J.cv.nb[1] * J.cv.nb[2] : nullptr;
-    TexCache tc;
     float m = -FLT_MAX, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
     if (hit) {
         const float step = J.step;
@@ -69,16 +76,58 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
             if (TEXAXIS >= 0) {
                 const CubeView &cv = J.cv;
                 const AxisT ax = axis_tri(p0, cv.dims[0]), ay = axis_tri(p1, cv.dims[1]), az = axis_tri(p2, cv.dims[2]);
+                if (SKIP) {
+                    // empty-space skipping: every sample whose voxel floor(p) lies in an
+                    // 8^3 macro-cell that cannot change the result is counted, not fetched
+                    const int cx = ax.ip >> 3, cy = ay.ip >> 3, cz = az.ip >> 3;
+                    const float cm = __ldg(J.cellmax + ((int64_t)cz * J.ncy + cy) * J.ncx + cx);
+                    if (MODE == 0 ? cm <= m : cm <= J.skip_below) {
+                        // last sample still inside the cell: slab estimate, then corrected
+                        // with the exact binary32 positions (positions are monotone along
+                        // the ray and the cell is convex, so every sample in between is in)
+                        const float lo[3] = {(float)(cx << 3), (float)(cy << 3), (float)(cz << 3)};
+                        float te = tout;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (d[a] != 0.f) {
+                                const float bnd = d[a] > 0.f ? lo[a] + 8.f : lo[a];
+                                te = fminf(te, (bnd - o[a]) / d[a]);
+                            }
+                        }
+                        int kl = max(k, (int)((te - tin) / step - 0.5f));
+                        bool verified = false;
+                        for (int it = 0; it < 6 && kl > k; ++it) {
+                            const float t2 = sample_t(tin, kl, step);
+                            bool in = t2 < tout;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                const float pa = __fadd_rn(o[a], __fmul_rn(t2, d[a]));
+                                const int ia = min(max((int)floorf(pa), 0), cv.dims[a] - 1) >> 3;
+                                in = in && ia == (a == 0 ? cx : (a == 1 ? cy : cz));
+                            }
+                            if (in) {
+                                verified = true;
+                                break;
+                            }
+                            kl = k + (kl - k) / 2;   // overshoot: back off towards k
+                        }
+                        if (!verified) kl = k;       // sample k itself is known to be in the cell
+                        nsamp += kl - k + 1;
+                        k = kl;
+                        continue;
+                    }
+                }
                 const int bx = ax.ip >> cv.logB, by = ay.ip >> cv.logB, bz = az.ip >> cv.logB;
                 const int b = (bz * cv.nb[1] + by) * cv.nb[0] + bx;
-                tc.t = __ldg(tex + b);   // cheaper than a per-ray cache of the handle (measured)
+                const unsigned long long th = __ldg(tex + b);
                 const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
-                s = tri_tex<DT, (TEXAXIS < 0 ? 0 : TEXAXIS)>(tc.t, ax, ay, az, bx << cv.logB, by << cv.logB,
+                s = tri_tex<DT, (TEXAXIS < 0 ? 0 : TEXAXIS)>(th, ax, ay, az, bx << cv.logB, by << cv.logB,
                                                              bz << cv.logB, scale);
             } else {
                 s = sample_resident<SAMPLING, DT>(J.cv, p0, p1, p2);
             }
             ++nsamp;
+            ++neval;
             if (MODE == 0) {
                 m = fmaxf(m, s);
             } else {
@@ -101,7 +150,7 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
 
 // Fused path, persistent: CTAs pull (job, tile) items from an atomic counter.
 // TEX: trilinear samples come from the cubes' texture copies.
-template <int MODE, int SAMPLING, int DT, bool TEX>
+template <int MODE, int SAMPLING, int DT, bool TEX, bool SKIP>
 __global__ void __launch_bounds__(kThreads, 5) k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs,
                                                            int64_t total_items, int *counter)
 {
@@ -109,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_render_fused(const JobDesc *__r
     __shared__ int64_t s_item;
     __shared__ int s_job;
     int loaded = -1;
-    uint32_t nsamp = 0;
+    uint32_t nsamp = 0, neval = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             s_item = atomicAdd(counter, 1);
@@ -128,13 +177,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_render_fused(const JobDesc *__r
         const int64_t t = item - J.item_begin;
         const int tx = (int)(t % J.tiles_x), ty = (int)(t / J.tiles_x);
         int lx, ly;
-        tile_pixel(J.tile_w, lx, ly);
+        tile_pixel(J.tile_w, J.warp_w, lx, ly);
         const int px = tx * J.tile_w + lx, py = ty * J.tile_h + ly;
         // TEX kernels are launched only when every job's cube has texture copies
         if (px < J.vp.W && py < J.vp.H)
-            trace_fused<MODE, SAMPLING, DT, ((TEX && SAMPLING == VRC_TRILINEAR) ? 2 : -1)>(J, s_tf, px, py, nsamp);
-        if (J.samples) warp_count(J.samples, nsamp);   // one atomic per warp and item
-        nsamp = 0;
+            trace_fused<MODE, SAMPLING, DT, ((TEX && SAMPLING == VRC_TRILINEAR) ? 2 : -1),
+                        (SKIP && TEX && SAMPLING == VRC_TRILINEAR)>(J, s_tf, px, py, nsamp, neval);
+        if (J.samples) warp_count2(J.samples, nsamp, neval);   // one atomic pair per warp and item
+        nsamp = neval = 0;
         __syncthreads();
     }
 }
@@ -198,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__res
     }
     const CubeView &cv = J.cv;
     int lx, ly;
-    tile_pixel(J.tile_w, lx, ly);
+    tile_pixel(J.tile_w, J.warp_w, lx, ly);
     const int px = it.tx + lx, py = it.ty + ly;
     uint32_t nsamp = 0;
     if (px < J.vp.W && py < J.vp.H) {
@@ -286,7 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__res
             }
         }
     }
-    if (samples) warp_count(samples, nsamp);
+    if (samples) warp_count2(samples, nsamp, nsamp);
 }
 
 // Sort-last composite of a partial image into the running image (DVR: over,
@@ -411,6 +461,8 @@ vrc_status check_rc(vrc_ctx *ctx, const vrc_raycfg *rc)
     if (rc->opacity_correction != 0 && rc->opacity_correction != 1) return set_err(ctx, VRC_E_INVAL, "bad opacity flag");
     if (rc->path != VRC_PATH_FUSED && rc->path != VRC_PATH_SORTLAST && rc->path != VRC_PATH_FUSED_LDG)
         return set_err(ctx, VRC_E_INVAL, "bad path");
+    if ((rc->skip_empty != 0 && rc->skip_empty != 1) || rc->reserved != 0)
+        return set_err(ctx, VRC_E_INVAL, "bad skip_empty/reserved");
     const bool tile0 = rc->tile_w == 0 && rc->tile_h == 0;
     const bool tile_ok = (rc->tile_w == 8 || rc->tile_w == 16 || rc->tile_w == 32) && rc->tile_w * rc->tile_h == 256;
     if (!tile0 && !tile_ok) return set_err(ctx, VRC_E_INVAL, "tile must be 8x32, 16x16 or 32x8");
@@ -431,6 +483,40 @@ void pick_tile(const Cube *c, const vrc_raycfg &rc, int &tw, int &th)
     }
 }
 
+// Warp shape for a view.  Texture copies are layered along z, so a warp should
+// spread its 32 pixels along the image axis that moves least in z: tall and
+// narrow when the image's x axis runs along z (rays mostly along x), wide and
+// flat when its y axis does, square-ish otherwise.
+int warp_shape(const ViewParams &vp, int tw, int th)
+{
+    const float rz = std::fabs(vp.DX[2]), uz = std::fabs(vp.DY[2]);
+    const float rn = std::sqrt(vp.DX[0] * vp.DX[0] + vp.DX[1] * vp.DX[1] + vp.DX[2] * vp.DX[2]);
+    const float un = std::sqrt(vp.DY[0] * vp.DY[0] + vp.DY[1] * vp.DY[1] + vp.DY[2] * vp.DY[2]);
+    const float fr = rn > 0 ? rz / rn : 0.f, fu = un > 0 ? uz / un : 0.f;
+    int ww = 8;
+    if (fr > 0.7f && fu < 0.5f) ww = 2;
+    else if (fu > 0.7f && fr < 0.5f) ww = 16;
+    while (ww > 1 && (tw % ww || th % (32 / ww))) ww >>= 1;   // fit the tile
+    while (ww < 32 && (tw % ww || th % (32 / ww))) ww <<= 1;
+    return ww;
+}
+
+// DVR empty-space threshold: with j0 the first TF entry of nonzero alpha, a
+// sample value s gives alpha exactly 0 when 255 (s - min)/(max - min) <= j0 - 1
+// (interpolation between zero entries).  The threshold keeps a 1e-5 relative
+// margin so that binary32 evaluation of the TF index cannot cross j0 - 1.
+float transparent_below(const Cube *c, const float *tf)
+{
+    int j0 = 0;
+    while (j0 < 256 && tf[4 * j0 + 3] == 0.f) ++j0;
+    if (j0 == 0) return -INFINITY;
+    const double range = (double)c->vmax - (double)c->vmin;
+    if (!(range > 0)) return j0 >= 1 ? INFINITY : -INFINITY;   // every sample has u = 0
+    if (j0 >= 256) return INFINITY;                            // the TF is transparent everywhere
+    const double thr = (double)c->vmin + (double)(j0 - 1) / 255.0 * range * (1.0 - 1e-5) - 1e-6 * std::fabs(c->vmin);
+    return (float)thr;
+}
+
 JobDesc make_job(const Cube *c, const vrc_camera &cam, const vrc_raycfg &rc, int mode, float term, const float4 *dtf,
                  float *out, int64_t out_offset, int tw, int th)
 {
@@ -445,67 +531,75 @@ JobDesc make_job(const Cube *c, const vrc_camera &cam, const vrc_raycfg &rc, int
     j.opacity_correction = rc.opacity_correction;
     j.tile_w = tw;
     j.tile_h = th;
+    j.warp_w = warp_shape(j.vp, tw, th);
     j.tiles_x = (rc.width + tw - 1) / tw;
     j.tiles_y = (rc.height + th - 1) / th;
     j.item_begin = 0;
     j.tf = dtf;
     j.out = out + (mode == 0 ? 1 : 4) * out_offset;
     j.samples = nullptr;
+    j.cellmax = (rc.skip_empty && c->cellmax && c->dtex && rc.sampling == VRC_TRILINEAR) ? c->cellmax : nullptr;
+    j.ncx = c->ncell[0];
+    j.ncy = c->ncell[1];
+    j.skip_below = -INFINITY;
     (void)mode;
     return j;
 }
 
-template <int MODE, int SAMPLING, int DT, bool TEX>
+template <int MODE, int SAMPLING, int DT, bool TEX, bool SKIP>
 int fused_occupancy()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fused<MODE, SAMPLING, DT, TEX>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fused<MODE, SAMPLING, DT, TEX, SKIP>, kThreads, 0);
     return n > 0 ? n : 1;
 }
 
-template <int MODE, int SAMPLING, int DT, bool TEX>
+template <int MODE, int SAMPLING, int DT, bool TEX, bool SKIP>
 void launch_fused_t(int grid, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total, int *counter)
 {
-    k_render_fused<MODE, SAMPLING, DT, TEX><<<grid, kThreads, 0, st>>>(jobs, n_jobs, total, counter);
+    k_render_fused<MODE, SAMPLING, DT, TEX, SKIP><<<grid, kThreads, 0, st>>>(jobs, n_jobs, total, counter);
 }
 
 typedef void (*fused_fn)(int, cudaStream_t, const JobDesc *, int, int64_t, int *);
 typedef int (*occ_fn)();
 
-// Texture gathers serve trilinear sampling only; nearest reads one voxel.
+// Variant: nearest reads one voxel; trilinear reads texture gathers when the
+// cubes have texture copies (TEX), optionally with empty-space skipping (SKIP).
 template <int MODE, int DT>
-fused_fn pick_fused3(int sampling, bool tex)
+fused_fn pick_fused3(int sampling, bool tex, bool skip)
 {
-    if (sampling == VRC_NEAREST) return launch_fused_t<MODE, VRC_NEAREST, DT, false>;
-    return tex ? launch_fused_t<MODE, VRC_TRILINEAR, DT, true> : launch_fused_t<MODE, VRC_TRILINEAR, DT, false>;
+    if (sampling == VRC_NEAREST) return launch_fused_t<MODE, VRC_NEAREST, DT, false, false>;
+    if (!tex) return launch_fused_t<MODE, VRC_TRILINEAR, DT, false, false>;
+    return skip ? launch_fused_t<MODE, VRC_TRILINEAR, DT, true, true> : launch_fused_t<MODE, VRC_TRILINEAR, DT, true, false>;
 }
 template <int MODE>
-fused_fn pick_fused2(int sampling, int dt, bool tex)
+fused_fn pick_fused2(int sampling, int dt, bool tex, bool skip)
 {
-    if (dt == VRC_F32) return pick_fused3<MODE, VRC_F32>(sampling, tex);
-    if (dt == VRC_BF16) return pick_fused3<MODE, VRC_BF16>(sampling, tex);
-    return pick_fused3<MODE, VRC_FP8E4M3>(sampling, tex);
+    if (dt == VRC_F32) return pick_fused3<MODE, VRC_F32>(sampling, tex, skip);
+    if (dt == VRC_BF16) return pick_fused3<MODE, VRC_BF16>(sampling, tex, skip);
+    return pick_fused3<MODE, VRC_FP8E4M3>(sampling, tex, skip);
 }
-fused_fn pick_fused(int mode, int sampling, int dt, bool tex)
+fused_fn pick_fused(int mode, int sampling, int dt, bool tex, bool skip = false)
 {
-    return mode == 0 ? pick_fused2<0>(sampling, dt, tex) : pick_fused2<1>(sampling, dt, tex);
+    return mode == 0 ? pick_fused2<0>(sampling, dt, tex, skip) : pick_fused2<1>(sampling, dt, tex, skip);
 }
 template <int MODE, int DT>
-occ_fn pick_occ3(int sampling, bool tex)
+occ_fn pick_occ3(int sampling, bool tex, bool skip)
 {
-    if (sampling == VRC_NEAREST) return fused_occupancy<MODE, VRC_NEAREST, DT, false>;
-    return tex ? fused_occupancy<MODE, VRC_TRILINEAR, DT, true> : fused_occupancy<MODE, VRC_TRILINEAR, DT, false>;
+    if (sampling == VRC_NEAREST) return fused_occupancy<MODE, VRC_NEAREST, DT, false, false>;
+    if (!tex) return fused_occupancy<MODE, VRC_TRILINEAR, DT, false, false>;
+    return skip ? fused_occupancy<MODE, VRC_TRILINEAR, DT, true, true> : fused_occupancy<MODE, VRC_TRILINEAR, DT, true, false>;
 }
 template <int MODE>
-occ_fn pick_occ2(int sampling, int dt, bool tex)
+occ_fn pick_occ2(int sampling, int dt, bool tex, bool skip)
 {
-    if (dt == VRC_F32) return pick_occ3<MODE, VRC_F32>(sampling, tex);
-    if (dt == VRC_BF16) return pick_occ3<MODE, VRC_BF16>(sampling, tex);
-    return pick_occ3<MODE, VRC_FP8E4M3>(sampling, tex);
+    if (dt == VRC_F32) return pick_occ3<MODE, VRC_F32>(sampling, tex, skip);
+    if (dt == VRC_BF16) return pick_occ3<MODE, VRC_BF16>(sampling, tex, skip);
+    return pick_occ3<MODE, VRC_FP8E4M3>(sampling, tex, skip);
 }
-int occupancy(int mode, int sampling, int dt, bool tex)
+int occupancy(int mode, int sampling, int dt, bool tex, bool skip = false)
 {
-    return mode == 0 ? pick_occ2<0>(sampling, dt, tex)() : pick_occ2<1>(sampling, dt, tex)();
+    return mode == 0 ? pick_occ2<0>(sampling, dt, tex, skip)() : pick_occ2<1>(sampling, dt, tex, skip)();
 }
 
 template <int MODE, int SAMPLING, int DT>
@@ -747,23 +841,27 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     if ((s = scratch_get(ctx, need, &scr)) != VRC_OK) return s;
     Arena ar{(char *)scr, 0, need};
     int *counter = ar.take<int>(1);
-    unsigned long long *dsamples = ar.take<unsigned long long>(1);
+    unsigned long long *dsamples = ar.take<unsigned long long>(2);
     float4 *dtf = ar.take<float4>(256);
     JobDesc *djobs = ar.take<JobDesc>(n_views);
+    const float thr = mode == 1 ? transparent_below(c, tf_rgba) : -INFINITY;
     for (auto &j : jobs) {
         if (mode == 1) j.tf = dtf;
         j.samples = dsamples;
+        j.skip_below = thr;
     }
-    VRC_CK(ctx, cudaMemsetAsync(dsamples, 0, sizeof(unsigned long long), st));
+    VRC_CK(ctx, cudaMemsetAsync(dsamples, 0, 2 * sizeof(unsigned long long), st));
     if (mode == 1) VRC_CK(ctx, cudaMemcpyAsync(dtf, tf_rgba, 1024 * 4, cudaMemcpyHostToDevice, st));
     VRC_CK(ctx, cudaMemcpyAsync(djobs, jobs.data(), sizeof(JobDesc) * n_views, cudaMemcpyHostToDevice, st));
     if (!sortlast) {
         VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
         const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
+        const bool skip = tex && jobs[0].cellmax != nullptr;
         int per_sm = ctas_override > 0 ? ctas_override
-                                       : (c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype, tex));
+                                       : (c->ctas_per_sm > 0 ? c->ctas_per_sm
+                                                             : occupancy(mode, rc->sampling, c->g.dtype, tex, skip));
         const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
-        pick_fused(mode, rc->sampling, c->g.dtype, tex)(grid, st, djobs, n_views, total, counter);
+        pick_fused(mode, rc->sampling, c->g.dtype, tex, skip)(grid, st, djobs, n_views, total, counter);
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
     } else if (!c->streamed) {
@@ -799,10 +897,10 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         if (s != VRC_OK) return s;
     }
     if (samples_out) {
-        VRC_CK(ctx, cudaMemcpyAsync(samples_out, dsamples, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        VRC_CK(ctx, cudaMemcpyAsync(samples_out, dsamples, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         if (host_sync_samples) VRC_CK(ctx, cudaStreamSynchronize(st));
     } else {
-        VRC_CK(ctx, cudaMemcpyAsync(ctx->h_samples, dsamples, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        VRC_CK(ctx, cudaMemcpyAsync(ctx->h_samples, dsamples, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         VRC_CK(ctx, cudaEventRecord(ctx->ev_samples, st));
     }
     return VRC_OK;
@@ -998,12 +1096,14 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     if ((s = dev_alloc(ctx, &mem, bytes)) != VRC_OK) return s;
     Arena ar{(char *)mem, 0, bytes};
     int *counter = ar.take<int>(1);
-    unsigned long long *dsamples = ar.take<unsigned long long>(1);
+    unsigned long long *dsamples = ar.take<unsigned long long>(2);
     float4 *dtf = ar.take<float4>(256);
     JobDesc *djobs = ar.take<JobDesc>(n_views);
+    const float thr = mode ? transparent_below(c, tf_rgba) : -INFINITY;
     for (int v = 0; v < n_views; ++v) {
         jobs[v] = make_job(c, cams[v], *rc, mode, term_alpha, mode ? dtf : nullptr, out, v * npix, tw, th);
         jobs[v].samples = dsamples;
+        jobs[v].skip_below = thr;
         jobs[v].item_begin = total;
         total += (int64_t)jobs[v].tiles_x * jobs[v].tiles_y;
     }
@@ -1014,7 +1114,8 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
         dev_free(ctx, mem, bytes);
         return cuda_err(ctx, e, "graph upload");
     }
-    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype, tex);
+    const bool skip = tex && jobs[0].cellmax != nullptr;
+    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype, tex, skip);
     const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
     cudaStream_t cs;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -1025,8 +1126,8 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(counter, 0, sizeof(int), cs);
-        cudaMemsetAsync(dsamples, 0, sizeof(unsigned long long), cs);
-        pick_fused(mode, rc->sampling, c->g.dtype, tex)(grid, cs, djobs, n_views, total, counter);
+        cudaMemsetAsync(dsamples, 0, 2 * sizeof(unsigned long long), cs);
+        pick_fused(mode, rc->sampling, c->g.dtype, tex, skip)(grid, cs, djobs, n_views, total, counter);
         e = cudaStreamEndCapture(cs, &gph->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gph->exec, gph->graph, 0);
@@ -1140,11 +1241,13 @@ size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs)
     return 1024 + 4096 * jobs.size() + sizeof(JobDesc) * jobs.size() + 1024;
 }
 
+size_t render_hetero_counter_bytes(size_t n_jobs) { return 16 * n_jobs; }
+
 size_t render_hetero_stage_bytes(size_t n_jobs) { return 4096 * n_jobs + sizeof(JobDesc) * n_jobs + 256; }
 
 // One persistent launch over renders of different cubes, image sizes, cameras
 // and transfer functions (all with the same mode/sampling/dtype).  Job i counts
-// its samples into dev_samples[i] (zeroed here).  host_stage: pinned host memory
+// its samples into dev_samples[2i] (lattice) and [2i+1] (evaluated), zeroed here.  host_stage: pinned host memory
 // of render_hetero_stage_bytes() used to upload the job table without waiting.
 vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream_t st, void *scratch,
                          size_t scratch_bytes, unsigned long long *dev_samples, void *host_stage)
@@ -1163,19 +1266,24 @@ vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream
         int tw, th;
         pick_tile(h.cube, h.rc, tw, th);
         hjobs[i] = make_job(h.cube, h.cam, h.rc, mode, h.term, mode ? dtf + 256 * i : nullptr, h.out, 0, tw, th);
-        hjobs[i].samples = dev_samples + i;
+        hjobs[i].samples = dev_samples + 2 * i;
+        hjobs[i].skip_below = mode ? transparent_below(h.cube, h.tf_host) : -INFINITY;
         hjobs[i].item_begin = total;
         total += (int64_t)hjobs[i].tiles_x * hjobs[i].tiles_y;
         if (mode) std::memcpy(htf + 1024 * i, h.tf_host, 4096);
     }
     VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    VRC_CK(ctx, cudaMemsetAsync(dev_samples, 0, sizeof(unsigned long long) * hj.size(), st));
+    VRC_CK(ctx, cudaMemsetAsync(dev_samples, 0, 2 * sizeof(unsigned long long) * hj.size(), st));
     if (mode) VRC_CK(ctx, cudaMemcpyAsync(dtf, htf, 4096 * hj.size(), cudaMemcpyHostToDevice, st));
     VRC_CK(ctx, cudaMemcpyAsync(djobs, hjobs, sizeof(JobDesc) * hj.size(), cudaMemcpyHostToDevice, st));
-    bool tex = true;
-    for (const HetJob &h : hj) tex = tex && h.cube->dtex != nullptr;
-    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt, tex), total);
-    pick_fused(mode, sampling, dt, tex)(grid, st, djobs, (int)hj.size(), total, counter);
+    bool tex = true, skip = true;
+    for (size_t i = 0; i < hj.size(); ++i) {
+        tex = tex && hj[i].cube->dtex != nullptr;
+        skip = skip && hjobs[i].cellmax != nullptr;
+    }
+    skip = skip && tex;
+    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt, tex, skip), total);
+    pick_fused(mode, sampling, dt, tex, skip)(grid, st, djobs, (int)hj.size(), total, counter);
     count_launch(ctx);
     VRC_CK(ctx, cudaGetLastError());
     return VRC_OK;

@@ -100,7 +100,7 @@ size_t batch_bytes(vrc_ctx *ctx, const std::vector<SReq *> &reqs, bool render)
 {
     if (render) {
         std::vector<HetJob> dummy(reqs.size());
-        return round256(render_hetero_scratch_bytes(dummy)) + round256(8 * reqs.size());
+        return round256(render_hetero_scratch_bytes(dummy)) + round256(16 * reqs.size());
     }
     size_t per = ((stats_scratch_bytes(ctx) + 255) & ~(size_t)255) + 256;
     size_t b = 0;
@@ -123,7 +123,7 @@ bool launch_batch(Server *S, SBatch *B, bool render)
     }
     ctx->used.fetch_add((int64_t)B->dbytes);
     const size_t n = B->reqs.size();
-    B->hmem = pinned_take(S, n * (sizeof(vrc_stats) + 8) + render_hetero_stage_bytes(n) + 256, &B->hbytes);
+    B->hmem = pinned_take(S, n * (sizeof(vrc_stats) + 16) + render_hetero_stage_bytes(n) + 256, &B->hbytes);
     if (!B->hmem) {
         cudaFreeAsync(B->dmem, B->st);
         ctx->used.fetch_sub((int64_t)B->dbytes);
@@ -149,9 +149,9 @@ bool launch_batch(Server *S, SBatch *B, bool render)
         const size_t sbytes = round256(render_hetero_scratch_bytes(jobs));
         unsigned long long *cnt = (unsigned long long *)((char *)B->dmem + sbytes);
         char *hcnt = (char *)B->hmem + n * sizeof(vrc_stats);
-        void *stage = (void *)round256((size_t)(hcnt + 8 * n));
+        void *stage = (void *)round256((size_t)(hcnt + 16 * n));
         s = render_hetero(ctx, jobs, B->st, B->dmem, sbytes, cnt, stage);
-        if (s == VRC_OK) cudaMemcpyAsync(hcnt, cnt, 8 * n, cudaMemcpyDeviceToHost, B->st);
+        if (s == VRC_OK) cudaMemcpyAsync(hcnt, cnt, 16 * n, cudaMemcpyDeviceToHost, B->st);
     } else {
         const size_t per = ((stats_scratch_bytes(ctx) + 255) & ~(size_t)255) + 256;
         char *p = (char *)B->dmem;
@@ -188,7 +188,7 @@ void retire(Server *S, SBatch *B, bool render)
         SReq *q = B->reqs[i];
         if (q->status == VRC_OK) {
             if (render) {
-                q->samples = cnt[i];
+                q->samples = cnt[2 * i];
             } else {
                 q->stats = ((const vrc_stats *)B->hmem)[i];
                 if (q->stats.n == 0) q->status = VRC_E_NONFINITE;

@@ -67,6 +67,10 @@ struct Cube {
     unsigned long long *dtex = nullptr;   // device [3][nbricks] texture handles by layer axis (0 where absent)
     int32_t tex_axes = 0;                 // bit a set: copy layered along axis a exists (only z is built)
     int64_t tex_bytes = 0;
+    // maximum stored value of every 8^3 macro-cell plus a one-voxel margin,
+    // read from the brick that owns the cell (empty-space skipping)
+    float *cellmax = nullptr;
+    int32_t ncell[3] = {0, 0, 0};
     // tuning (0 = default)
     int32_t tile_w = 0, tile_h = 0, ctas_per_sm = 0;
     std::atomic<int> refs{0};
@@ -95,7 +99,7 @@ struct vrc_ctx {
     int64_t inj_left = 0;
     Server *server = nullptr;
     std::mutex srv_mu;
-    // sample count of the last render (pinned host word + completion event)
+    // sample counts of the last render: [lattice, evaluated] (pinned host words + completion event)
     unsigned long long *h_samples = nullptr;
     cudaEvent_t ev_samples = nullptr;
 };

@@ -361,3 +361,30 @@ def test_texture_gather_equals_global_loads(ctx, dtype, cube128):
     b = ctx.render_mip(cid, cams, vrc.raycfg(64, 48, 0.5, path="fused_ldg")).cpu()
     assert torch.equal(a, b)
     ctx.cube_free(cid)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_empty_space_skipping_is_exact(ctx, dtype, cube128):
+    """skip_empty skips samples whose 8^3 macro-cell cannot change the result
+    (transparent under the TF for DVR, below the ray's running max for MIP);
+    the image must be bit-identical and fewer samples fetched."""
+    vrc = vrcmod()
+    v = cube128[:96, :80, :112].copy()
+    dims = (112, 80, 96)
+    cid = ctx.cube_upload(v, dtype, brick=32)
+    cams = cubegen.orbit_cameras(dims, 3) + cubegen.random_cameras(dims, 2, 11)
+    for tf in (cubegen.tf_sparse(), cubegen.tf_random(4)):
+        a = ctx.render_dvr(cid, cams, vrc.raycfg(72, 56, 0.5), tf).cpu()
+        n0, e0 = ctx.last_render_samples(evaluated=True)
+        b = ctx.render_dvr(cid, cams, vrc.raycfg(72, 56, 0.5, skip_empty=True), tf).cpu()
+        n1, e1 = ctx.last_render_samples(evaluated=True)
+        assert torch.equal(a, b)
+        assert n0 == n1 == e0 and e1 <= e0
+    tf = cubegen.tf_sparse()
+    _, e1 = ctx.render_dvr(cid, cams, vrc.raycfg(72, 56, 0.5, skip_empty=True), tf), None
+    n1, e1 = ctx.last_render_samples(evaluated=True)
+    assert e1 < 0.5 * n1          # the sparse TF leaves most of the noise transparent
+    a = ctx.render_mip(cid, cams, vrc.raycfg(72, 56, 0.5)).cpu()
+    b = ctx.render_mip(cid, cams, vrc.raycfg(72, 56, 0.5, skip_empty=True)).cpu()
+    assert torch.equal(a, b)
+    ctx.cube_free(cid)
