@@ -49,6 +49,48 @@ def workload(name: str) -> dict:
     raise SystemExit(f"unknown workload {name}")
 
 
+def workload_config(w: dict, views: int) -> dict:
+    """Workload identity shared by both arms of the benchmark."""
+    return {"workload": w["name"], "dims": list(w["dims"]), "sources": w["n_sources"], "seed": w["seed"],
+            "brick": w["brick"], "storage": w["storage"], "views": views, "image": [w["W"], w["H"]],
+            "step": w["step"], "sampling": "trilinear", "tf": w["tf"], "term_alpha": w["term"],
+            "hist_bins": w["nbins"]}
+
+
+RENDER_SOURCES = ("paper_1111_6661_b300/csrc/render.cu", "paper_1111_6661_b300/csrc/ray.cuh")
+TRAFFIC_PROFILE = "profiles/k_render_fused_dvr1024_traffic.md"
+
+
+def render_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in RENDER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def render_traffic():
+    """DRAM bytes per launch of the render kernel from the committed ncu
+    summary, or None if the kernel sources changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != render_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(PEAKS) as f:
@@ -198,8 +240,7 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": w["name"], "dims": list(w["dims"]), "views": w["views"],
-                       "image": [w["W"], w["H"]], "step": w["step"], "storage": w["storage"]},
+            "config": dict(workload_config(w, len(cams)), parallelism="rank0 only (CPU oracle)"),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
                              "sample": f"{pix_total} random pixels over {args.steps} steps, ~{budget:.0f} s each"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -324,16 +365,13 @@ def run_gpu(args, w):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": w["name"], "dims": list(w["dims"]), "sources": w["n_sources"],
-                           "brick": w["brick"], "storage": w["storage"], "views": len(cams),
-                           "image": [w["W"], w["H"]], "step": w["step"], "sampling": "trilinear",
-                           "tf": w["tf"], "term_alpha": w["term"], "hist_bins": w["nbins"],
-                           "samples_per_step": samples_per_step, "parallelism": f"replicas{ws}",
-                           "render_copy_bytes": info["render_copy_bytes"],
-                           "l2": "inputs larger than L2 (cube bricks %.1f GB > 126 MB)" % (info["bytes"] / 1e9)},
+                "config": dict(workload_config(w, len(cams)),
+                               **{"samples_per_step": samples_per_step, "parallelism": f"replicas{ws}",
+                                  "render_copy_bytes": info["render_copy_bytes"],
+                                  "l2": "inputs larger than L2 (cube bricks %.1f GB > 126 MB)" % (info["bytes"] / 1e9)}),
                 "roofline": {"bound": "alu", "kernel": "k_render_fused (DVR)", "achieved": achieved_tflops,
                              "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp32_peak_tflops,
-                             "traffic": None, "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
+                             "traffic": render_traffic(), "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz"},
                 "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms,

@@ -131,7 +131,9 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
             if (MODE == 0) {
                 m = fmaxf(m, s);
             } else {
-                if (s == s) {
+                // s <= skip_below gives alpha exactly 0 under the TF: the over step
+                // would add zero, so the lookup is not made (exact)
+                if (s == s && !(s <= J.skip_below)) {
                     const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
                     const float a = opacity(c.w, step, J.opacity_correction);
                     const float w = (1.f - A) * a;
