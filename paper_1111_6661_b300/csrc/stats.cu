@@ -66,8 +66,8 @@ __device__ __forceinline__ void decode16(const uint4 &raw, float scale, float *x
     }
 }
 
-constexpr int kVecPerLane = 4;                 // 16-byte vectors in flight per lane
-constexpr int kLogChunk = 7;                   // 128 vectors per warp iteration
+constexpr int kVecPerLane = 8;                 // 16-byte vectors in flight per lane
+constexpr int kLogChunk = 8;                   // 256 vectors per warp iteration (32 lanes x 8)
 
 struct Acc {
     float2 s_hi, s_lo;                         // TwoSum accumulation of d (two lanes of f32x2)
@@ -120,9 +120,12 @@ __device__ __forceinline__ void accumulate(const float *x, int nvalid, const Sta
         acc.q_hi = T;
         acc.q_lo = __fadd2_rn(acc.q_lo, __ffma2_rn(En, m1, Er));
         if (HIST) {
+            // bin = trunc(t), t = fl(fl(x - min) * scale) in [0, nbins * (1 + 2^-23)]: t == nbins
+            // (x == max) lands in a guard counter that the flush folds into the last bin
             const float2 Tb = __fmul2_rn(__fadd2_rn(X, nvmin2), hs2);
             const int nbm1 = a.nbins - 1;
-            const int b0 = min((int)Tb.x, nbm1), b1 = min((int)Tb.y, nbm1);
+            const int b0 = HIST == 1 ? (int)Tb.x : min((int)Tb.x, nbm1);
+            const int b1 = HIST == 1 ? (int)Tb.y : min((int)Tb.y, nbm1);
             if (!CHECK || v0) {
                 if (HIST == 1) atomicAdd(&sh[b0], 1u);
                 else atomicAdd(&a.hist[b0], 1ull);
@@ -145,14 +148,14 @@ __device__ __forceinline__ void accumulate(const float *x, int nvalid, const Sta
 // binary64 per block.  Histogram: the stated binary32 bin formula into shared-memory
 // counters (HIST 1) or global counters (HIST 2), flushed once per block.
 template <int DT, int HIST>
-__global__ void __launch_bounds__(kStatsThreads) k_stats(StatsArgs a)
+__global__ void __launch_bounds__(kStatsThreads, 4) k_stats(StatsArgs a)
 {
     extern __shared__ uint32_t sh_hist[];
     constexpr int VE = DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 8 : 16);
     constexpr int LOG_VE = DT == VRC_F32 ? 2 : (DT == VRC_BF16 ? 3 : 4);
     const BrickGeom &g = a.g;
     if (HIST == 1) {
-        for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) sh_hist[i] = 0;
+        for (int i = threadIdx.x; i <= a.nbins; i += blockDim.x) sh_hist[i] = 0;   // nbins + guard
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
@@ -229,8 +232,9 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(StatsArgs a)
         a.partials[blockIdx.x] = r;
     }
     if (HIST == 1) {
+        __syncthreads();
         for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) {
-            const uint32_t cnt = sh_hist[i];
+            const uint32_t cnt = sh_hist[i] + (i == a.nbins - 1 ? sh_hist[a.nbins] : 0u);
             if (cnt) atomicAdd(&a.hist[i], (unsigned long long)cnt);
         }
     }
@@ -407,7 +411,7 @@ vrc_status stats_launch_with(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *de
     a.partials = (StatPartial *)partials;
     if (nbins > 0) VRC_CK(ctx, cudaMemsetAsync(dev_hist, 0, sizeof(uint64_t) * nbins, st));
     const int hist = nbins == 0 ? 0 : (nbins <= kSmemBinsMax ? 1 : 2);
-    const size_t smem = hist == 1 ? sizeof(uint32_t) * nbins : 0;
+    const size_t smem = hist == 1 ? sizeof(uint32_t) * (nbins + 1) : 0;
     int used = 0;
     if (g.dtype == VRC_F32) used = launch_stats<VRC_F32>(a, ctx->sm_count, grid, smem, hist, st);
     else if (g.dtype == VRC_BF16) used = launch_stats<VRC_BF16>(a, ctx->sm_count, grid, smem, hist, st);
