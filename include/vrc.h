@@ -83,20 +83,27 @@ typedef struct {
                                   trilinear samples through texture gathers */
 #define VRC_PATH_SORTLAST 1    /* per-brick partial images, composited in visibility order */
 #define VRC_PATH_FUSED_LDG 2   /* fused, trilinear samples by 8 global loads (no textures) */
+#define VRC_PATH_ZEROCOPY  3   /* streamed cubes: the sort-last kernels read the bricks in place
+                                  from mapped pinned host memory (no copies, no device ring) */
 typedef struct {
     int32_t width, height;     /* image size in pixels (1..16384) */
-    float step;                /* sample spacing along the unit ray, voxel units (> 0) */
+    float step;                /* sample spacing along the unit ray, voxel units (> 0, and
+                                  at least the cube's diagonal / 2^22: VRC_E_INVAL below) */
     int32_t sampling;          /* VRC_NEAREST or VRC_TRILINEAR */
     int32_t opacity_correction;/* DVR: 0 = alpha as in the transfer function,
                                   1 = 1-(1-alpha)^step */
-    int32_t path;              /* VRC_PATH_FUSED, VRC_PATH_SORTLAST or VRC_PATH_FUSED_LDG */
+    int32_t path;              /* VRC_PATH_FUSED, VRC_PATH_SORTLAST, VRC_PATH_FUSED_LDG or
+                                  VRC_PATH_ZEROCOPY (streamed cubes only) */
     int32_t tile_w, tile_h;    /* ray tile; 0,0 = tuned default.  tile_w*tile_h = 256,
                                   tile_w in {8,16,32} */
-    int32_t skip_empty;        /* fused trilinear path: 1 = skip samples that cannot
-                                  change the image (DVR: the transfer function is
-                                  transparent up to the 8^3 macro-cell's maximum;
-                                  MIP: the cell's maximum cannot raise the ray's max).
-                                  The image is identical; 0 = sample everything */
+    int32_t skip_empty;        /* 1 = skip work that cannot change the image; the
+                                  image is identical.  Fused trilinear path: skip
+                                  samples whose 8^3 macro-cell maximum is transparent
+                                  under the transfer function (DVR) or cannot raise
+                                  the ray's max (MIP).  Sort-last paths (DVR): cull
+                                  whole bricks whose maximum, halo included, is
+                                  transparent; a streamed cube then copies fewer
+                                  bricks.  0 = sample everything */
     int32_t reserved;          /* must be 0 */
 } vrc_raycfg;
 
@@ -279,6 +286,20 @@ vrc_status vrc_render_dvr(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams,
  * render to finish.  Outputs are HOST memory.
  */
 vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *evaluated);
+
+/*
+ * Bricks of the most recent sort-last render on this context (Sec. 2: each
+ * brick is rendered on its own into a partial image): *traversed = distinct
+ * bricks that some view's rays cross and that were rendered (for a streamed
+ * cube: copied to the device, or read in place on the zero-copy path);
+ * *culled = distinct bricks those rays cross that were skipped because no
+ * sample inside them can be visible (skip_empty with DVR: the brick's largest
+ * value, halo included, is at or below the transfer function's transparent
+ * threshold).  Both 0 after a fused render.  Outputs are HOST memory;
+ * VRC_E_INVAL on NULL arguments.  Culled bricks' samples are not traversed and
+ * are not counted by vrc_last_render_samples.
+ */
+vrc_status vrc_last_render_bricks(vrc_ctx *ctx, int64_t *traversed, int64_t *culled);
 
 /*
  * Sort-last combination of two image buffers (Sec. 2: gathered partial

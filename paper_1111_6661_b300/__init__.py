@@ -195,6 +195,12 @@ class Context:
         self._check(self._lib.vrc_last_render_samples(self.h, ctypes.byref(n), ctypes.byref(e)))
         return (n.value, e.value) if evaluated else n.value
 
+    def last_render_bricks(self):
+        """(traversed, culled) distinct bricks of the last sort-last render."""
+        t, c = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.vrc_last_render_bricks(self.h, ctypes.byref(t), ctypes.byref(c)))
+        return t.value, c.value
+
     def composite(self, front, back, mode: str = "dvr", out=None, stream=None):
         import torch
         if out is None:

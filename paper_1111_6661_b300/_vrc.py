@@ -16,7 +16,7 @@ STATUS = {0: "VRC_OK", 1: "VRC_PENDING", -1: "VRC_E_INVAL", -2: "VRC_E_NOMEM", -
           -9: "VRC_E_UNSUPPORTED"}
 DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
 SAMPLING = {"nearest": 0, "trilinear": 1}
-PATHS = {"fused": 0, "sortlast": 1, "fused_ldg": 2}
+PATHS = {"fused": 0, "sortlast": 1, "fused_ldg": 2, "zerocopy": 3}
 INJECT = {"none": 0, "alloc": 1, "h2d": 2, "drop": 3}
 
 
@@ -78,6 +78,7 @@ PROTOTYPES = {
     "vrc_render_dvr": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p, c_f32,
                                c_p, c_p]),
     "vrc_last_render_samples": (c_i32, [c_p, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)]),
+    "vrc_last_render_bricks": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "vrc_composite": (c_i32, [c_p, c_p, c_p, c_p, c_i64, c_i32, c_p]),
     "vrc_graph_create": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p,
                                  c_f32, c_p, ctypes.POINTER(c_p)]),

@@ -271,4 +271,12 @@ vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *ev
     return VRC_OK;
 }
 
+vrc_status vrc_last_render_bricks(vrc_ctx *ctx, int64_t *traversed, int64_t *culled)
+{
+    if (!ctx || !traversed || !culled) return VRC_E_INVAL;
+    *traversed = ctx->last_bricks[0].load();
+    *culled = ctx->last_bricks[1].load();
+    return VRC_OK;
+}
+
 }  // extern "C"

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "vrc_internal.h"
 
@@ -204,9 +205,26 @@ vrc_status finish_metadata(vrc_ctx *ctx, Cube *c, cudaStream_t st, const double 
 // surface.  Copy `axis` a stores local voxel l at texel (u, v, layer) =
 // (l[a1]+1, l[a2]+1, l[a]+1) with (a1, a2) = (x, y) for a = z, (y, z) for
 // a = x, (z, x) for a = y.  grid.y = layer.
+// FP8 bricks are copied as binary16 code values (every e4m3 value is exact in
+// binary16), so the texture unit returns them as fp32 with no conversion
+// instructions in the sampler; the per-brick scale is applied after the lerps.
+struct Fp8AsHalf {};
+template <typename T> struct TexElem { using type = T; };
+template <> struct TexElem<Fp8AsHalf> { using type = unsigned short; };
+
+template <typename T>
+__device__ __forceinline__ typename TexElem<T>::type tex_value(const uint8_t *brick, int64_t e)
+{
+    if constexpr (std::is_same<T, Fp8AsHalf>::value)
+        return __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)brick[e], __NV_E4M3).x;
+    else
+        return reinterpret_cast<const T *>(brick)[e];
+}
+
 template <typename T>
 __global__ void k_fill_array(const uint8_t *__restrict__ brick, BrickGeom g, int axis, cudaSurfaceObject_t surf)
 {
+    using E = typename TexElem<T>::type;
     const int layer = blockIdx.y;
     const int R = g.R;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R * R; i += gridDim.x * blockDim.x) {
@@ -215,8 +233,8 @@ __global__ void k_fill_array(const uint8_t *__restrict__ brick, BrickGeom g, int
         if (axis == 2) { sx = u; sy = v; sz = layer; }
         else if (axis == 0) { sy = u; sz = v; sx = layer; }
         else { sz = u; sx = v; sy = layer; }
-        const T val = reinterpret_cast<const T *>(brick)[((int64_t)sz * R + sy) * g.P + (g.O - 1) + sx];
-        surf2DLayeredwrite(val, surf, u * (int)sizeof(T), v, layer);
+        const E val = tex_value<T>(brick, ((int64_t)sz * R + sy) * g.P + (g.O - 1) + sx);
+        surf2DLayeredwrite(val, surf, u * (int)sizeof(E), v, layer);
     }
 }
 
@@ -277,6 +295,18 @@ vrc_status build_cellmax(vrc_ctx *ctx, Cube *c, cudaStream_t st)
                                                       c->ncell[1], c->ncell[2], c->cellmax);
     count_launch(ctx);
     VRC_CK(ctx, cudaGetLastError());
+    // per-brick maximum over the brick's cells (the cells with their margins
+    // cover the interior and the halo)
+    std::vector<float> h(n);
+    VRC_CK(ctx, cudaMemcpyAsync(h.data(), c->cellmax, n * 4, cudaMemcpyDeviceToHost, st));
+    VRC_CK(ctx, cudaStreamSynchronize(st));
+    c->h_bhalo_max.assign(g.nbricks, -INFINITY);
+    for (int64_t i = 0; i < n; ++i) {
+        const int cx = (int)(i % c->ncell[0]), cy = (int)((i / c->ncell[0]) % c->ncell[1]);
+        const int cz = (int)(i / ((int64_t)c->ncell[0] * c->ncell[1]));
+        const int64_t b = ((int64_t)(cz / cpb) * g.nb[1] + cy / cpb) * g.nb[0] + cx / cpb;
+        c->h_bhalo_max[b] = std::fmax(c->h_bhalo_max[b], h[i]);
+    }
     return VRC_OK;
 }
 
@@ -298,13 +328,14 @@ void release_textures(vrc_ctx *ctx, Cube *c)
 vrc_status build_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
 {
     const BrickGeom &g = c->g;
-    const int64_t per_copy = g.esize * (int64_t)g.R * g.R * g.R * g.nbricks + (1 << 20);
+    const int64_t tex_esize = g.dtype == VRC_FP8E4M3 ? 2 : g.esize;
+    const int64_t per_copy = tex_esize * (int64_t)g.R * g.R * g.R * g.nbricks + (1 << 20);
     vrc_status s = dev_alloc(ctx, (void **)&c->dtex, 3 * g.nbricks * 8);
     if (s != VRC_OK) return s;
     VRC_CK(ctx, cudaMemsetAsync(c->dtex, 0, 3 * g.nbricks * 8, st));
     cudaChannelFormatDesc desc = g.dtype == VRC_F32 ? cudaCreateChannelDesc<float>()
                                : (g.dtype == VRC_BF16 ? cudaCreateChannelDesc<unsigned short>()
-                                                      : cudaCreateChannelDesc<unsigned char>());
+                                                      : cudaCreateChannelDescHalf());
     // leave room in the budget for the render scratch of a large multi-view call
     const int64_t reserve = (int64_t)2 << 30;
     // one copy layered along z: copies along x and y were measured to buy ~5% on
@@ -331,7 +362,7 @@ vrc_status build_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
             dim3 grid((unsigned)std::min<int64_t>((int64_t)g.R * g.R / 256 + 1, 64), (unsigned)g.R);
             if (g.dtype == VRC_F32) k_fill_array<float><<<grid, 256, 0, st>>>(src, g, axis, surf);
             else if (g.dtype == VRC_BF16) k_fill_array<unsigned short><<<grid, 256, 0, st>>>(src, g, axis, surf);
-            else k_fill_array<unsigned char><<<grid, 256, 0, st>>>(src, g, axis, surf);
+            else k_fill_array<Fp8AsHalf><<<grid, 256, 0, st>>>(src, g, axis, surf);
             count_launch(ctx);
             cudaError_t e = cudaGetLastError();
             VRC_CK(ctx, cudaStreamSynchronize(st));
@@ -487,11 +518,14 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
     vrc_status s = VRC_OK;
     if (inject_fire(ctx, VRC_INJECT_ALLOC)) s = set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
     if (s == VRC_OK) {
-        cudaError_t e = cudaHostAlloc(&c->host_pool, (size_t)n_host_bricks * g.brick_bytes, cudaHostAllocPortable);
+        cudaError_t e = cudaHostAlloc(&c->host_pool, (size_t)n_host_bricks * g.brick_bytes,
+                                      cudaHostAllocPortable | cudaHostAllocMapped);
         if (e != cudaSuccess) {
             c->host_pool = nullptr;
             s = cuda_err(ctx, e, "cudaHostAlloc (pinned brick store)");
             if (s == VRC_E_CUDA) s = VRC_E_NOMEM;
+        } else if ((e = cudaHostGetDevicePointer(&c->host_pool_dev, c->host_pool, 0)) != cudaSuccess) {
+            s = cuda_err(ctx, e, "cudaHostGetDevicePointer (pinned brick store)");
         }
     }
     if (s == VRC_OK) s = dev_alloc(ctx, &c->ring_pool, (size_t)ring_bricks * g.brick_bytes);
@@ -504,6 +538,7 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
     c->h_bmin.assign(g.nbricks, FLT_MAX);
     c->h_bmax.assign(g.nbricks, -FLT_MAX);
     c->h_bnonfinite.assign(g.nbricks, 0);
+    c->h_bhalo_max.assign(g.nbricks, -INFINITY);
     std::vector<float> ones(g.nbricks, 1.f);
     cudaMemcpy(c->scales, ones.data(), g.nbricks * 4, cudaMemcpyHostToDevice);
     c->charged = (int64_t)ring_bricks * g.brick_bytes;
@@ -521,7 +556,7 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
     const BrickGeom &g = c->g;
     const int R = g.R;
     float *dst = reinterpret_cast<float *>((char *)c->host_pool + slot * g.brick_bytes);
-    float mn = FLT_MAX, mx = -FLT_MAX;
+    float mn = FLT_MAX, mx = -FLT_MAX, hmx = -INFINITY;
     int32_t nnf = 0;
     for (int zr = 0; zr < R; ++zr)
         for (int yr = 0; yr < R; ++yr) {
@@ -529,6 +564,7 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
             const float *in = bw + ((int64_t)zr * R + yr) * R;
             std::memset(row, 0, sizeof(float) * g.P);
             std::memcpy(row + g.O - 1, in, sizeof(float) * R);
+            for (int x = 0; x < R; ++x) hmx = std::fmax(hmx, in[x]);   // NaN ignored, +inf kept
             if (zr >= 1 && zr <= g.B && yr >= 1 && yr <= g.B)
                 for (int x = 1; x <= g.B; ++x) {
                     float v = in[x];
@@ -540,12 +576,16 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
                     }
                 }
         }
-    c->host_filled[slot] = 1;
+    if (!c->host_filled[slot]) {
+        c->host_filled[slot] = 1;
+        ++c->n_filled;
+    }
     // every logical brick aliased to this slot gets its extrema
     for (int64_t b = slot; b < g.nbricks; b += c->n_host) {
         c->h_bmin[b] = mn;
         c->h_bmax[b] = mx;
         c->h_bnonfinite[b] = nnf;
+        c->h_bhalo_max[b] = hmx;
     }
     float vmn = FLT_MAX, vmx = -FLT_MAX;
     for (int64_t b = 0; b < g.nbricks; ++b) {

@@ -181,7 +181,7 @@ template <int DT>
 __device__ __forceinline__ float4 gather4(unsigned long long tex, int layer, float u, float v)
 {
     float4 r;
-    if (DT == VRC_F32) {
+    if (DT == VRC_F32 || DT == VRC_FP8E4M3) {   // fp32 texels, or fp8 codes stored as binary16
         asm volatile("tld4.r.a2d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
                      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
                      : "l"(tex), "r"(layer), "f"(u), "f"(v));
@@ -190,15 +190,8 @@ __device__ __forceinline__ float4 gather4(unsigned long long tex, int layer, flo
         asm volatile("tld4.r.a2d.v4.u32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
                      : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
                      : "l"(tex), "r"(layer), "f"(u), "f"(v));
-        if (DT == VRC_BF16) {
-            r = make_float4(__uint_as_float(a << 16), __uint_as_float(b << 16), __uint_as_float(c << 16),
-                            __uint_as_float(d << 16));
-        } else {
-            auto f8 = [](uint32_t q) {
-                return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
-            };
-            r = make_float4(f8(a), f8(b), f8(c), f8(d));
-        }
+        r = make_float4(__uint_as_float(a << 16), __uint_as_float(b << 16), __uint_as_float(c << 16),
+                        __uint_as_float(d << 16));   // bf16 bits
     }
     return r;
 }

@@ -150,11 +150,101 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
     else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(cr, cg, cb, A);
 }
 
+// One ray of the fused path on the texture copies.  A sample belongs to the
+// brick of voxel clamp(floor(p)); along one ray the binary32 positions are
+// monotone on every axis, so the samples of one brick are consecutive and
+// leaving it is decided by one compare per axis against the face the ray moves
+// towards (faces on the cube's border are infinite).  Brick index, texture
+// handle and origin are recomputed only when a sample leaves the brick (one
+// loop, so the lanes of a warp stay in step).  Texel coordinates are formed in
+// binary32 from floor(p - 0.5) (exact small integers): every sample reads the
+// same texels with the same weights as the per-sample lookup of trace_fused.
+template <int MODE, int DT>
+__device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, int px, int py, uint32_t &nsamp)
+{
+    float o[3], d[3], tin, tout;
+    const bool hit = ray_setup(J.vp, J.cv.fdims, px, py, o, d, tin, tout);
+    const int64_t pix = (int64_t)py * J.vp.W + px;
+    float m = -FLT_MAX, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+    if (hit) {
+        const float step = J.step;
+        const CubeView &cv = J.cv;
+        const bool neg0 = d[0] < 0.f, neg1 = d[1] < 0.f, neg2 = d[2] < 0.f;
+        // exit faces; the initial values make the first sample enter its brick
+        float E0 = neg0 ? INFINITY : -INFINITY, E1 = neg1 ? INFINITY : -INFINITY, E2 = neg2 ? INFINITY : -INFINITY;
+        float c0 = 0.f, c1 = 0.f, scale = 1.f;
+        int zo = 0;
+        unsigned long long th = 0;
+        float kh = 0.5f;   // k + 0.5, exact: rays have fewer than 2^22 samples
+#pragma unroll 1
+        for (;;) {
+            const float t = __fadd_rn(tin, __fmul_rn(kh, step));
+            if (!(t < tout)) break;
+            const float p0 = __fadd_rn(o[0], __fmul_rn(t, d[0]));
+            const float p1 = __fadd_rn(o[1], __fmul_rn(t, d[1]));
+            const float p2 = __fadd_rn(o[2], __fmul_rn(t, d[2]));
+            if ((p0 >= E0) != neg0 || (p1 >= E1) != neg1 || (p2 >= E2) != neg2) {
+                // entering the brick of this sample
+                const int bx = min(max((int)floorf(p0), 0), cv.dims[0] - 1) >> cv.logB;
+                const int by = min(max((int)floorf(p1), 0), cv.dims[1] - 1) >> cv.logB;
+                const int bz = min(max((int)floorf(p2), 0), cv.dims[2] - 1) >> cv.logB;
+                const int b = (bz * cv.nb[1] + by) * cv.nb[0] + bx;
+                th = __ldg(cv.tex + (int64_t)2 * cv.nb[0] * cv.nb[1] * cv.nb[2] + b);
+                if (DT == VRC_FP8E4M3) scale = __ldg(cv.scales + b);
+                auto face = [&](int bi, int nbi, float da) {
+                    if (da > 0.f) return bi == nbi - 1 ? INFINITY : (float)((bi + 1) << cv.logB);
+                    if (da < 0.f) return bi == 0 ? -INFINITY : (float)(bi << cv.logB);
+                    return INFINITY;
+                };
+                E0 = face(bx, cv.nb[0], d[0]);
+                E1 = face(by, cv.nb[1], d[1]);
+                E2 = face(bz, cv.nb[2], d[2]);
+                // texel (u, v) = floor(p - 0.5) - origin + 2; layer = floor(p_z - 0.5) - origin_z + 1
+                c0 = (float)((bx << cv.logB) - 2);
+                c1 = (float)((by << cv.logB) - 2);
+                zo = (bz << cv.logB) - 1;
+            }
+            const float q0 = __fsub_rn(p0, 0.5f), q1 = __fsub_rn(p1, 0.5f), q2 = __fsub_rn(p2, 0.5f);
+            const float f0 = floorf(q0), f1 = floorf(q1), f2 = floorf(q2);
+            const float wx = __fsub_rn(q0, f0), wy = __fsub_rn(q1, f1), wz = __fsub_rn(q2, f2);
+            const float u = __fsub_rn(f0, c0), v = __fsub_rn(f1, c1);
+            const int layer = (int)f2 - zo;
+            const float4 g0 = gather4<DT>(th, layer, u, v);
+            const float4 g1 = gather4<DT>(th, layer + 1, u, v);
+            // gather order: x = (u-1, v), y = (u, v), z = (u, v-1), w = (u-1, v-1)
+            const float c00 = fmaf(wx, g0.z - g0.w, g0.w), c10 = fmaf(wx, g0.y - g0.x, g0.x);
+            const float c01 = fmaf(wx, g1.z - g1.w, g1.w), c11 = fmaf(wx, g1.y - g1.x, g1.x);
+            const float e0 = fmaf(wy, c10 - c00, c00), e1 = fmaf(wy, c11 - c01, c01);
+            float sv = fmaf(wz, e1 - e0, e0);
+            if (DT == VRC_FP8E4M3) sv = sv * scale;
+            ++nsamp;
+            if (MODE == 0) {
+                m = fmaxf(m, sv);
+            } else {
+                if (sv == sv && !(sv <= J.skip_below)) {
+                    const float4 c = classify(s_tf, sv, J.vmin, J.inv_range);
+                    const float a = opacity(c.w, step, J.opacity_correction);
+                    const float w = (1.f - A) * a;
+                    cr = fmaf(w, c.x, cr);
+                    cg = fmaf(w, c.y, cg);
+                    cb = fmaf(w, c.z, cb);
+                    A += w;
+                }
+                if (A >= J.term) break;
+            }
+            kh = __fadd_rn(kh, 1.f);
+        }
+    }
+    if (MODE == 0) J.out[pix] = m;
+    else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(cr, cg, cb, A);
+}
+
 // Fused path, persistent: CTAs pull (job, tile) items from an atomic counter.
-// TEX: trilinear samples come from the cubes' texture copies.
+// TEX: trilinear samples come from the cubes' texture copies.  Register caps
+// (CTAs per SM) are the measured best: 6 for texture MIP, 5 otherwise.
 template <int MODE, int SAMPLING, int DT, bool TEX, bool SKIP>
-__global__ void __launch_bounds__(kThreads, 5) k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs,
-                                                           int64_t total_items, int *counter)
+__global__ void __launch_bounds__(kThreads, (MODE == 0 && TEX && !SKIP) ? 6 : 5)
+    k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs, int64_t total_items, int *counter)
 {
     __shared__ float4 s_tf[256];
     __shared__ int64_t s_item;
@@ -182,9 +272,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_render_fused(const JobDesc *__r
         tile_pixel(J.tile_w, J.warp_w, lx, ly);
         const int px = tx * J.tile_w + lx, py = ty * J.tile_h + ly;
         // TEX kernels are launched only when every job's cube has texture copies
-        if (px < J.vp.W && py < J.vp.H)
-            trace_fused<MODE, SAMPLING, DT, ((TEX && SAMPLING == VRC_TRILINEAR) ? 2 : -1),
-                        (SKIP && TEX && SAMPLING == VRC_TRILINEAR)>(J, s_tf, px, py, nsamp, neval);
+        if (px < J.vp.W && py < J.vp.H) {
+            if (TEX && SAMPLING == VRC_TRILINEAR && !SKIP) {
+                trace_tex<MODE, DT>(J, s_tf, px, py, nsamp);
+                neval = nsamp;
+            } else {
+                trace_fused<MODE, SAMPLING, DT, ((TEX && SAMPLING == VRC_TRILINEAR) ? 2 : -1),
+                            (SKIP && TEX && SAMPLING == VRC_TRILINEAR)>(J, s_tf, px, py, nsamp, neval);
+            }
+        }
         if (J.samples) warp_count2(J.samples, nsamp, neval);   // one atomic pair per warp and item
         nsamp = neval = 0;
         __syncthreads();
@@ -461,7 +557,8 @@ vrc_status check_rc(vrc_ctx *ctx, const vrc_raycfg *rc)
         return set_err(ctx, VRC_E_INVAL, "step must be >= 1e-3");
     if (rc->sampling != VRC_NEAREST && rc->sampling != VRC_TRILINEAR) return set_err(ctx, VRC_E_INVAL, "bad sampling");
     if (rc->opacity_correction != 0 && rc->opacity_correction != 1) return set_err(ctx, VRC_E_INVAL, "bad opacity flag");
-    if (rc->path != VRC_PATH_FUSED && rc->path != VRC_PATH_SORTLAST && rc->path != VRC_PATH_FUSED_LDG)
+    if (rc->path != VRC_PATH_FUSED && rc->path != VRC_PATH_SORTLAST && rc->path != VRC_PATH_FUSED_LDG &&
+        rc->path != VRC_PATH_ZEROCOPY)
         return set_err(ctx, VRC_E_INVAL, "bad path");
     if ((rc->skip_empty != 0 && rc->skip_empty != 1) || rc->reserved != 0)
         return set_err(ctx, VRC_E_INVAL, "bad skip_empty/reserved");
@@ -726,10 +823,20 @@ struct SortLastPlan {
     std::vector<BrickItem> items;              // grouped by wavefront, then brick
     std::vector<int64_t> brick_item_begin;     // per (wavefront, brick) entry
     std::vector<int64_t> wave_item_begin;      // per wavefront (+ end)
+    int64_t culled = 0;                        // crossed bricks left out (transparent)
+    int64_t traversed() const
+    {
+        int64_t n = 0;
+        for (const auto &w : wave_bricks) n += (int64_t)w.size();
+        return n;
+    }
 };
 
+// Bricks whose largest sample value (halo included) is at or below cull_le
+// hold no visible sample (DVR, transparent transfer function) and are left out;
+// cull_le = -inf keeps every brick.
 void plan_sortlast(const Cube *c, const std::vector<JobDesc> &jobs, const std::vector<vrc_camera> &cams,
-                   SortLastPlan &plan)
+                   float cull_le, SortLastPlan &plan)
 {
     const BrickGeom &g = c->g;
     const int nb = (int)g.nbricks;
@@ -748,15 +855,21 @@ void plan_sortlast(const Cube *c, const std::vector<JobDesc> &jobs, const std::v
     plan.wave_bricks.clear();
     plan.wave_item_begin.clear();
     plan.brick_item_begin.clear();
+    plan.culled = 0;
+    const bool cull = cull_le > -INFINITY && (int64_t)c->h_bhalo_max.size() == g.nbricks;
     for (int k = 0; k <= maxkey; ++k) {
         std::vector<int> bricks;
         const int64_t wbeg = (int64_t)plan.items.size();
         for (int b = 0; b < nb; ++b) {
             const int64_t bbeg = (int64_t)plan.items.size();
+            const bool culled = cull && c->h_bhalo_max[b] <= cull_le;
+            bool crossed = false;
             for (size_t v = 0; v < jobs.size(); ++v) {
                 if (key[v][b] != k) continue;
                 int box[4];
                 if (!brick_bbox(cams[v], g, jobs[v].vp.W, jobs[v].vp.H, b, box)) continue;
+                crossed = true;
+                if (culled) continue;
                 const int tw = jobs[v].tile_w, th = jobs[v].tile_h;
                 for (int y = (box[1] / th) * th; y < box[3]; y += th)
                     for (int x = (box[0] / tw) * tw; x < box[2]; x += tw)
@@ -766,6 +879,7 @@ void plan_sortlast(const Cube *c, const std::vector<JobDesc> &jobs, const std::v
                 bricks.push_back(b);
                 plan.brick_item_begin.push_back(bbeg);
             }
+            plan.culled += culled && crossed;
         }
         if ((int64_t)plan.items.size() > wbeg) {
             plan.wave_key.push_back(k);
@@ -804,13 +918,13 @@ vrc_status validate_render(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams
         if (!valid_cam(cams[v])) return set_err(ctx, VRC_E_INVAL, "bad camera %d", v);
     Cube *c = find_cube(ctx, cube_id);
     if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    if ((s = validate_step(ctx, c, rc->step)) != VRC_OK) return s;
     *cube = c;
     return VRC_OK;
 }
 
-vrc_status render_streamed(vrc_ctx *ctx, Cube *c, const std::vector<JobDesc> &jobs_in,
-                           const std::vector<vrc_camera> &cams, const vrc_raycfg &rc, float *out, int64_t npix_total,
-                           int mode, cudaStream_t st, unsigned long long *dsamples, Arena &ar, const float4 *dtf,
+vrc_status render_streamed(vrc_ctx *ctx, Cube *c, SortLastPlan &plan, const vrc_raycfg &rc, float *out,
+                           int64_t npix_total, int mode, cudaStream_t st, unsigned long long *dsamples, Arena &ar,
                            const JobDesc *djobs);
 
 vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg *rc,
@@ -832,10 +946,19 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         jobs[v].item_begin = total;
         total += (int64_t)jobs[v].tiles_x * jobs[v].tiles_y;
     }
+    if (rc->path == VRC_PATH_ZEROCOPY && !c->streamed)
+        return set_err(ctx, VRC_E_UNSUPPORTED, "zero-copy rendering is for streamed cubes");
+    const bool zerocopy = rc->path == VRC_PATH_ZEROCOPY;
     const bool sortlast = c->streamed || rc->path == VRC_PATH_SORTLAST;
     if (!sortlast && !c->pool) return set_err(ctx, VRC_E_UNSUPPORTED, "cube has no resident bricks");
+    if (c->streamed && c->n_filled < c->n_host)
+        return set_err(ctx, VRC_E_INVAL, "streamed cube: %lld of %lld host slots never written",
+                       (long long)(c->n_host - c->n_filled), (long long)c->n_host);
+    const float thr = mode == 1 ? transparent_below(c, tf_rgba) : -INFINITY;
     SortLastPlan plan;
-    if (sortlast) plan_sortlast(c, jobs, camv, plan);
+    if (sortlast) plan_sortlast(c, jobs, camv, rc->skip_empty && mode == 1 ? thr : -INFINITY, plan);
+    ctx->last_bricks[0] = sortlast ? plan.traversed() : 0;
+    ctx->last_bricks[1] = sortlast ? plan.culled : 0;
     const size_t img_floats = (size_t)n_views * npix * (mode == 0 ? 1 : 4);
     size_t need = 4096 + 1024 * 4 + sizeof(JobDesc) * n_views + 256 * 4;
     if (sortlast) need += sizeof(BrickItem) * plan.items.size() + sizeof(float) * img_floats + 1024;
@@ -846,7 +969,6 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     unsigned long long *dsamples = ar.take<unsigned long long>(2);
     float4 *dtf = ar.take<float4>(256);
     JobDesc *djobs = ar.take<JobDesc>(n_views);
-    const float thr = mode == 1 ? transparent_below(c, tf_rgba) : -INFINITY;
     for (auto &j : jobs) {
         if (mode == 1) j.tf = dtf;
         j.samples = dsamples;
@@ -866,7 +988,11 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         pick_fused(mode, rc->sampling, c->g.dtype, tex, skip)(grid, st, djobs, n_views, total, counter);
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
-    } else if (!c->streamed) {
+    } else if (!c->streamed || zerocopy) {
+        // resident bricks, or (zero-copy) bricks read in place from mapped pinned host memory
+        if (zerocopy)
+            for (BrickItem &it : plan.items) it.slot = (int32_t)(it.brick % c->n_host);
+        const uint8_t *slot_base = (const uint8_t *)(zerocopy ? c->host_pool_dev : c->pool);
         BrickItem *ditems = ar.take<BrickItem>(std::max<size_t>(1, plan.items.size()));
         float *partial = ar.take<float>(img_floats);
         if (!plan.items.empty())
@@ -887,7 +1013,7 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         for (size_t w = 0; w + 1 < plan.wave_item_begin.size(); ++w) {
             const int64_t b0 = plan.wave_item_begin[w], b1 = plan.wave_item_begin[w + 1];
             if (b1 <= b0) continue;
-            bf(b1 - b0, st, djobs, ditems + b0, (const uint8_t *)c->pool, c->g.brick_bytes, out, partial, dsamples);
+            bf(b1 - b0, st, djobs, ditems + b0, slot_base, c->g.brick_bytes, out, partial, dsamples);
             const int gc = grid_for(npx, ctx->sm_count * 8);
             if (mode == 0) k_composite<0><<<gc, 256, 0, st>>>(out, partial, nullptr, nullptr, nullptr, npx, 1);
             else k_composite<1><<<gc, 256, 0, st>>>(out, partial, nullptr, nullptr, nullptr, npx, 1);
@@ -895,7 +1021,7 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         }
         VRC_CK(ctx, cudaGetLastError());
     } else {
-        s = render_streamed(ctx, c, jobs, camv, *rc, out, (int64_t)n_views * npix, mode, st, dsamples, ar, dtf, djobs);
+        s = render_streamed(ctx, c, plan, *rc, out, (int64_t)n_views * npix, mode, st, dsamples, ar, djobs);
         if (s != VRC_OK) return s;
     }
     if (samples_out) {
@@ -912,15 +1038,11 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
 // device ring on a side stream, in wavefront order, in chunks of half the ring;
 // chunk i renders while chunk i+1 copies.  Each wavefront's partial image is
 // composited after its last chunk.
-vrc_status render_streamed(vrc_ctx *ctx, Cube *c, const std::vector<JobDesc> &jobs_in,
-                           const std::vector<vrc_camera> &cams, const vrc_raycfg &rc, float *out, int64_t npx,
-                           int mode, cudaStream_t st, unsigned long long *dsamples, Arena &ar, const float4 *dtf,
+vrc_status render_streamed(vrc_ctx *ctx, Cube *c, SortLastPlan &plan, const vrc_raycfg &rc, float *out,
+                           int64_t npx, int mode, cudaStream_t st, unsigned long long *dsamples, Arena &ar,
                            const JobDesc *djobs)
 {
-    (void)dtf;
     const BrickGeom &g = c->g;
-    SortLastPlan plan;
-    plan_sortlast(c, jobs_in, cams, plan);
     // chunks: runs of consecutive bricks inside one wavefront, at most half the ring
     const int half = c->ring / 2;
     struct Chunk {
@@ -1292,4 +1414,15 @@ vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream
 }
 
 vrc_status validate_raycfg(vrc_ctx *ctx, const vrc_raycfg *rc) { return check_rc(ctx, rc); }
+
+// A ray crosses at most the cube's diagonal; the samplers count samples in
+// binary32 (k + 0.5 must stay exact), so a ray may hold at most 2^22 samples.
+vrc_status validate_step(vrc_ctx *ctx, const Cube *c, float step)
+{
+    const double diag = std::sqrt((double)c->g.dims[0] * c->g.dims[0] + (double)c->g.dims[1] * c->g.dims[1] +
+                                  (double)c->g.dims[2] * c->g.dims[2]);
+    if (!(diag / (double)step < 4194304.0))
+        return set_err(ctx, VRC_E_INVAL, "step %g too small: more than 2^22 samples per ray", (double)step);
+    return VRC_OK;
+}
 bool camera_is_valid(const vrc_camera &c) { return valid_cam(c); }

@@ -349,6 +349,7 @@ vrc_status vrc_submit(vrc_ctx *ctx, const vrc_request *req, uint64_t *ticket)
         if (req->nbins < 0 || req->nbins > 65536) return set_err(ctx, VRC_E_INVAL, "bad nbins");
     } else {
         vrc_status s = validate_raycfg(ctx, &req->rc);
+        if (s == VRC_OK) s = validate_step(ctx, c, req->rc.step);
         if (s != VRC_OK) return s;
         if (req->rc.path != VRC_PATH_FUSED) return set_err(ctx, VRC_E_UNSUPPORTED, "serving renders use the fused path");
         if (!camera_is_valid(req->cam)) return set_err(ctx, VRC_E_INVAL, "bad camera");

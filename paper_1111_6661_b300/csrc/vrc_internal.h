@@ -50,16 +50,22 @@ struct Cube {
     int32_t *bnonfinite = nullptr;// device [nbricks] non-finite interior voxels
     std::vector<float> h_bmin, h_bmax;
     std::vector<int32_t> h_bnonfinite;
+    // largest stored value a sample of brick b can read (interior plus halo;
+    // NaN ignored, +inf kept): bricks at or below the transparent threshold of a
+    // transfer function are culled from sort-last renders
+    std::vector<float> h_bhalo_max;
     float vmin = 0.f, vmax = 0.f; // stored extrema over finite voxels
     float shift = 0.f;            // approximate mean (upload pass): centres the statistics sums
     bool has_finite = false;
     int64_t charged = 0;          // bytes charged to the budget
     // out-of-core
-    void *host_pool = nullptr;    // pinned, n_host slots of brick_bytes
+    void *host_pool = nullptr;    // pinned and mapped, n_host slots of brick_bytes
+    void *host_pool_dev = nullptr;// device address of host_pool (zero-copy reads)
     int64_t n_host = 0;
     int32_t ring = 0;
     void *ring_pool = nullptr;    // device, ring slots
     std::vector<uint8_t> host_filled;
+    int64_t n_filled = 0;         // host slots written at least once
     // render copies of the bricks as 2D layered CUDA arrays (layers along z),
     // read by texture gathers (2x2 texel footprints) in the fused renderer
     std::vector<cudaArray_t> tex_arrays;
@@ -102,6 +108,8 @@ struct vrc_ctx {
     // sample counts of the last render: [lattice, evaluated] (pinned host words + completion event)
     unsigned long long *h_samples = nullptr;
     cudaEvent_t ev_samples = nullptr;
+    // sort-last brick counts of the last render: [traversed, culled] (host)
+    std::atomic<int64_t> last_bricks[2] = {{0}, {0}};
 };
 
 // ------------------------------------------------------------------ helpers
@@ -112,6 +120,7 @@ vrc_status dev_alloc(vrc_ctx *ctx, void **p, size_t bytes);
 void dev_free(vrc_ctx *ctx, void *p, size_t bytes);
 vrc_status scratch_get(vrc_ctx *ctx, size_t bytes, void **p);
 Cube *find_cube(vrc_ctx *ctx, int64_t id);
+vrc_status validate_step(vrc_ctx *ctx, const Cube *c, float step);   // at most 2^22 samples per ray
 inline void count_launch(vrc_ctx *ctx, uint64_t n = 1) { ctx->launches.fetch_add(n); }
 
 #define VRC_CK(ctx, call)                                   \

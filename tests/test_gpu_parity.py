@@ -317,6 +317,13 @@ def test_error_codes(ctx, cube128):
     with pytest.raises(vrc.VrcError, match="INVAL"):
         ctx.cube_stats(cid, 70000)
     ctx.cube_free(cid)
+    # more than 2^22 samples per ray: diagonal 5793 voxels at step 1e-3 (checked
+    # before anything is read, so the streamed cube needs no bricks)
+    big = (4096, 4096, 64)
+    sid = ctx.cube_create_streamed(big, 256, 1, 2)
+    with pytest.raises(vrc.VrcError, match=r"2\^22"):
+        ctx.render_mip(sid, [cubegen.ortho_z_camera(big)], vrc.raycfg(8, 8, 1e-3))
+    ctx.cube_free(sid)
 
 
 def test_budget_and_injected_allocation_failure():

@@ -94,3 +94,109 @@ def test_injected_h2d_failure(ctx, cube128):
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
     ctx.cube_free(sid)
+
+
+def test_zero_copy_matches_streamed(ctx, cube128):
+    """Zero-copy variant: the brick kernels read the pinned host slots in place
+    (mapped memory) instead of copying them to a device ring.  It runs the
+    resident sort-last schedule, so it is bit-identical to the resident cube's
+    sort-last render, and within the DVR tolerance of the streamed render (whose
+    wavefronts are split into ring-sized chunks)."""
+    import paper_1111_6661_b300 as vrc
+    v = cube128[:64, :48, :80].copy()
+    dims = (80, 48, 64)
+    sid, _ = make_streamed(ctx, v, 16, ring=4)
+    rid = ctx.cube_upload(v, "f32", brick=16)
+    cams = cubegen.orbit_cameras(dims, 2)
+    tf = cubegen.tf_dense()
+    zc = vrc.raycfg(40, 32, 0.5, path="zerocopy")
+    z = ctx.render_dvr(sid, cams, zc, tf).cpu()
+    assert torch.equal(z, ctx.render_dvr(rid, cams, vrc.raycfg(40, 32, 0.5, path="sortlast"), tf).cpu())
+    assert (z - ctx.render_dvr(sid, cams, vrc.raycfg(40, 32, 0.5), tf).cpu()).abs().max() <= 1e-4
+    z = ctx.render_mip(sid, cams, zc).cpu()
+    assert torch.equal(z, ctx.render_mip(sid, cams, vrc.raycfg(40, 32, 0.5)).cpu())
+    with pytest.raises(vrc.VrcError, match="UNSUPPORTED"):
+        ctx.render_mip(rid, cams, zc)
+    ctx.cube_free(rid)
+    ctx.cube_free(sid)
+
+
+def test_zero_copy_aliased_slots(ctx, cube128):
+    """With fewer host slots than bricks, the zero-copy path reads slot b % n."""
+    import paper_1111_6661_b300 as vrc
+    v = cube128[:48, :48, :48].copy()
+    K = 5
+    aid, _ = make_streamed(ctx, v, 16, n_host=K)
+    fid, _ = make_streamed(ctx, v, 16, n_host=None, source=lambda b: b % K)
+    cams = cubegen.orbit_cameras((48, 48, 48), 2)
+    rc = vrc.raycfg(32, 32, 0.5, path="zerocopy")
+    tf = cubegen.tf_sparse()
+    assert torch.equal(ctx.render_dvr(aid, cams, rc, tf).cpu(), ctx.render_dvr(fid, cams, rc, tf).cpu())
+    ctx.cube_free(aid)
+    ctx.cube_free(fid)
+
+
+def _tf_threshold(u0):
+    t = cubegen.tf_sparse()
+    t[: int(np.ceil(u0 * 255)), 3] = 0.0
+    return t
+
+
+@pytest.mark.parametrize("path", ["sortlast", "streamed", "zerocopy"])
+def test_brick_culling_is_exact(ctx, cube128, path):
+    """skip_empty on the sort-last paths culls bricks whose maximum (halo
+    included) is transparent under the TF; the image is bit-identical and the
+    culled bricks are neither rendered nor (streamed) copied."""
+    import paper_1111_6661_b300 as vrc
+    v = cube128[:64, :48, :80].copy()
+    dims = (80, 48, 64)
+    if path == "sortlast":
+        cid = ctx.cube_upload(v, "f32", brick=16)
+    else:
+        cid, _ = make_streamed(ctx, v, 16, ring=4)
+    p = "sortlast" if path == "sortlast" else ("zerocopy" if path == "zerocopy" else "fused")
+    cams = cubegen.orbit_cameras(dims, 2) + [cubegen.ortho_z_camera(dims)]
+    for tf in (cubegen.tf_sparse(), _tf_threshold(0.3), cubegen.tf_dense()):
+        a = ctx.render_dvr(cid, cams, vrc.raycfg(40, 32, 0.5, path=p), tf).cpu()
+        t0, c0 = ctx.last_render_bricks()
+        b = ctx.render_dvr(cid, cams, vrc.raycfg(40, 32, 0.5, path=p, skip_empty=True), tf).cpu()
+        t1, c1 = ctx.last_render_bricks()
+        assert torch.equal(a, b)
+        assert c0 == 0 and t1 + c1 == t0
+        if tf[0, 3] > 0:
+            assert c1 == 0          # no transparent range: nothing to cull
+    assert c1 == 0
+    b = ctx.render_dvr(cid, cams, vrc.raycfg(40, 32, 0.5, path=p, skip_empty=True), _tf_threshold(0.3)).cpu()
+    assert ctx.last_render_bricks()[1] > 0
+    # MIP never culls
+    ctx.render_mip(cid, cams, vrc.raycfg(40, 32, 0.5, path=p, skip_empty=True))
+    assert ctx.last_render_bricks()[1] == 0
+    ctx.cube_free(cid)
+
+
+def test_brick_culling_keeps_inf_halo(ctx):
+    """A +inf voxel on a brick face is visible (u clamps to 1) from the
+    neighbouring brick through its halo: neither brick may be culled."""
+    import paper_1111_6661_b300 as vrc
+    v = np.zeros((32, 32, 48), dtype=np.float32)
+    v[:, :, :] = np.linspace(0.0, 1.0, 48, dtype=np.float32)[None, None, :] * 0.01
+    v[0, 0, 0] = 100.0            # sets the range
+    v[16, 16, 16] = np.inf        # first voxel of brick (1,1,1)
+    cid = ctx.cube_upload(v, "f32", brick=16)
+    tf = _tf_threshold(0.5)
+    cams = [cubegen.camera("persp", (60.0, 50.0, -40.0), (24.0, 16.0, 16.0), (0, 1, 0), fovy_deg=40)]
+    a = ctx.render_dvr(cid, cams, vrc.raycfg(64, 64, 0.5, path="sortlast"), tf).cpu()
+    b = ctx.render_dvr(cid, cams, vrc.raycfg(64, 64, 0.5, path="sortlast", skip_empty=True), tf).cpu()
+    assert torch.equal(a, b)
+    assert float(a[..., 3].max()) > 0
+    ctx.cube_free(cid)
+
+
+def test_unfilled_streamed_cube_is_rejected(ctx, cube128):
+    import paper_1111_6661_b300 as vrc
+    v = cube128[:32, :32, :32].copy()
+    cid = ctx.cube_create_streamed((32, 32, 32), 16, 8, 4)
+    ctx.cube_put_brick(cid, 0, brick_with_halo(v, 16, 0, (2, 2, 2)))
+    with pytest.raises(vrc.VrcError, match="INVAL"):
+        ctx.render_mip(cid, cubegen.orbit_cameras((32, 32, 32), 1), vrc.raycfg(16, 16, 0.5))
+    ctx.cube_free(cid)
