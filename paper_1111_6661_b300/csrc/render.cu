@@ -175,6 +175,14 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
         float c0 = 0.f, c1 = 0.f, scale = 1.f;
         int zo = 0;
         unsigned long long th = 0;
+        // fp32 MIP: texels of the previous sample's 2x2x2 cell, reused when the
+        // next sample falls in the same cell (step < 1).  Measured: +7% for fp32
+        // MIP; for DVR and for 2-byte texels the extra live registers cost as
+        // much as the saved gathers or more (bf16 MIP spills and halves).
+        constexpr bool kReuse = MODE == 0 && DT == VRC_F32;
+        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+        float pu = -1.f, pv = -1.f;
+        int pl = -1;
         float kh = 0.5f;   // k + 0.5, exact: rays have fewer than 2^22 samples
 #pragma unroll 1
         for (;;) {
@@ -203,14 +211,20 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
                 c0 = (float)((bx << cv.logB) - 2);
                 c1 = (float)((by << cv.logB) - 2);
                 zo = (bz << cv.logB) - 1;
+                pl = -1;   // texel coordinates are local to the brick
             }
             const float q0 = __fsub_rn(p0, 0.5f), q1 = __fsub_rn(p1, 0.5f), q2 = __fsub_rn(p2, 0.5f);
             const float f0 = floorf(q0), f1 = floorf(q1), f2 = floorf(q2);
             const float wx = __fsub_rn(q0, f0), wy = __fsub_rn(q1, f1), wz = __fsub_rn(q2, f2);
             const float u = __fsub_rn(f0, c0), v = __fsub_rn(f1, c1);
             const int layer = (int)f2 - zo;
-            const float4 g0 = gather4<DT>(th, layer, u, v);
-            const float4 g1 = gather4<DT>(th, layer + 1, u, v);
+            if (!kReuse || layer != pl || u != pu || v != pv) {
+                g0 = gather4<DT>(th, layer, u, v);
+                g1 = gather4<DT>(th, layer + 1, u, v);
+                pl = layer;
+                pu = u;
+                pv = v;
+            }
             // gather order: x = (u-1, v), y = (u, v), z = (u, v-1), w = (u-1, v-1)
             const float c00 = fmaf(wx, g0.z - g0.w, g0.w), c10 = fmaf(wx, g0.y - g0.x, g0.x);
             const float c01 = fmaf(wx, g1.z - g1.w, g1.w), c11 = fmaf(wx, g1.y - g1.x, g1.x);
@@ -221,7 +235,7 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
             if (MODE == 0) {
                 m = fmaxf(m, sv);
             } else {
-                if (sv == sv && !(sv <= J.skip_below)) {
+                if (sv > J.skip_below) {   // false for NaN
                     const float4 c = classify(s_tf, sv, J.vmin, J.inv_range);
                     const float a = opacity(c.w, step, J.opacity_correction);
                     const float w = (1.f - A) * a;
