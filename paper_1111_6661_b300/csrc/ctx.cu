@@ -2,7 +2,9 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <cmath>
+#include <iterator>
 
 #include "vrc_internal.h"
 
@@ -40,20 +42,70 @@ bool inject_fire(vrc_ctx *ctx, int32_t what)
     return false;
 }
 
+// Block sizes are rounded (512 B below 1 MiB, 2 MiB above) so that repeated
+// allocations of one shape (cube pools, staging, metadata) hit the cache.
+static size_t round_block(size_t bytes)
+{
+    const size_t q = bytes < ((size_t)1 << 20) ? 512 : ((size_t)2 << 20);
+    return (bytes + q - 1) / q * q;
+}
+
+void destroy_tex_array(const TexArray &a)
+{
+    if (a.tex) cudaDestroyTextureObject(a.tex);
+    if (a.surf) cudaDestroySurfaceObject(a.surf);
+    if (a.arr) cudaFreeArray(a.arr);
+}
+
+void cache_trim(vrc_ctx *ctx, int64_t keep_bytes)
+{
+    std::lock_guard<std::mutex> lk(ctx->cache_mu);
+    while (ctx->cached.load() > keep_bytes && !ctx->cached_arrays.empty()) {
+        auto it = ctx->cached_arrays.begin();
+        destroy_tex_array(it->second);
+        ctx->cached.fetch_sub(it->second.bytes);
+        ctx->cached_arrays.erase(it);
+    }
+    while (ctx->cached.load() > keep_bytes && !ctx->cached_blocks.empty()) {
+        auto it = std::prev(ctx->cached_blocks.end());   // largest first
+        cudaFree(it->second);
+        ctx->cached.fetch_sub((int64_t)it->first);
+        ctx->cached_blocks.erase(it);
+    }
+}
+
 vrc_status dev_alloc(vrc_ctx *ctx, void **p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) return VRC_OK;
     if (inject_fire(ctx, VRC_INJECT_ALLOC)) return set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
-    int64_t prev = ctx->used.fetch_add((int64_t)bytes);
-    if (prev + (int64_t)bytes > ctx->budget) {
-        ctx->used.fetch_sub((int64_t)bytes);
+    const size_t rb = round_block(bytes);
+    int64_t prev = ctx->used.fetch_add((int64_t)rb);
+    if (prev + (int64_t)rb > ctx->budget) {
+        ctx->used.fetch_sub((int64_t)rb);
         return set_err(ctx, VRC_E_NOMEM, "HBM budget exceeded: %lld used + %zu requested > %lld",
-                       (long long)prev, bytes, (long long)ctx->budget);
+                       (long long)prev, rb, (long long)ctx->budget);
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        auto it = ctx->cached_blocks.find(rb);
+        if (it != ctx->cached_blocks.end()) {
+            *p = it->second;
+            ctx->cached_blocks.erase(it);
+            ctx->cached.fetch_sub((int64_t)rb);
+            return VRC_OK;
+        }
+    }
+    cache_trim(ctx, std::max<int64_t>(0, ctx->budget - ctx->used.load()));
+    cudaError_t e = cudaMalloc(p, rb);
     if (e != cudaSuccess) {
-        ctx->used.fetch_sub((int64_t)bytes);
+        cudaGetLastError();
+        cache_trim(ctx, 0);   // cached blocks may be what fills the device
+        e = cudaMalloc(p, rb);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->used.fetch_sub((int64_t)rb);
         *p = nullptr;
         return cuda_err(ctx, e, "cudaMalloc");
     }
@@ -63,8 +115,31 @@ vrc_status dev_alloc(vrc_ctx *ctx, void **p, size_t bytes)
 void dev_free(vrc_ctx *ctx, void *p, size_t bytes)
 {
     if (!p) return;
-    cudaFree(p);
-    ctx->used.fetch_sub((int64_t)bytes);
+    const size_t rb = round_block(bytes);
+    {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        ctx->cached_blocks.emplace(rb, p);
+        ctx->cached.fetch_add((int64_t)rb);
+    }
+    ctx->used.fetch_sub((int64_t)rb);
+}
+
+bool tex_array_take(vrc_ctx *ctx, uint64_t key, TexArray *a)
+{
+    std::lock_guard<std::mutex> lk(ctx->cache_mu);
+    auto it = ctx->cached_arrays.find(key);
+    if (it == ctx->cached_arrays.end()) return false;
+    *a = it->second;
+    ctx->cached.fetch_sub(a->bytes);
+    ctx->cached_arrays.erase(it);
+    return true;
+}
+
+void tex_array_give(vrc_ctx *ctx, uint64_t key, const TexArray &a)
+{
+    std::lock_guard<std::mutex> lk(ctx->cache_mu);
+    ctx->cached_arrays.emplace(key, a);
+    ctx->cached.fetch_add(a.bytes);
 }
 
 vrc_status scratch_get(vrc_ctx *ctx, size_t bytes, void **p)
@@ -237,6 +312,8 @@ vrc_status vrc_destroy(vrc_ctx *ctx)
     }
     for (int64_t id : ids) vrc_cube_free(ctx, id);
     if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
+    cudaDeviceSynchronize();
+    cache_trim(ctx, 0);
     if (ctx->ev_samples) cudaEventDestroy(ctx->ev_samples);
     if (ctx->h_samples) cudaFreeHost(ctx->h_samples);
     delete ctx;

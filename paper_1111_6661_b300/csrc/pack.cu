@@ -167,18 +167,29 @@ __global__ void __launch_bounds__(256) k_brick_pack(const float *__restrict__ sr
     }
 }
 
-vrc_status finish_metadata(vrc_ctx *ctx, Cube *c, cudaStream_t st, const double *dbsum)
+// Per-brick metadata to the host: brick extrema, non-finite counts, sums,
+// halo-inclusive maxima.  Issued last on the upload stream; the device-to-
+// pageable copies return when they are done.
+vrc_status fetch_metadata(vrc_ctx *ctx, Cube *c, cudaStream_t st, const double *dbsum, std::vector<double> &bsum)
 {
     const BrickGeom &g = c->g;
-    std::vector<double> bsum(2 * g.nbricks);
-    VRC_CK(ctx, cudaMemcpyAsync(bsum.data(), dbsum, g.nbricks * 16, cudaMemcpyDeviceToHost, st));
+    bsum.resize(2 * g.nbricks);
     c->h_bmin.resize(g.nbricks);
     c->h_bmax.resize(g.nbricks);
     c->h_bnonfinite.resize(g.nbricks);
+    c->h_bhalo_max.resize(g.nbricks);
+    VRC_CK(ctx, cudaMemcpyAsync(bsum.data(), dbsum, g.nbricks * 16, cudaMemcpyDeviceToHost, st));
     VRC_CK(ctx, cudaMemcpyAsync(c->h_bmin.data(), c->bmin, g.nbricks * 4, cudaMemcpyDeviceToHost, st));
     VRC_CK(ctx, cudaMemcpyAsync(c->h_bmax.data(), c->bmax, g.nbricks * 4, cudaMemcpyDeviceToHost, st));
     VRC_CK(ctx, cudaMemcpyAsync(c->h_bnonfinite.data(), c->bnonfinite, g.nbricks * 4, cudaMemcpyDeviceToHost, st));
-    VRC_CK(ctx, cudaStreamSynchronize(st));
+    VRC_CK(ctx, cudaMemcpyAsync(c->h_bhalo_max.data(), c->bhalo, g.nbricks * 4, cudaMemcpyDeviceToHost, st));
+    return VRC_OK;
+}
+
+// Cube extrema (TF range) and the statistics shift from the per-brick values.
+void finish_metadata(Cube *c, const std::vector<double> &bsum)
+{
+    const BrickGeom &g = c->g;
     float mn = FLT_MAX, mx = -FLT_MAX;
     bool any = false;
     for (int64_t b = 0; b < g.nbricks; ++b) {
@@ -198,7 +209,6 @@ vrc_status finish_metadata(vrc_ctx *ctx, Cube *c, cudaStream_t st, const double 
     }
     c->shift = cnt > 0 ? (float)(tot / cnt) : 0.f;
     if (!std::isfinite(c->shift)) c->shift = c->vmin;
-    return VRC_OK;
 }
 
 // Copy one packed brick (interior + halo) into a layered CUDA array through a
@@ -275,14 +285,43 @@ __global__ void k_cell_max(const uint8_t *__restrict__ pool, BrickGeom g, const 
     }
 }
 
-vrc_status build_cellmax(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+// Largest cell maximum of each brick (the cells with their margins cover the
+// brick's interior and halo).  One block per brick.
+__global__ void k_brick_halo_max(const float *__restrict__ cellmax, BrickGeom g, int ncx, int ncy, int cpb,
+                                 float *__restrict__ bhalo)
+{
+    const int b = blockIdx.x;
+    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+    const int n = cpb * cpb * cpb;
+    float m = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int lx = i % cpb, ly = (i / cpb) % cpb, lz = i / (cpb * cpb);
+        const int64_t cell = ((int64_t)(bz * cpb + lz) * ncy + (by * cpb + ly)) * ncx + (bx * cpb + lx);
+        m = fmaxf(m, cellmax[cell]);
+    }
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+        bhalo[b] = m;
+    }
+}
+
+vrc_status alloc_cellmax(vrc_ctx *ctx, Cube *c)
 {
     const BrickGeom &g = c->g;
     const int cpb = g.B / 8;
     for (int a = 0; a < 3; ++a) c->ncell[a] = g.nb[a] * cpb;
     const int64_t n = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
-    vrc_status s = dev_alloc(ctx, (void **)&c->cellmax, n * 4);
-    if (s != VRC_OK) return s;
+    return dev_alloc(ctx, (void **)&c->cellmax, n * 4);
+}
+
+vrc_status launch_cellmax(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    const int64_t n = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 16);
     if (g.dtype == VRC_F32)
         k_cell_max<VRC_F32><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0], c->ncell[1],
@@ -293,28 +332,20 @@ vrc_status build_cellmax(vrc_ctx *ctx, Cube *c, cudaStream_t st)
     else
         k_cell_max<VRC_FP8E4M3><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0],
                                                       c->ncell[1], c->ncell[2], c->cellmax);
-    count_launch(ctx);
+    k_brick_halo_max<<<(unsigned)g.nbricks, 256, 0, st>>>(c->cellmax, g, c->ncell[0], c->ncell[1], g.B / 8, c->bhalo);
+    count_launch(ctx, 2);
     VRC_CK(ctx, cudaGetLastError());
-    // per-brick maximum over the brick's cells (the cells with their margins
-    // cover the interior and the halo)
-    std::vector<float> h(n);
-    VRC_CK(ctx, cudaMemcpyAsync(h.data(), c->cellmax, n * 4, cudaMemcpyDeviceToHost, st));
-    VRC_CK(ctx, cudaStreamSynchronize(st));
-    c->h_bhalo_max.assign(g.nbricks, -INFINITY);
-    for (int64_t i = 0; i < n; ++i) {
-        const int cx = (int)(i % c->ncell[0]), cy = (int)((i / c->ncell[0]) % c->ncell[1]);
-        const int cz = (int)(i / ((int64_t)c->ncell[0] * c->ncell[1]));
-        const int64_t b = ((int64_t)(cz / cpb) * g.nb[1] + cy / cpb) * g.nb[0] + cx / cpb;
-        c->h_bhalo_max[b] = std::fmax(c->h_bhalo_max[b], h[i]);
-    }
     return VRC_OK;
 }
 
+static uint64_t tex_array_key(const BrickGeom &g) { return ((uint64_t)g.R << 8) | (uint64_t)g.dtype; }
+
+// Return the cube's render copies to the context's cache (the arrays keep
+// their surface and texture objects).  The caller guarantees no work in
+// flight reads them.
 void release_textures(vrc_ctx *ctx, Cube *c)
 {
-    for (cudaTextureObject_t t : c->tex_objs) cudaDestroyTextureObject(t);
-    for (cudaArray_t a : c->tex_arrays) cudaFreeArray(a);
-    c->tex_objs.clear();
+    for (const TexArray &a : c->tex_arrays) tex_array_give(ctx, tex_array_key(c->g), a);
     c->tex_arrays.clear();
     if (c->dtex) dev_free(ctx, c->dtex, 3 * c->g.nbricks * 8);
     c->dtex = nullptr;
@@ -323,75 +354,86 @@ void release_textures(vrc_ctx *ctx, Cube *c)
     c->tex_bytes = 0;
 }
 
-// Build the texture copies, z first, then x, then y, as long as each whole
-// copy fits the budget.  Charged to the budget.
-vrc_status build_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+// Allocate the render copy (one 2D-layered array per brick, layers along z)
+// as long as it fits the budget; charged to the budget.  Arrays come from the
+// context's cache when a freed cube left some of this shape.  Only host work:
+// it may run while earlier work still occupies the device.
+vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
 {
     const BrickGeom &g = c->g;
     const int64_t tex_esize = g.dtype == VRC_FP8E4M3 ? 2 : g.esize;
-    const int64_t per_copy = tex_esize * (int64_t)g.R * g.R * g.R * g.nbricks + (1 << 20);
+    const int64_t arr_bytes = tex_esize * (int64_t)g.R * g.R * g.R;
+    const int64_t per_copy = arr_bytes * g.nbricks + (1 << 20);
+    // leave room in the budget for the render scratch of a large multi-view call
+    const int64_t reserve = (int64_t)2 << 30;
+    if (ctx->used.load() + per_copy + reserve > ctx->budget)
+        return set_err(ctx, VRC_E_NOMEM, "budget: no room for texture copies");
     vrc_status s = dev_alloc(ctx, (void **)&c->dtex, 3 * g.nbricks * 8);
     if (s != VRC_OK) return s;
-    VRC_CK(ctx, cudaMemsetAsync(c->dtex, 0, 3 * g.nbricks * 8, st));
+    ctx->used.fetch_add(per_copy);
+    c->tex_bytes += per_copy;
     cudaChannelFormatDesc desc = g.dtype == VRC_F32 ? cudaCreateChannelDesc<float>()
                                : (g.dtype == VRC_BF16 ? cudaCreateChannelDesc<unsigned short>()
                                                       : cudaCreateChannelDescHalf());
-    // leave room in the budget for the render scratch of a large multi-view call
-    const int64_t reserve = (int64_t)2 << 30;
-    // one copy layered along z: copies along x and y were measured to buy ~5% on
-    // orbit views at twice the register pressure and three times the memory
-    const int order[1] = {2};
-    for (int k = 0; k < 1; ++k) {
-        const int axis = order[k];
-        if (ctx->used.load() + per_copy + reserve > ctx->budget) break;
-        ctx->used.fetch_add(per_copy);
-        c->tex_bytes += per_copy;
-        std::vector<unsigned long long> h(g.nbricks);
-        for (int64_t b = 0; b < g.nbricks; ++b) {
-            cudaArray_t arr = nullptr;
-            if (inject_fire(ctx, VRC_INJECT_ALLOC)) return set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
-            VRC_CK(ctx, cudaMalloc3DArray(&arr, &desc, make_cudaExtent(g.R, g.R, g.R),
-                                          cudaArrayLayered | cudaArraySurfaceLoadStore));
-            c->tex_arrays.push_back(arr);
-            cudaResourceDesc sd = {};
-            sd.resType = cudaResourceTypeArray;
-            sd.res.array.array = arr;
-            cudaSurfaceObject_t surf = 0;
-            VRC_CK(ctx, cudaCreateSurfaceObject(&surf, &sd));
-            const uint8_t *src = (const uint8_t *)c->pool + b * g.brick_bytes;
-            dim3 grid((unsigned)std::min<int64_t>((int64_t)g.R * g.R / 256 + 1, 64), (unsigned)g.R);
-            if (g.dtype == VRC_F32) k_fill_array<float><<<grid, 256, 0, st>>>(src, g, axis, surf);
-            else if (g.dtype == VRC_BF16) k_fill_array<unsigned short><<<grid, 256, 0, st>>>(src, g, axis, surf);
-            else k_fill_array<Fp8AsHalf><<<grid, 256, 0, st>>>(src, g, axis, surf);
-            count_launch(ctx);
-            cudaError_t e = cudaGetLastError();
-            VRC_CK(ctx, cudaStreamSynchronize(st));
-            cudaDestroySurfaceObject(surf);
-            if (e != cudaSuccess) return cuda_err(ctx, e, "array fill");
+    const uint64_t key = tex_array_key(g);
+    c->h_tex.assign(3 * g.nbricks, 0ull);
+    for (int64_t b = 0; b < g.nbricks; ++b) {
+        if (inject_fire(ctx, VRC_INJECT_ALLOC)) return set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
+        TexArray a;
+        if (!tex_array_take(ctx, key, &a)) {
+            cache_trim(ctx, std::max<int64_t>(0, ctx->budget - ctx->used.load()));
+            a.bytes = arr_bytes;
+            cudaError_t e = cudaMalloc3DArray(&a.arr, &desc, make_cudaExtent(g.R, g.R, g.R),
+                                              cudaArrayLayered | cudaArraySurfaceLoadStore);
             cudaResourceDesc rd = {};
             rd.resType = cudaResourceTypeArray;
-            rd.res.array.array = arr;
+            rd.res.array.array = a.arr;
+            if (e == cudaSuccess) e = cudaCreateSurfaceObject(&a.surf, &rd);
             cudaTextureDesc td = {};
             td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
             td.filterMode = cudaFilterModePoint;
             td.readMode = cudaReadModeElementType;
             td.normalizedCoords = 0;
-            cudaTextureObject_t t = 0;
-            VRC_CK(ctx, cudaCreateTextureObject(&t, &rd, &td, nullptr));
-            c->tex_objs.push_back(t);
-            h[b] = t;
+            if (e == cudaSuccess) e = cudaCreateTextureObject(&a.tex, &rd, &td, nullptr);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                destroy_tex_array(a);
+                return cuda_err(ctx, e, "render copy array");
+            }
         }
-        VRC_CK(ctx, cudaMemcpyAsync(c->dtex + axis * g.nbricks, h.data(), 8 * g.nbricks, cudaMemcpyHostToDevice, st));
-        VRC_CK(ctx, cudaStreamSynchronize(st));
-        c->tex_axes |= 1 << axis;
+        c->tex_arrays.push_back(a);
+        c->h_tex[2 * g.nbricks + b] = a.tex;   // the z-layered copy
     }
-    if (!c->tex_axes) return set_err(ctx, VRC_E_NOMEM, "budget: no room for texture copies");
+    return VRC_OK;
+}
+
+// Fill the render copy from the packed bricks (one kernel per brick) and
+// upload the table of texture handles (the z copy; x and y entries are 0).
+vrc_status launch_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    const int axis = 2;
+    for (int64_t b = 0; b < g.nbricks; ++b) {
+        const cudaSurfaceObject_t surf = c->tex_arrays[b].surf;
+        const uint8_t *src = (const uint8_t *)c->pool + b * g.brick_bytes;
+        dim3 grid((unsigned)std::min<int64_t>((int64_t)g.R * g.R / 256 + 1, 64), (unsigned)g.R);
+        if (g.dtype == VRC_F32) k_fill_array<float><<<grid, 256, 0, st>>>(src, g, axis, surf);
+        else if (g.dtype == VRC_BF16) k_fill_array<unsigned short><<<grid, 256, 0, st>>>(src, g, axis, surf);
+        else k_fill_array<Fp8AsHalf><<<grid, 256, 0, st>>>(src, g, axis, surf);
+        count_launch(ctx);
+    }
+    VRC_CK(ctx, cudaGetLastError());
+    VRC_CK(ctx, cudaMemcpyAsync(c->dtex, c->h_tex.data(), 8 * 3 * g.nbricks, cudaMemcpyHostToDevice, st));
+    c->tex_axes |= 1 << axis;
     return VRC_OK;
 }
 
 void release_cube(vrc_ctx *ctx, Cube *c)
 {
     const BrickGeom &g = c->g;
+    // the memory goes back to the context's cache and may be handed out at
+    // once: no launch still in flight may read it
+    cudaDeviceSynchronize();
     release_textures(ctx, c);
     if (c->pool) dev_free(ctx, c->pool, g.nbricks * g.brick_bytes);
     if (c->ring_pool) dev_free(ctx, c->ring_pool, (size_t)c->ring * g.brick_bytes);
@@ -400,6 +442,7 @@ void release_cube(vrc_ctx *ctx, Cube *c)
     if (c->bmin) dev_free(ctx, c->bmin, g.nbricks * 4);
     if (c->bmax) dev_free(ctx, c->bmax, g.nbricks * 4);
     if (c->bnonfinite) dev_free(ctx, c->bnonfinite, g.nbricks * 4);
+    if (c->bhalo) dev_free(ctx, c->bhalo, g.nbricks * 4);
     if (c->host_pool) cudaFreeHost(c->host_pool);
     delete c;
 }
@@ -412,6 +455,7 @@ vrc_status alloc_meta(vrc_ctx *ctx, Cube *c)
     if ((s = dev_alloc(ctx, (void **)&c->bmin, n * 4)) != VRC_OK) return s;
     if ((s = dev_alloc(ctx, (void **)&c->bmax, n * 4)) != VRC_OK) return s;
     if ((s = dev_alloc(ctx, (void **)&c->bnonfinite, n * 4)) != VRC_OK) return s;
+    if ((s = dev_alloc(ctx, (void **)&c->bhalo, n * 4)) != VRC_OK) return s;
     return VRC_OK;
 }
 
@@ -441,23 +485,33 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
     Cube *c = new (std::nothrow) Cube();
     if (!c) return VRC_E_NOMEM;
     c->g = g;
+    // 1. every allocation first (host work that overlaps earlier device work)
     vrc_status s = dev_alloc(ctx, &c->pool, g.nbricks * g.brick_bytes);
     if (s == VRC_OK) s = alloc_meta(ctx, c);
-    const float *dsrc = src;
+    if (s == VRC_OK) s = alloc_cellmax(ctx, c);
     void *staging = nullptr;
     const size_t src_bytes = (size_t)(nx * ny * nz) * 4;
-    if (s == VRC_OK && !src_on_device) {
-        s = dev_alloc(ctx, &staging, src_bytes);
-        if (s == VRC_OK) {
-            cudaError_t e = cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) s = cuda_err(ctx, e, "cube upload H2D");
-            dsrc = (const float *)staging;
-        }
-    }
+    if (s == VRC_OK && !src_on_device) s = dev_alloc(ctx, &staging, src_bytes);
     ScanPartial *part = nullptr;
     const size_t part_bytes = g.nbricks * (kScanSplit * sizeof(ScanPartial) + 16);
     if (s == VRC_OK) s = dev_alloc(ctx, (void **)&part, part_bytes);
     double *dbsum = part ? reinterpret_cast<double *>(part + g.nbricks * kScanSplit) : nullptr;
+    bool tex = false;
+    if (s == VRC_OK && getenv("VRC_NO_TEXTURES") == nullptr) {
+        // texture copies are an accelerator: without room for them the cube still renders
+        tex = alloc_textures(ctx, c) == VRC_OK;
+        if (!tex) {
+            release_textures(ctx, c);
+            fprintf(stderr, "vrc: no texture render copies for this cube (%s)\n", vrc_last_error(ctx));
+        }
+    }
+    // 2. the device work, in stream order
+    const float *dsrc = src;
+    if (s == VRC_OK && staging) {
+        cudaError_t e = cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) s = cuda_err(ctx, e, "cube upload H2D");
+        dsrc = (const float *)staging;
+    }
     if (s == VRC_OK) {
         k_brick_scan<<<dim3((unsigned)g.nbricks, kScanSplit), 256, 0, st>>>(dsrc, g, part);
         k_brick_finish<<<(unsigned)((g.nbricks + 127) / 128), 128, 0, st>>>(part, g, c->scales, c->bmin, c->bmax,
@@ -470,25 +524,16 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = cuda_err(ctx, e, "brick pack launch");
     }
-    if (s == VRC_OK) s = finish_metadata(ctx, c, st, dbsum);
-    if (s == VRC_OK) s = build_cellmax(ctx, c, st);
-    if (s == VRC_OK && getenv("VRC_NO_TEXTURES") == nullptr) {
-        // texture copies are an accelerator: without room for them the cube still renders
-        if (build_textures(ctx, c, st) != VRC_OK) {
-            cudaStreamSynchronize(st);
-            cudaGetLastError();
-            release_textures(ctx, c);
-            fprintf(stderr, "vrc: no texture render copies for this cube (%s)\n", vrc_last_error(ctx));
-        }
-    }
-    if (part) {
-        cudaStreamSynchronize(st);
-        dev_free(ctx, part, part_bytes);
-    }
-    if (staging) {
-        cudaStreamSynchronize(st);
-        dev_free(ctx, staging, src_bytes);
-    }
+    if (s == VRC_OK) s = launch_cellmax(ctx, c, st);
+    if (s == VRC_OK && tex) s = launch_textures(ctx, c, st);
+    std::vector<double> bsum;
+    if (s == VRC_OK) s = fetch_metadata(ctx, c, st, dbsum, bsum);
+    // 3. one wait, then the host-side metadata
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == VRC_OK && e != cudaSuccess) s = cuda_err(ctx, e, "cube upload");
+    if (s == VRC_OK) finish_metadata(c, bsum);
+    if (part) dev_free(ctx, part, part_bytes);
+    if (staging) dev_free(ctx, staging, src_bytes);
     if (s != VRC_OK) {
         release_cube(ctx, c);
         return s;

@@ -39,6 +39,15 @@ bool make_geom(int64_t nx, int64_t ny, int64_t nz, int32_t B, int32_t dtype, Bri
 
 struct vrc_ctx;
 
+// One brick's render copy: a layered CUDA array with the surface used to fill
+// it and the point-sampled texture object that reads it.
+struct TexArray {
+    cudaArray_t arr = nullptr;
+    cudaSurfaceObject_t surf = 0;
+    cudaTextureObject_t tex = 0;
+    int64_t bytes = 0;
+};
+
 struct Cube {
     int64_t id = 0;
     BrickGeom g{};
@@ -54,6 +63,7 @@ struct Cube {
     // NaN ignored, +inf kept): bricks at or below the transparent threshold of a
     // transfer function are culled from sort-last renders
     std::vector<float> h_bhalo_max;
+    float *bhalo = nullptr;       // device [nbricks]: the same maxima (filled at upload)
     float vmin = 0.f, vmax = 0.f; // stored extrema over finite voxels
     float shift = 0.f;            // approximate mean (upload pass): centres the statistics sums
     bool has_finite = false;
@@ -68,8 +78,8 @@ struct Cube {
     int64_t n_filled = 0;         // host slots written at least once
     // render copies of the bricks as 2D layered CUDA arrays (layers along z),
     // read by texture gathers (2x2 texel footprints) in the fused renderer
-    std::vector<cudaArray_t> tex_arrays;
-    std::vector<cudaTextureObject_t> tex_objs;
+    std::vector<TexArray> tex_arrays;
+    std::vector<unsigned long long> h_tex;   // texture handles staged for the device table
     unsigned long long *dtex = nullptr;   // device [3][nbricks] texture handles by layer axis (0 where absent)
     int32_t tex_axes = 0;                 // bit a set: copy layered along axis a exists (only z is built)
     int64_t tex_bytes = 0;
@@ -110,6 +120,13 @@ struct vrc_ctx {
     cudaEvent_t ev_samples = nullptr;
     // sort-last brick counts of the last render: [traversed, culled] (host)
     std::atomic<int64_t> last_bricks[2] = {{0}, {0}};
+    // caching allocator: device blocks and texture arrays released by freed
+    // cubes and scratch, reused by later allocations of the same size.  `used`
+    // counts live bytes; live + cached bytes never exceed the budget.
+    std::mutex cache_mu;
+    std::multimap<size_t, void *> cached_blocks;       // rounded size -> block
+    std::multimap<uint64_t, TexArray> cached_arrays;   // tex_array_key -> array
+    std::atomic<int64_t> cached{0};
 };
 
 // ------------------------------------------------------------------ helpers
@@ -117,7 +134,11 @@ vrc_status set_err(vrc_ctx *ctx, vrc_status s, const char *fmt, ...);
 vrc_status cuda_err(vrc_ctx *ctx, cudaError_t e, const char *what);
 bool inject_fire(vrc_ctx *ctx, int32_t what);
 vrc_status dev_alloc(vrc_ctx *ctx, void **p, size_t bytes);
-void dev_free(vrc_ctx *ctx, void *p, size_t bytes);
+void dev_free(vrc_ctx *ctx, void *p, size_t bytes);   // the block must be idle (no work in flight uses it)
+bool tex_array_take(vrc_ctx *ctx, uint64_t key, TexArray *a);
+void tex_array_give(vrc_ctx *ctx, uint64_t key, const TexArray &a);   // idle arrays only
+void cache_trim(vrc_ctx *ctx, int64_t keep_bytes);                     // release cached memory down to keep_bytes
+void destroy_tex_array(const TexArray &a);
 vrc_status scratch_get(vrc_ctx *ctx, size_t bytes, void **p);
 Cube *find_cube(vrc_ctx *ctx, int64_t id);
 vrc_status validate_step(vrc_ctx *ctx, const Cube *c, float step);   // at most 2^22 samples per ray

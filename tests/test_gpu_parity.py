@@ -395,3 +395,34 @@ def test_empty_space_skipping_is_exact(ctx, dtype, cube128):
     b = ctx.render_mip(cid, cams, vrc.raycfg(72, 56, 0.5, skip_empty=True)).cpu()
     assert torch.equal(a, b)
     ctx.cube_free(cid)
+
+
+def test_cached_allocations_reused_and_trimmed(cube128):
+    """Freed cubes return their device blocks and render-copy arrays to the
+    context's cache; a cube of the same shape reuses them and renders the same
+    image, and a small budget still admits a differently shaped cube (the
+    cache gives way)."""
+    vrc = vrcmod()
+    c = vrc.Context(0)
+    cams = cubegen.orbit_cameras((128, 128, 128), 2)
+    rc = vrc.raycfg(48, 40, 0.5)
+    cid = c.cube_upload(cube128, "f32", brick=64)
+    assert c.cube_info(cid)["render_copy_bytes"] > 0
+    a = c.render_mip(cid, cams, rc).cpu()
+    d = c.render_dvr(cid, cams, rc, cubegen.tf_dense()).cpu()
+    used = c.memory()[0]
+    c.cube_free(cid)
+    cid = c.cube_upload(cube128, "f32", brick=64)
+    assert torch.equal(a, c.render_mip(cid, cams, rc).cpu())
+    assert torch.equal(d, c.render_dvr(cid, cams, rc, cubegen.tf_dense()).cpu())
+    assert c.memory()[0] == used
+    c.cube_free(cid)
+    c.close()
+    small = vrc.Context(0, hbm_budget_bytes=32 << 20)
+    for brick in (64, 32, 64, 32):
+        sid = small.cube_upload(cube128, "f32", brick=brick)
+        st, _ = small.cube_stats(sid, 16)
+        assert st["n"] == 128 ** 3
+        small.cube_free(sid)
+        assert small.memory()[0] <= 32 << 20
+    small.close()
