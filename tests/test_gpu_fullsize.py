@@ -1,0 +1,105 @@
+"""Parity at full size, in the launch configuration the benchmark times.
+
+The 1024^3 float32 cube of the DVR workload (N(0,1) noise + 2000 Gaussian
+sources, seed 2, 256^3 bricks): the statistics pass with 4096 bins over all
+2^30 voxels against the oracle in full (min/max and every histogram count
+bit-exact, mean/std within 1e-9 relative), and the 32-view 1920x1080 DVR
+orbit rendered in one persistent launch, checked on sampled pixels of every
+view (a random set plus one full row) against the oracle pixel by pixel
+(1e-4 absolute per RGBA channel; termination-fragile pixels inside the
+oracle's bracket).  The empty-space-skipping variant must give the same
+image bit for bit on every pixel.
+"""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import cubegen
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+PIXELS_PER_VIEW = 512
+
+
+@pytest.fixture(scope="module")
+def full():
+    import paper_1111_6661_b300 as vrc
+    w = bench.workload("dvr1024")
+    v, cams, tf = bench.make_inputs(w)
+    ctx = vrc.Context(0)
+    cid = ctx.cube_upload(v, w["storage"], brick=w["brick"])
+    yield w, v, cams, tf, ctx, cid
+    ctx.cube_free(cid)
+    ctx.close()
+
+
+def test_fullsize_stats(full):
+    w, v, cams, tf, ctx, cid = full
+    dstats = torch.empty(8, dtype=torch.float64, device="cuda")
+    dhist = torch.empty(w["nbins"], dtype=torch.int64, device="cuda")
+    ctx.cube_stats_async(cid, w["nbins"], dstats, dhist)
+    torch.cuda.synchronize()
+    s = dstats.cpu().numpy()
+    n = dstats.cpu().view(torch.int64).numpy()[4:6]
+    ref = oracle.stats(v)
+    assert int(n[0]) == ref["n"] == v.size and int(n[1]) == 0
+    assert s[0] == ref["min"] and s[1] == ref["max"]
+    assert abs(s[2] - ref["mean"]) <= 1e-9 * max(abs(ref["mean"]), ref["std"]), (s[2], ref["mean"])
+    assert abs(s[3] - ref["std"]) <= 1e-9 * ref["std"], (s[3], ref["std"])
+    h = oracle.histogram(v, ref["min"], ref["max"], w["nbins"])
+    assert np.array_equal(dhist.cpu().numpy().astype(np.uint64), h)
+    assert int(h.sum()) == v.size
+
+
+def test_fullsize_dvr_orbit(full):
+    import paper_1111_6661_b300 as vrc
+    w, v, cams, tf, ctx, cid = full
+    info = ctx.cube_info(cid)
+    W, H = w["W"], w["H"]
+    rc = vrc.raycfg(W, H, w["step"], "trilinear")
+    out = torch.empty((len(cams), H, W, 4), dtype=torch.float32, device="cuda")
+    ctx.render_dvr(cid, cams, rc, tf, w["term"], out=out)
+    torch.cuda.synchronize()
+    assert ctx.last_render_samples() > 0
+    rng = np.random.default_rng(12)
+    img = out.cpu().numpy().reshape(len(cams), -1, 4).astype(np.float64)
+    nonzero = 0
+    for i, cam in enumerate(cams):
+        row = int(rng.integers(0, H))
+        pix = np.unique(np.concatenate([rng.choice(W * H, size=PIXELS_PER_VIEW, replace=False),
+                                        row * W + np.arange(W)]))
+        r = oracle.render(v, cam, W, H, w["step"], "trilinear", "dvr", tf=tf, vmin=info["vmin"],
+                          vmax=info["vmax"], term=w["term"], pixels=pix)
+        got = img[i, pix]
+        d = np.abs(got - r["out"]).max(axis=1)
+        ok = d <= 1e-4
+        inside = np.all((got >= r["lo"] - 1e-4) & (got <= r["hi"] + 1e-4), axis=1)
+        ok |= r["fragile"] & inside
+        assert ok.all(), (i, int((~ok).sum()), float(d.max()))
+        assert r["fragile"].mean() < 0.05
+        nonzero += int((r["out"][:, 3] > 0).sum())
+    assert nonzero > 0   # the sampled pixels see sources, not only background
+
+    # empty-space skipping: the same image, bit for bit, on every pixel of every view
+    out2 = torch.empty_like(out)
+    ctx.render_dvr(cid, cams, vrc.raycfg(W, H, w["step"], "trilinear", skip_empty=True), tf, w["term"], out=out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
+
+
+def test_fullsize_trilinear_mip(full):
+    import paper_1111_6661_b300 as vrc
+    w, v, cams, tf, ctx, cid = full
+    W, H = w["W"], w["H"]
+    views = [cams[0], cams[11]]
+    img = ctx.render_mip(cid, views, vrc.raycfg(W, H, w["step"], "trilinear"))
+    torch.cuda.synchronize()
+    got = img.cpu().numpy().reshape(len(views), -1).astype(np.float64)
+    rng = np.random.default_rng(13)
+    for i, cam in enumerate(views):
+        pix = rng.choice(W * H, size=PIXELS_PER_VIEW, replace=False)
+        r = oracle.render(v, cam, W, H, w["step"], "trilinear", "mip", pixels=pix)
+        err = np.abs(got[i, pix] - r["out"]) / np.maximum(np.abs(r["out"]), 1.0)
+        assert err.max() <= 1e-5, (i, err.max())
