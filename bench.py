@@ -260,7 +260,7 @@ def run_gpu(args, w):
     st = torch.cuda.current_stream()
     cid = ctx.cube_upload(v, w["storage"], brick=w["brick"])
     info = ctx.cube_info(cid)
-    rc = vrc.raycfg(w["W"], w["H"], w["step"], "trilinear")
+    rc = vrc.raycfg(w["W"], w["H"], w["step"], "trilinear", path=args.path)
     out = torch.empty((len(cams), w["H"], w["W"], 4), dtype=torch.float32, device=dev)
     dstats = torch.empty(8, dtype=torch.float64, device=dev)
     dhist = torch.empty(w["nbins"], dtype=torch.int64, device=dev)
@@ -648,6 +648,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-skip-variant", action="store_true")
+    ap.add_argument("--path", default="fused", choices=["fused", "slab"], help="render path of the timed step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
     ap.add_argument("--dims", type=int, nargs=3, default=None, help="precision/ooc: cube dims")
@@ -671,6 +672,11 @@ def main():
     w = workload(args.workload)
     if args.views:
         w["views"] = args.views
+    if args.dims:   # profiling: a smaller cube of the same recipe (sources scaled with the volume)
+        scale = args.dims[0] * args.dims[1] * args.dims[2] / float(np.prod(w["dims"]))
+        w["dims"] = tuple(args.dims)
+        w["n_sources"] = max(1, int(round(w["n_sources"] * scale)))
+        w["name"] = w["name"] + "-dims%dx%dx%d" % tuple(args.dims)
     if args.impl == "reference":
         run_reference(args, w)
     else:

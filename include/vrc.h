@@ -85,6 +85,11 @@ typedef struct {
 #define VRC_PATH_FUSED_LDG 2   /* fused, trilinear samples by 8 global loads (no textures) */
 #define VRC_PATH_ZEROCOPY  3   /* streamed cubes: the sort-last kernels read the bricks in place
                                   from mapped pinned host memory (no copies, no device ring) */
+#define VRC_PATH_SLAB      4   /* resident float32 cubes, trilinear: each 16x16 ray tile marches
+                                  through the cube in slabs; the region its samples touch is
+                                  staged in shared memory by TMA from a clamp-to-edge copy of
+                                  the cube (built on first use, counted against the budget).
+                                  Same image as VRC_PATH_FUSED, bit for bit */
 typedef struct {
     int32_t width, height;     /* image size in pixels (1..16384) */
     float step;                /* sample spacing along the unit ray, voxel units (> 0, and
@@ -92,8 +97,8 @@ typedef struct {
     int32_t sampling;          /* VRC_NEAREST or VRC_TRILINEAR */
     int32_t opacity_correction;/* DVR: 0 = alpha as in the transfer function,
                                   1 = 1-(1-alpha)^step */
-    int32_t path;              /* VRC_PATH_FUSED, VRC_PATH_SORTLAST, VRC_PATH_FUSED_LDG or
-                                  VRC_PATH_ZEROCOPY (streamed cubes only) */
+    int32_t path;              /* VRC_PATH_FUSED, VRC_PATH_SORTLAST, VRC_PATH_FUSED_LDG,
+                                  VRC_PATH_ZEROCOPY (streamed cubes only) or VRC_PATH_SLAB */
     int32_t tile_w, tile_h;    /* ray tile; 0,0 = tuned default.  tile_w*tile_h = 256,
                                   tile_w in {8,16,32} */
     int32_t skip_empty;        /* 1 = skip work that cannot change the image; the
@@ -283,7 +288,10 @@ vrc_status vrc_render_dvr(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams,
  * context: *samples = lattice samples inside the cube up to early termination
  * (the work the method defines); *evaluated = samples actually fetched and
  * composited (smaller only with skip_empty; may be NULL).  Waits for that
- * render to finish.  Outputs are HOST memory.
+ * render to finish.  Outputs are HOST memory.  VRC_E_TIMEOUT (counts still
+ * written) if a bounded device-side wait of that render gave up (VRC_PATH_SLAB:
+ * a shared-memory staging copy that did not complete within 0.5 s); its image
+ * is then unspecified.
  */
 vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *evaluated);
 

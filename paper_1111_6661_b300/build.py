@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libvrc.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["ctx.cu", "pack.cu", "stats.cu", "render.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["ctx.cu", "pack.cu", "stats.cu", "render.cu", "serve.cu", "noalloc.cu", "slab.cu"]
 HEADERS = ["vrc_internal.h", "ray.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

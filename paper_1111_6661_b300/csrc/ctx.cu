@@ -287,14 +287,14 @@ vrc_status vrc_create(vrc_ctx **out, const vrc_config *cfg)
     ctx->cfg = c;
     ctx->budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : (int64_t)(0.9 * (double)freeb);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, c.device);
-    if (cudaHostAlloc(&ctx->h_samples, 2 * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess ||
+    if (cudaHostAlloc(&ctx->h_samples, 4 * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_samples, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->h_samples) cudaFreeHost(ctx->h_samples);
         delete ctx;
         return VRC_E_CUDA;
     }
-    ctx->h_samples[0] = ctx->h_samples[1] = 0;
+    ctx->h_samples[0] = ctx->h_samples[1] = ctx->h_samples[2] = 0;
     *out = ctx;
     return VRC_OK;
 }
@@ -345,6 +345,7 @@ vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *ev
     VRC_CK(ctx, cudaEventSynchronize(ctx->ev_samples));
     *samples = ctx->h_samples[0];
     if (evaluated) *evaluated = ctx->h_samples[1];
+    if (ctx->h_samples[2]) return set_err(ctx, VRC_E_TIMEOUT, "a device-side wait of the last render gave up");
     return VRC_OK;
 }
 

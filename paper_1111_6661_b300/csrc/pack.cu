@@ -435,6 +435,7 @@ void release_cube(vrc_ctx *ctx, Cube *c)
     // once: no launch still in flight may read it
     cudaDeviceSynchronize();
     release_textures(ctx, c);
+    slab_release(ctx, c);
     if (c->pool) dev_free(ctx, c->pool, g.nbricks * g.brick_bytes);
     if (c->ring_pool) dev_free(ctx, c->ring_pool, (size_t)c->ring * g.brick_bytes);
     if (c->scales) dev_free(ctx, c->scales, g.nbricks * 4);

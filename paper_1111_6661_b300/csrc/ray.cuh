@@ -274,3 +274,63 @@ __device__ __forceinline__ float opacity(float a, float step, int correct)
 {
     return correct ? 1.f - __powf(fmaxf(1.f - a, 0.f), step) : a;
 }
+
+// ------------------------------------------------------------------ work items
+
+// Thread -> pixel inside a tile_w x tile_h tile: warps cover ww x (32/ww)
+// pixel blocks (ww a power of two dividing tile_w).
+__device__ __forceinline__ void tile_pixel(int tile_w, int ww, int &lx, int &ly)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wx = tile_w / ww, wh = 32 / ww;
+    lx = (warp % wx) * ww + (lane % ww);
+    ly = (warp / wx) * wh + (lane / ww);
+}
+
+// Tile t of a view, in strips of kSuper tile rows walked kSuper tile columns
+// at a time: the tiles in flight at any moment cover a compact patch of the
+// image, so their rays cross a narrow part of the cube (cache and TLB reach).
+// Measured against row-major order: +0.4% on a 1024^3 cube, +2.5% on a
+// 2048x2048x4096 cube (kSuper 4 and 8 in between).
+constexpr int kSuper = 16;
+__device__ __forceinline__ void tile_of(const JobDesc &J, int64_t t, int &tx, int &ty)
+{
+    if (kSuper <= 1) {
+        tx = (int)(t % J.tiles_x);
+        ty = (int)(t / J.tiles_x);
+        return;
+    }
+    const int64_t strip_tiles = (int64_t)kSuper * J.tiles_x;
+    const int strip = (int)(t / strip_tiles);
+    const int r = (int)(t - strip * strip_tiles);
+    const int h = min(kSuper, J.tiles_y - strip * kSuper);    // tile rows in this strip
+    const int nblk = (J.tiles_x + kSuper - 1) / kSuper;
+    const int cb = min(r / (kSuper * h), nblk - 1);
+    const int rr = r - cb * kSuper * h;
+    const int w = cb == nblk - 1 ? J.tiles_x - cb * kSuper : kSuper;   // tile columns in this block
+    ty = strip * kSuper + rr / w;
+    tx = cb * kSuper + rr % w;
+}
+
+__device__ __forceinline__ int find_job(const JobDesc *jobs, int n_jobs, int64_t item)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item_begin <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void warp_count2(unsigned long long *counters, uint32_t lattice, uint32_t evaluated)
+{
+    for (int o = 16; o; o >>= 1) {
+        lattice += __shfl_xor_sync(0xffffffffu, lattice, o);
+        evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lattice) atomicAdd(counters, (unsigned long long)lattice);
+        if (evaluated) atomicAdd(counters + 1, (unsigned long long)evaluated);
+    }
+}

@@ -16,64 +16,6 @@ constexpr int kThreads = 256;
 
 // ------------------------------------------------------------------ kernels
 
-// Thread -> pixel inside a tile_w x tile_h tile: warps cover ww x (32/ww)
-// pixel blocks (ww a power of two dividing tile_w).
-__device__ __forceinline__ void tile_pixel(int tile_w, int ww, int &lx, int &ly)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wx = tile_w / ww, wh = 32 / ww;
-    lx = (warp % wx) * ww + (lane % ww);
-    ly = (warp / wx) * wh + (lane / ww);
-}
-
-// Tile t of a view, in strips of kSuper tile rows walked kSuper tile columns
-// at a time: the tiles in flight at any moment cover a compact patch of the
-// image, so their rays cross a narrow part of the cube (cache and TLB reach).
-// Measured against row-major order: +0.4% on a 1024^3 cube, +2.5% on a
-// 2048x2048x4096 cube (kSuper 4 and 8 in between).
-constexpr int kSuper = 16;
-__device__ __forceinline__ void tile_of(const JobDesc &J, int64_t t, int &tx, int &ty)
-{
-    if (kSuper <= 1) {
-        tx = (int)(t % J.tiles_x);
-        ty = (int)(t / J.tiles_x);
-        return;
-    }
-    const int64_t strip_tiles = (int64_t)kSuper * J.tiles_x;
-    const int strip = (int)(t / strip_tiles);
-    const int r = (int)(t - strip * strip_tiles);
-    const int h = min(kSuper, J.tiles_y - strip * kSuper);    // tile rows in this strip
-    const int nblk = (J.tiles_x + kSuper - 1) / kSuper;
-    const int cb = min(r / (kSuper * h), nblk - 1);
-    const int rr = r - cb * kSuper * h;
-    const int w = cb == nblk - 1 ? J.tiles_x - cb * kSuper : kSuper;   // tile columns in this block
-    ty = strip * kSuper + rr / w;
-    tx = cb * kSuper + rr % w;
-}
-
-__device__ __forceinline__ int find_job(const JobDesc *jobs, int n_jobs, int64_t item)
-{
-    int lo = 0, hi = n_jobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].item_begin <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void warp_count2(unsigned long long *counters, uint32_t lattice, uint32_t evaluated)
-{
-    for (int o = 16; o; o >>= 1) {
-        lattice += __shfl_xor_sync(0xffffffffu, lattice, o);
-        evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (lattice) atomicAdd(counters, (unsigned long long)lattice);
-        if (evaluated) atomicAdd(counters + 1, (unsigned long long)evaluated);
-    }
-}
-
 // One ray of the fused path: all samples in ray order, each read from the
 // brick that contains it (per-brick segments are composited in registers).
 // TEXAXIS < 0: trilinear/nearest from the packed bricks with global loads;
@@ -606,7 +548,7 @@ vrc_status check_rc(vrc_ctx *ctx, const vrc_raycfg *rc)
     if (rc->sampling != VRC_NEAREST && rc->sampling != VRC_TRILINEAR) return set_err(ctx, VRC_E_INVAL, "bad sampling");
     if (rc->opacity_correction != 0 && rc->opacity_correction != 1) return set_err(ctx, VRC_E_INVAL, "bad opacity flag");
     if (rc->path != VRC_PATH_FUSED && rc->path != VRC_PATH_SORTLAST && rc->path != VRC_PATH_FUSED_LDG &&
-        rc->path != VRC_PATH_ZEROCOPY)
+        rc->path != VRC_PATH_ZEROCOPY && rc->path != VRC_PATH_SLAB)
         return set_err(ctx, VRC_E_INVAL, "bad path");
     if ((rc->skip_empty != 0 && rc->skip_empty != 1) || rc->reserved != 0)
         return set_err(ctx, VRC_E_INVAL, "bad skip_empty/reserved");
@@ -996,6 +938,13 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     }
     if (rc->path == VRC_PATH_ZEROCOPY && !c->streamed)
         return set_err(ctx, VRC_E_UNSUPPORTED, "zero-copy rendering is for streamed cubes");
+    const bool slab = rc->path == VRC_PATH_SLAB;
+    if (slab) {
+        if (!slab_supported(c) || rc->sampling != VRC_TRILINEAR || rc->skip_empty)
+            return set_err(ctx, VRC_E_UNSUPPORTED, "slab path: resident float32 cubes, trilinear, no skip_empty");
+        if ((s = slab_prepare(ctx, c, st)) != VRC_OK) return s;
+        for (auto &j : jobs) j.warp_w = 8;   // 8x4-pixel warps: compact footprints in the staged box
+    }
     const bool zerocopy = rc->path == VRC_PATH_ZEROCOPY;
     const bool sortlast = c->streamed || rc->path == VRC_PATH_SORTLAST;
     if (!sortlast && !c->pool) return set_err(ctx, VRC_E_UNSUPPORTED, "cube has no resident bricks");
@@ -1014,7 +963,7 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     if ((s = scratch_get(ctx, need, &scr)) != VRC_OK) return s;
     Arena ar{(char *)scr, 0, need};
     int *counter = ar.take<int>(1);
-    unsigned long long *dsamples = ar.take<unsigned long long>(2);
+    unsigned long long *dsamples = ar.take<unsigned long long>(3);   // lattice, evaluated, wait failure
     float4 *dtf = ar.take<float4>(256);
     JobDesc *djobs = ar.take<JobDesc>(n_views);
     for (auto &j : jobs) {
@@ -1022,10 +971,17 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         j.samples = dsamples;
         j.skip_below = thr;
     }
-    VRC_CK(ctx, cudaMemsetAsync(dsamples, 0, 2 * sizeof(unsigned long long), st));
+    VRC_CK(ctx, cudaMemsetAsync(dsamples, 0, 3 * sizeof(unsigned long long), st));
     if (mode == 1) VRC_CK(ctx, cudaMemcpyAsync(dtf, tf_rgba, 1024 * 4, cudaMemcpyHostToDevice, st));
     VRC_CK(ctx, cudaMemcpyAsync(djobs, jobs.data(), sizeof(JobDesc) * n_views, cudaMemcpyHostToDevice, st));
-    if (!sortlast) {
+    if (slab) {
+        VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
+        const int per_sm = ctas_override > 0 ? ctas_override : slab_occupancy(mode);
+        const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
+        slab_launch(c, mode, grid, st, djobs, n_views, total, counter, reinterpret_cast<int *>(dsamples + 2));
+        count_launch(ctx);
+        VRC_CK(ctx, cudaGetLastError());
+    } else if (!sortlast) {
         VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
         const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
         const bool skip = tex && jobs[0].cellmax != nullptr;
@@ -1076,7 +1032,7 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         VRC_CK(ctx, cudaMemcpyAsync(samples_out, dsamples, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         if (host_sync_samples) VRC_CK(ctx, cudaStreamSynchronize(st));
     } else {
-        VRC_CK(ctx, cudaMemcpyAsync(ctx->h_samples, dsamples, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        VRC_CK(ctx, cudaMemcpyAsync(ctx->h_samples, dsamples, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         VRC_CK(ctx, cudaEventRecord(ctx->ev_samples, st));
     }
     return VRC_OK;
@@ -1254,7 +1210,7 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     Cube *c = nullptr;
     vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c);
     if (s != VRC_OK) return s;
-    if (c->streamed || rc->path == VRC_PATH_SORTLAST)
+    if (c->streamed || rc->path == VRC_PATH_SORTLAST || rc->path == VRC_PATH_SLAB)
         return set_err(ctx, VRC_E_UNSUPPORTED, "graphs capture the fused path of resident cubes");
     const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
     VRC_CK(ctx, cudaSetDevice(ctx->device));
@@ -1268,7 +1224,7 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     if ((s = dev_alloc(ctx, &mem, bytes)) != VRC_OK) return s;
     Arena ar{(char *)mem, 0, bytes};
     int *counter = ar.take<int>(1);
-    unsigned long long *dsamples = ar.take<unsigned long long>(2);
+    unsigned long long *dsamples = ar.take<unsigned long long>(3);   // lattice, evaluated, wait failure
     float4 *dtf = ar.take<float4>(256);
     JobDesc *djobs = ar.take<JobDesc>(n_views);
     const float thr = mode ? transparent_below(c, tf_rgba) : -INFINITY;

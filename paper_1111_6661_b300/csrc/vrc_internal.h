@@ -87,6 +87,11 @@ struct Cube {
     // read from the brick that owns the cell (empty-space skipping)
     float *cellmax = nullptr;
     int32_t ncell[3] = {0, 0, 0};
+    // slab renderer (float32 resident cubes): clamp-to-edge halo copy, dims + 2 on
+    // every axis, rows of halo_pitch elements, and its three TMA tensor maps
+    float *halo = nullptr;
+    int64_t halo_bytes = 0, halo_pitch = 0;
+    alignas(64) unsigned char slab_maps[3 * 128];
     // tuning (0 = default)
     int32_t tile_w = 0, tile_h = 0, ctas_per_sm = 0;
     std::atomic<int> refs{0};
@@ -115,7 +120,8 @@ struct vrc_ctx {
     int64_t inj_left = 0;
     Server *server = nullptr;
     std::mutex srv_mu;
-    // sample counts of the last render: [lattice, evaluated] (pinned host words + completion event)
+    // sample counts of the last render: [lattice, evaluated, device-wait failure]
+    // (pinned host words + completion event)
     unsigned long long *h_samples = nullptr;
     cudaEvent_t ev_samples = nullptr;
     // sort-last brick counts of the last render: [traversed, culled] (host)
@@ -181,3 +187,12 @@ size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs);
 size_t render_hetero_stage_bytes(size_t n_jobs);
 
 void server_stop(vrc_ctx *ctx);
+
+// Slab renderer (slab.cu).
+struct JobDesc;
+bool slab_supported(const Cube *c);
+vrc_status slab_prepare(vrc_ctx *ctx, Cube *c, cudaStream_t st);
+void slab_release(vrc_ctx *ctx, Cube *c);
+int slab_occupancy(int mode);
+void slab_launch(const Cube *c, int mode, int grid, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total,
+                 int *counter, int *err);

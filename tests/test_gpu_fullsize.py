@@ -7,8 +7,8 @@ bit-exact, mean/std within 1e-9 relative), and the 32-view 1920x1080 DVR
 orbit rendered in one persistent launch, checked on sampled pixels of every
 view (a random set plus one full row) against the oracle pixel by pixel
 (1e-4 absolute per RGBA channel; termination-fragile pixels inside the
-oracle's bracket).  The empty-space-skipping variant must give the same
-image bit for bit on every pixel.
+oracle's bracket).  The empty-space-skipping variant and the slab march must
+give the same image bit for bit on every pixel.
 """
 import numpy as np
 import pytest
@@ -82,11 +82,16 @@ def test_fullsize_dvr_orbit(full):
         nonzero += int((r["out"][:, 3] > 0).sum())
     assert nonzero > 0   # the sampled pixels see sources, not only background
 
-    # empty-space skipping: the same image, bit for bit, on every pixel of every view
-    out2 = torch.empty_like(out)
-    ctx.render_dvr(cid, cams, vrc.raycfg(W, H, w["step"], "trilinear", skip_empty=True), tf, w["term"], out=out2)
-    torch.cuda.synchronize()
-    assert torch.equal(out, out2)
+    # empty-space skipping and the slab march: the same image, bit for bit, on
+    # every pixel of every view
+    n_fused = ctx.last_render_samples()
+    for rc2 in (vrc.raycfg(W, H, w["step"], "trilinear", skip_empty=True),
+                vrc.raycfg(W, H, w["step"], "trilinear", path="slab")):
+        out2 = torch.empty_like(out)
+        ctx.render_dvr(cid, cams, rc2, tf, w["term"], out=out2)
+        torch.cuda.synchronize()
+        assert torch.equal(out, out2)
+        assert ctx.last_render_samples() == n_fused
 
 
 def test_fullsize_trilinear_mip(full):

@@ -426,3 +426,91 @@ def test_cached_allocations_reused_and_trimmed(cube128):
         small.cube_free(sid)
         assert small.memory()[0] <= 32 << 20
     small.close()
+
+
+# ------------------------------------------------------------------ slab path
+def axis_cameras(dims):
+    """Views whose rays run mainly along +-x, +-y and +-z (every principal
+    axis and direction of the slab march), perspective and orthographic, and
+    one with the eye inside the cube."""
+    nx, ny, nz = dims
+    c = (nx / 2, ny / 2, nz / 2)
+    d = 2.5 * max(dims)
+    cams = []
+    for a in range(3):
+        for sgn in (1, -1):
+            eye = list(c)
+            eye[a] += sgn * d
+            eye[(a + 1) % 3] += 0.21 * d   # a little off-axis
+            up = (0.0, 0.0, 1.0) if a == 1 else (0.0, 1.0, 0.0)
+            cams.append(cubegen.camera("persp", eye, c, up, fovy_deg=30))
+    cams.append(cubegen.camera("ortho", (c[0] + 0.3, c[1] - 0.2, -d), c, (0, 1, 0), ortho_height=1.3 * ny))
+    cams.append(cubegen.camera("persp", (0.6 * nx, 0.45 * ny, 0.5 * nz), (0, 0, 0), (0, 1, 0), fovy_deg=80))
+    return cams
+
+
+@pytest.mark.parametrize("mode", ["mip", "dvr"])
+def test_slab_path_matches_oracle_and_fused(ctx, mode, cube128):
+    """The slab march (tiles staged in shared memory by TMA) against the
+    oracle at the stated tolerances, and bit-identical to the fused texture
+    renderer, on a ragged cube, for every principal axis and direction."""
+    v = cube128[:70, :50, :90].copy()
+    dims = (90, 50, 70)
+    cid = ctx.cube_upload(v, "f32", brick=32)
+    cams = axis_cameras(dims) + cubegen.orbit_cameras(dims, 3) + cubegen.random_cameras(dims, 3, 17)
+    W, H = 75, 53   # ragged against the 16x16 tiles
+    if mode == "mip":
+        a = render_check_mip(ctx, v, cid, cams, W, H, 0.5, "trilinear", path="slab")
+        n_slab = ctx.last_render_samples()
+        b = render_check_mip(ctx, v, cid, cams, W, H, 0.5, "trilinear", path="fused")
+        assert np.array_equal(a, b)
+    else:
+        tf = cubegen.tf_dense()
+        a = render_check_dvr(ctx, v, cid, cams, W, H, 0.5, tf, path="slab")
+        n_slab = ctx.last_render_samples()
+        b = render_check_dvr(ctx, v, cid, cams, W, H, 0.5, tf, path="fused")
+        assert np.array_equal(a, b)
+    assert n_slab == ctx.last_render_samples()
+    ctx.cube_free(cid)
+
+
+def test_slab_path_large_tiles_and_steps(ctx, cube128):
+    """Bigger cube than one staged box in every direction, coarse and fine
+    steps, sparse TF with early termination off and on."""
+    vrc = vrcmod()
+    cid = ctx.cube_upload(cube128, "f32", brick=64)
+    dims = (128, 128, 128)
+    cams = axis_cameras(dims)[:4] + cubegen.orbit_cameras(dims, 2)
+    for step, tf, term in [(0.37, cubegen.tf_sparse(), 0.99), (1.0, cubegen.tf_dense(), 2.0),
+                           (0.5, cubegen.tf_random(5), 0.99)]:
+        rc_s = vrc.raycfg(96, 80, step, "trilinear", path="slab")
+        rc_f = vrc.raycfg(96, 80, step, "trilinear", path="fused")
+        a = ctx.render_dvr(cid, cams, rc_s, tf, term)
+        b = ctx.render_dvr(cid, cams, rc_f, tf, term)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), step
+    got = a.cpu().numpy().reshape(len(cams), -1, 4).astype(np.float64)
+    info = ctx.cube_info(cid)
+    rng = np.random.default_rng(3)
+    for i in (0, 5):
+        pix = rng.choice(96 * 80, size=600, replace=False)
+        r = oracle.render(cube128, cams[i], 96, 80, 0.5, "trilinear", "dvr", tf=cubegen.tf_random(5),
+                          vmin=info["vmin"], vmax=info["vmax"], term=0.99, pixels=pix)
+        check_dvr(got[i, pix], r)
+    ctx.cube_free(cid)
+
+
+def test_slab_path_rejects_what_it_does_not_cover(ctx, cube128):
+    vrc = vrcmod()
+    v = cube128[:32, :32, :32].copy()
+    cam = cubegen.orbit_cameras((32, 32, 32), 1)
+    cid = ctx.cube_upload(v, "bf16", brick=16)
+    with pytest.raises(vrc.VrcError):
+        ctx.render_mip(cid, cam, vrc.raycfg(16, 16, 0.5, "trilinear", path="slab"))
+    ctx.cube_free(cid)
+    cid = ctx.cube_upload(v, "f32", brick=16)
+    for rc in (vrc.raycfg(16, 16, 0.5, "nearest", path="slab"),
+               vrc.raycfg(16, 16, 0.5, "trilinear", path="slab", skip_empty=True)):
+        with pytest.raises(vrc.VrcError):
+            ctx.render_mip(cid, cam, rc)
+    ctx.cube_free(cid)
