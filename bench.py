@@ -354,38 +354,50 @@ def run_gpu(args, w):
         ctx.cube_free(cid)
         cid = None
         torch.cuda.synchronize()
-        cubes = []
-        t0 = time.perf_counter()
-        nxt = ctx.cube_upload(vt, w["storage"], brick=w["brick"], stream=s_up)
-        for i in range(e2e_steps):
-            cur = nxt
-            cubes.append(cur)
+        def issue_step(i, cube):
             b = i % 2
             if i >= 2:
                 s_rd.wait_event(copied[b])          # images and statistics of step i-2 are back on the host
-            ctx.cube_stats_async(cur, w["nbins"], dst[b], dhi[b], stream=s_rd)
-            ctx.render_dvr(cur, cams, rc, tf, w["term"], out=outs[b], stream=s_rd)
+            ctx.cube_stats_async(cube, w["nbins"], dst[b], dhi[b], stream=s_rd)
+            ctx.render_dvr(cube, cams, rc, tf, w["term"], out=outs[b], stream=s_rd)
             rendered[b].record(s_rd)
+
+        # Order of host calls: step i+1 is issued before step i's images are
+        # copied back.  A render's small input tables are read from host memory
+        # by the device; such reads wait behind an image download in flight to
+        # host memory, so they go first.
+        t0 = time.perf_counter()
+        cubes = [ctx.cube_upload(vt, w["storage"], brick=w["brick"], stream=s_up)]
+        issue_step(0, cubes[0])
+        if e2e_steps > 1:
+            cubes.append(ctx.cube_upload(vt, w["storage"], brick=w["brick"], stream=s_up))
+        for i in range(e2e_steps):
+            b = i % 2
+            if i + 1 < e2e_steps:
+                issue_step(i + 1, cubes[i + 1])
             s_dn.wait_event(rendered[b])
             with torch.cuda.stream(s_dn):
                 host_img[b].copy_(outs[b], non_blocking=True)
                 host_stats.copy_(dst[b], non_blocking=True)
                 host_hist.copy_(dhi[b], non_blocking=True)
             copied[b].record(s_dn)
-            if i + 1 < e2e_steps:
-                nxt = ctx.cube_upload(vt, w["storage"], brick=w["brick"], stream=s_up)
+            # every read of cube i is ordered before the copies on s_dn: release
+            # it there, so a later upload reuses its memory without a device wait
+            ctx.cube_free_async(cubes[i], stream=s_dn)
+            if i + 2 < e2e_steps:
+                # its host-to-device copy overlaps the render of step i+1
+                cubes.append(ctx.cube_upload(vt, w["storage"], brick=w["brick"], stream=s_up))
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-        for c in cubes:
-            ctx.cube_free(c)
         e2e_s = barrier_max(e2e_s, ws)
         e2e = {"value": ws * samples_per_step / e2e_s, "unit": "samples/s",
                "h2d_bytes_per_step": int(v.nbytes + 4096 + 48 * len(cams)),
                "d2h_bytes_per_step": int(host_img[0].numel() * 4 + 8 * w["nbins"] + 64),
                "ms_per_step": 1e3 * e2e_s, "steps": e2e_steps,
-               "pipeline": "upload of step i+1 overlaps the render of step i; images of step i copied back "
-                           "while step i+1 renders; timed from the first upload to the last image on the host "
-                           "(fill and drain included); cubes freed after the timed region"}
+               "pipeline": "upload of step i+2 overlaps the render of step i+1; images of step i copied back "
+                           "while step i+1 renders; each cube released in stream order after its images "
+                           "(vrc_cube_free_async), so uploads reuse its memory; timed from the first upload to "
+                           "the last image on the host (fill and drain included)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

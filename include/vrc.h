@@ -196,8 +196,21 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
  */
 vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const float *brick_with_halo);
 
-/* Release a cube.  VRC_E_BUSY while serving requests still reference it. */
+/* Release a cube.  Waits for the device (the memory may be reused at once).
+ * VRC_E_BUSY while serving requests still reference it. */
 vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id);
+
+/*
+ * Release a cube without waiting for the device.  The caller guarantees that
+ * every piece of work that reads the cube was issued on `stream`, or before
+ * work already issued on `stream` (stream order, e.g. through events).  The id
+ * is invalid on return; the cube's memory goes back to the context's cache
+ * when the work issued on `stream` so far has completed, and a later upload
+ * of the same shape reuses it without new device allocations.  Errors:
+ * VRC_E_BADID, VRC_E_BUSY (serving requests reference the cube; nothing is
+ * released), VRC_E_CUDA (the cube was released after a device-wide wait).
+ */
+vrc_status vrc_cube_free_async(vrc_ctx *ctx, int64_t cube_id, void *stream);
 
 /* dims, brick edge, storage dtype, brick count, stored bytes, the stored
  * min/max recorded at upload, and the bytes of the texture render copies

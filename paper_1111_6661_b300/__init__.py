@@ -133,6 +133,10 @@ class Context:
     def cube_free(self, cube_id: int):
         self._check(self._lib.vrc_cube_free(self.h, cube_id))
 
+    def cube_free_async(self, cube_id: int, stream=None):
+        """Release once the work issued on `stream` so far has completed."""
+        self._check(self._lib.vrc_cube_free_async(self.h, cube_id, _stream_ptr(stream)))
+
     def cube_info(self, cube_id: int) -> dict:
         dims = (ctypes.c_int64 * 3)()
         B, st, nb, by = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <iterator>
 
+#include <cstring>
+
 #include "vrc_internal.h"
 
 vrc_status set_err(vrc_ctx *ctx, vrc_status s, const char *fmt, ...)
@@ -74,15 +76,116 @@ void cache_trim(vrc_ctx *ctx, int64_t keep_bytes)
     }
 }
 
+// Cubes released by vrc_cube_free_async whose event has completed (all of
+// them, waiting, if `wait`) give their memory to the cache.
+bool reap_pending(vrc_ctx *ctx, bool wait)
+{
+    std::vector<std::pair<cudaEvent_t, Cube *>> done;
+    {
+        std::lock_guard<std::mutex> lk(ctx->pend_mu);
+        for (auto it = ctx->pending.begin(); it != ctx->pending.end();) {
+            const cudaError_t q = wait ? cudaEventSynchronize(it->first) : cudaEventQuery(it->first);
+            if (q == cudaErrorNotReady) {
+                ++it;
+                continue;
+            }
+            if (q != cudaSuccess) cudaGetLastError();   // a failed stream: its work is over all the same
+            done.push_back(*it);
+            it = ctx->pending.erase(it);
+        }
+    }
+    for (auto &d : done) {
+        cudaEventDestroy(d.first);
+        release_cube(ctx, d.second, false);
+    }
+    return !done.empty();
+}
+
+namespace {
+constexpr int kStageMax = 8;
+struct StageArgs {
+    int n;
+    uint32_t *dst[kStageMax];
+    const uint32_t *src[kStageMax];   // mapped pinned host memory, or null: zero fill
+    uint32_t words[kStageMax];
+};
+__global__ void k_stage(StageArgs a)
+{
+    for (int i = 0; i < a.n; ++i)
+        for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.words[i]; w += gridDim.x * blockDim.x)
+            a.dst[i][w] = a.src[i] ? a.src[i][w] : 0u;
+}
+
+vrc_status slot_alloc(vrc_ctx *ctx, vrc_ctx::PinnedSlot &s, size_t cap)
+{
+    if (s.p) cudaFreeHost(s.p);
+    s.p = s.dp = nullptr;
+    s.cap = 0;
+    VRC_CK(ctx, cudaHostAlloc((void **)&s.p, cap, cudaHostAllocMapped));
+    VRC_CK(ctx, cudaHostGetDevicePointer((void **)&s.dp, s.p, 0));
+    s.cap = cap;
+    return VRC_OK;
+}
+}  // namespace
+
+vrc_status stage_h2d(vrc_ctx *ctx, cudaStream_t st, const std::vector<H2DCopy> &copies)
+{
+    size_t total = 0;
+    for (const H2DCopy &c : copies) {
+        if (c.bytes % 4) return set_err(ctx, VRC_E_INVAL, "staged copy of %zu bytes", c.bytes);
+        if (c.src) total += (c.bytes + 255) & ~(size_t)255;
+    }
+    std::lock_guard<std::mutex> lk(ctx->stage_mu);
+    vrc_ctx::PinnedSlot &s = ctx->stage[ctx->stage_next];
+    ctx->stage_next = (ctx->stage_next + 1) % 4;
+    if (!s.ev) VRC_CK(ctx, cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+    VRC_CK(ctx, cudaEventSynchronize(s.ev));   // this slot's previous contents have been read
+    if (s.cap < total) {
+        const vrc_status r = slot_alloc(ctx, s, std::max<size_t>(total, (size_t)256 << 10));
+        if (r != VRC_OK) return r;
+    }
+    StageArgs a = {};
+    size_t off = 0, most = 0;
+    for (const H2DCopy &c : copies) {
+        if (!c.bytes) continue;
+        if (a.n == kStageMax) {
+            k_stage<<<(unsigned)std::min<size_t>((most + 1023) / 1024, 256), 256, 0, st>>>(a);
+            count_launch(ctx);
+            a = StageArgs{};
+            most = 0;
+        }
+        a.dst[a.n] = static_cast<uint32_t *>(c.dst);
+        a.src[a.n] = nullptr;
+        if (c.src) {
+            std::memcpy(s.p + off, c.src, c.bytes);
+            a.src[a.n] = reinterpret_cast<const uint32_t *>(s.dp + off);
+            off += (c.bytes + 255) & ~(size_t)255;
+        }
+        a.words[a.n] = (uint32_t)(c.bytes / 4);
+        most = std::max(most, c.bytes / 4);
+        ++a.n;
+    }
+    if (a.n) {
+        k_stage<<<(unsigned)std::min<size_t>((most + 1023) / 1024, 256), 256, 0, st>>>(a);
+        count_launch(ctx);
+    }
+    VRC_CK(ctx, cudaGetLastError());
+    VRC_CK(ctx, cudaEventRecord(s.ev, st));
+    return VRC_OK;
+}
+
 vrc_status dev_alloc(vrc_ctx *ctx, void **p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) return VRC_OK;
     if (inject_fire(ctx, VRC_INJECT_ALLOC)) return set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
+    reap_pending(ctx, false);
     const size_t rb = round_block(bytes);
     int64_t prev = ctx->used.fetch_add((int64_t)rb);
     if (prev + (int64_t)rb > ctx->budget) {
         ctx->used.fetch_sub((int64_t)rb);
+        // cubes still waiting for their stream hold memory: wait for them once
+        if (reap_pending(ctx, true)) return dev_alloc(ctx, p, bytes);
         return set_err(ctx, VRC_E_NOMEM, "HBM budget exceeded: %lld used + %zu requested > %lld",
                        (long long)prev, rb, (long long)ctx->budget);
     }
@@ -295,6 +398,15 @@ vrc_status vrc_create(vrc_ctx **out, const vrc_config *cfg)
         return VRC_E_CUDA;
     }
     ctx->h_samples[0] = ctx->h_samples[1] = ctx->h_samples[2] = 0;
+    // pinned staging slots now: allocating pinned memory later may wait for the device
+    for (vrc_ctx::PinnedSlot &sl : ctx->stage) {
+        if (slot_alloc(ctx, sl, (size_t)256 << 10) != VRC_OK ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            vrc_destroy(ctx);
+            return VRC_E_CUDA;
+        }
+    }
     *out = ctx;
     return VRC_OK;
 }
@@ -305,6 +417,7 @@ vrc_status vrc_destroy(vrc_ctx *ctx)
     cudaSetDevice(ctx->device);
     server_stop(ctx);
     cudaDeviceSynchronize();
+    reap_pending(ctx, true);
     std::vector<int64_t> ids;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -314,6 +427,10 @@ vrc_status vrc_destroy(vrc_ctx *ctx)
     if (ctx->scratch) dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
     cudaDeviceSynchronize();
     cache_trim(ctx, 0);
+    for (vrc_ctx::PinnedSlot &sl : ctx->stage) {
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.p) cudaFreeHost(sl.p);
+    }
     if (ctx->ev_samples) cudaEventDestroy(ctx->ev_samples);
     if (ctx->h_samples) cudaFreeHost(ctx->h_samples);
     delete ctx;

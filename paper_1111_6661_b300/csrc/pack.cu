@@ -28,35 +28,45 @@ __device__ __forceinline__ int64_t clamp64(int64_t i, int64_t n) { return i < 0 
 
 // Pass 1: per brick, min/max of finite interior source values, absmax of finite
 // values over the stored region (interior + halo, clamp-to-edge), count of
-// non-finite interior voxels.
-__global__ void __launch_bounds__(256) k_brick_scan(const float *__restrict__ src, BrickGeom g,
-                                                    ScanPartial *__restrict__ part)
+// non-finite interior voxels.  A warp takes one stored row (B + 2 values) at a
+// time and issues up to 9 loads per lane before it reduces them.
+constexpr int kScanK = 9;   // 32-value loads in flight per lane (a B = 256 row is 258 values)
+__global__ void __launch_bounds__(256, 4) k_brick_scan(const float *__restrict__ src, BrickGeom g,
+                                                       ScanPartial *__restrict__ part)
 {
     const int64_t b = blockIdx.x;
     const int split = blockIdx.y;
     const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    const int lane = threadIdx.x & 31;
     float mn = FLT_MAX, mx = -FLT_MAX, am = 0.f;
     int nnf = 0, cnt = 0;
     float sum = 0.f;
     const int R = g.R;
+    const int nx = (int)g.dims[0], gx0 = bx * g.B - 1 + lane;   // value k of this lane: stored column lane + 32k
     for (int row = split * (blockDim.x / 32) + threadIdx.x / 32; row < R * R; row += kScanSplit * (blockDim.x / 32)) {
         const int ly = row % R - 1, lz = row / R - 1;
         const int64_t gy = (int64_t)by * g.B + ly, gz = (int64_t)bz * g.B + lz;
         const bool yz_in = ly >= 0 && ly < g.B && lz >= 0 && lz < g.B && gy < g.dims[1] && gz < g.dims[2];
         const float *rowp = src + (clamp64(gz, g.dims[2]) * g.dims[1] + clamp64(gy, g.dims[1])) * g.dims[0];
-        for (int lx = (int)(threadIdx.x % 32) - 1; lx <= g.B; lx += 32) {
-            const int64_t gx = (int64_t)bx * g.B + lx;
-            const float x = rowp[clamp64(gx, g.dims[0])];
-            const bool fin = fabsf(x) <= FLT_MAX;
-            if (fin) am = fmaxf(am, fabsf(x));
-            if (yz_in && lx >= 0 && lx < g.B && gx < g.dims[0]) {
-                if (fin) {
-                    mn = fminf(mn, x);
-                    mx = fmaxf(mx, x);
-                    sum += x;
-                    ++cnt;
-                } else {
-                    ++nnf;
+        for (int k0 = 0; k0 < R; k0 += 32 * kScanK) {
+            float x[kScanK];
+#pragma unroll
+            for (int k = 0; k < kScanK; ++k) x[k] = __ldg(rowp + min(max(gx0 + k0 + 32 * k, 0), nx - 1));
+#pragma unroll
+            for (int k = 0; k < kScanK; ++k) {
+                const int lx = lane - 1 + k0 + 32 * k;
+                if (lx > g.B) break;
+                const bool fin = fabsf(x[k]) <= FLT_MAX;
+                if (fin) am = fmaxf(am, fabsf(x[k]));
+                if (yz_in && lx >= 0 && lx < g.B && gx0 + k0 + 32 * k < nx) {
+                    if (fin) {
+                        mn = fminf(mn, x[k]);
+                        mx = fmaxf(mx, x[k]);
+                        sum += x[k];
+                        ++cnt;
+                    } else {
+                        ++nnf;
+                    }
                 }
             }
         }
@@ -366,7 +376,8 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
     const int64_t per_copy = arr_bytes * g.nbricks + (1 << 20);
     // leave room in the budget for the render scratch of a large multi-view call
     const int64_t reserve = (int64_t)2 << 30;
-    if (ctx->used.load() + per_copy + reserve > ctx->budget)
+    if (ctx->used.load() + per_copy + reserve > ctx->budget &&
+        !(reap_pending(ctx, true) && ctx->used.load() + per_copy + reserve <= ctx->budget))
         return set_err(ctx, VRC_E_NOMEM, "budget: no room for texture copies");
     vrc_status s = dev_alloc(ctx, (void **)&c->dtex, 3 * g.nbricks * 8);
     if (s != VRC_OK) return s;
@@ -409,6 +420,8 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
 
 // Fill the render copy from the packed bricks (one kernel per brick) and
 // upload the table of texture handles (the z copy; x and y entries are 0).
+// (Writing the copy from k_brick_pack instead measured 6.6 ms against 4.9 ms
+// for the two passes on a 1024^3 cube.)
 vrc_status launch_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
 {
     const BrickGeom &g = c->g;
@@ -423,17 +436,21 @@ vrc_status launch_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
         count_launch(ctx);
     }
     VRC_CK(ctx, cudaGetLastError());
-    VRC_CK(ctx, cudaMemcpyAsync(c->dtex, c->h_tex.data(), 8 * 3 * g.nbricks, cudaMemcpyHostToDevice, st));
+    vrc_status s = stage_h2d(ctx, st, {{c->dtex, c->h_tex.data(), (size_t)8 * 3 * g.nbricks}});
+    if (s != VRC_OK) return s;
     c->tex_axes |= 1 << axis;
     return VRC_OK;
 }
 
-void release_cube(vrc_ctx *ctx, Cube *c)
+}  // namespace
+
+void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
 {
     const BrickGeom &g = c->g;
     // the memory goes back to the context's cache and may be handed out at
-    // once: no launch still in flight may read it
-    cudaDeviceSynchronize();
+    // once: no launch still in flight may read it (the caller's event
+    // guarantees that when sync is false)
+    if (sync) cudaDeviceSynchronize();
     release_textures(ctx, c);
     slab_release(ctx, c);
     if (c->pool) dev_free(ctx, c->pool, g.nbricks * g.brick_bytes);
@@ -447,6 +464,8 @@ void release_cube(vrc_ctx *ctx, Cube *c)
     if (c->host_pool) cudaFreeHost(c->host_pool);
     delete c;
 }
+
+namespace {
 
 vrc_status alloc_meta(vrc_ctx *ctx, Cube *c)
 {
@@ -536,7 +555,7 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
     if (part) dev_free(ctx, part, part_bytes);
     if (staging) dev_free(ctx, staging, src_bytes);
     if (s != VRC_OK) {
-        release_cube(ctx, c);
+        release_cube(ctx, c, true);
         return s;
     }
     c->charged = g.nbricks * g.brick_bytes + 16 * g.nbricks;
@@ -577,7 +596,7 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
     if (s == VRC_OK) s = dev_alloc(ctx, &c->ring_pool, (size_t)ring_bricks * g.brick_bytes);
     if (s == VRC_OK) s = alloc_meta(ctx, c);
     if (s != VRC_OK) {
-        release_cube(ctx, c);
+        release_cube(ctx, c, true);
         return s;
     }
     c->host_filled.assign(n_host_bricks, 0);
@@ -659,7 +678,36 @@ vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id)
         ctx->cubes.erase(it);
     }
     cudaDeviceSynchronize();
-    release_cube(ctx, c);
+    release_cube(ctx, c, true);
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_free_async(vrc_ctx *ctx, int64_t cube_id, void *stream)
+{
+    if (!ctx) return VRC_E_INVAL;
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    cudaEvent_t ev;
+    VRC_CK(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    Cube *c = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->cubes.find(cube_id);
+        if (it == ctx->cubes.end() || it->second->refs.load() > 0) {
+            const bool busy = it != ctx->cubes.end();
+            cudaEventDestroy(ev);
+            return busy ? set_err(ctx, VRC_E_BUSY, "cube referenced by serving requests") : VRC_E_BADID;
+        }
+        c = it->second;
+        ctx->cubes.erase(it);
+    }
+    const cudaError_t e = cudaEventRecord(ev, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        release_cube(ctx, c, true);   // the cube is gone either way; fall back to a device-wide wait
+        return cuda_err(ctx, e, "vrc_cube_free_async event");
+    }
+    std::lock_guard<std::mutex> lk(ctx->pend_mu);
+    ctx->pending.emplace_back(ev, c);
     return VRC_OK;
 }
 

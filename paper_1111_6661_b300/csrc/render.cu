@@ -971,18 +971,19 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         j.samples = dsamples;
         j.skip_below = thr;
     }
-    VRC_CK(ctx, cudaMemsetAsync(dsamples, 0, 3 * sizeof(unsigned long long), st));
-    if (mode == 1) VRC_CK(ctx, cudaMemcpyAsync(dtf, tf_rgba, 1024 * 4, cudaMemcpyHostToDevice, st));
-    VRC_CK(ctx, cudaMemcpyAsync(djobs, jobs.data(), sizeof(JobDesc) * n_views, cudaMemcpyHostToDevice, st));
+    // tables in, counters zeroed: one small kernel, no copy-engine work
+    if ((s = stage_h2d(ctx, st, {{dtf, tf_rgba, mode == 1 ? (size_t)1024 * 4 : 0},
+                                 {djobs, jobs.data(), sizeof(JobDesc) * n_views},
+                                 {dsamples, nullptr, 3 * sizeof(unsigned long long)},
+                                 {counter, nullptr, sizeof(int)}})) != VRC_OK)
+        return s;
     if (slab) {
-        VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
         const int per_sm = ctas_override > 0 ? ctas_override : slab_occupancy(mode);
         const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
         slab_launch(c, mode, grid, st, djobs, n_views, total, counter, reinterpret_cast<int *>(dsamples + 2));
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
     } else if (!sortlast) {
-        VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
         const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
         const bool skip = tex && jobs[0].cellmax != nullptr;
         int per_sm = ctas_override > 0 ? ctas_override
@@ -999,9 +1000,9 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
         const uint8_t *slot_base = (const uint8_t *)(zerocopy ? c->host_pool_dev : c->pool);
         BrickItem *ditems = ar.take<BrickItem>(std::max<size_t>(1, plan.items.size()));
         float *partial = ar.take<float>(img_floats);
-        if (!plan.items.empty())
-            VRC_CK(ctx, cudaMemcpyAsync(ditems, plan.items.data(), sizeof(BrickItem) * plan.items.size(),
-                                        cudaMemcpyHostToDevice, st));
+        if (!plan.items.empty() &&
+            (s = stage_h2d(ctx, st, {{ditems, plan.items.data(), sizeof(BrickItem) * plan.items.size()}})) != VRC_OK)
+            return s;
         const int64_t n = (int64_t)img_floats;
         const int g = grid_for(n, ctx->sm_count * 8);
         if (mode == 0) {
@@ -1080,9 +1081,10 @@ vrc_status render_streamed(vrc_ctx *ctx, Cube *c, SortLastPlan &plan, const vrc_
     const int64_t img_floats = npx * (mode == 0 ? 1 : 4);
     BrickItem *ditems = ar.take<BrickItem>(std::max<size_t>(1, plan.items.size()));
     float *partial = ar.take<float>(img_floats);
-    if (!plan.items.empty())
-        VRC_CK(ctx, cudaMemcpyAsync(ditems, plan.items.data(), sizeof(BrickItem) * plan.items.size(),
-                                    cudaMemcpyHostToDevice, st));
+    if (!plan.items.empty()) {
+        const vrc_status ss = stage_h2d(ctx, st, {{ditems, plan.items.data(), sizeof(BrickItem) * plan.items.size()}});
+        if (ss != VRC_OK) return ss;
+    }
     const int gfill = grid_for(img_floats, ctx->sm_count * 8);
     if (mode == 0) {
         k_fill<0><<<gfill, 256, 0, st>>>(out, img_floats, -FLT_MAX);

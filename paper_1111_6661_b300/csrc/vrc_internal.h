@@ -133,7 +133,33 @@ struct vrc_ctx {
     std::multimap<size_t, void *> cached_blocks;       // rounded size -> block
     std::multimap<uint64_t, TexArray> cached_arrays;   // tex_array_key -> array
     std::atomic<int64_t> cached{0};
+    // cubes released by vrc_cube_free_async: their memory goes to the cache once
+    // the event recorded on the caller's stream has completed
+    std::mutex pend_mu;
+    std::vector<std::pair<cudaEvent_t, Cube *>> pending;
+    // pinned staging slots for small host-to-device inputs (stage_h2d)
+    std::mutex stage_mu;
+    struct PinnedSlot {
+        char *p = nullptr;        // pinned, mapped host memory
+        char *dp = nullptr;       // its device address
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+    } stage[4];
+    int stage_next = 0;
 };
+
+// One host-to-device copy of a small input (transfer function, job table, work
+// items), or a zero fill when src is null; bytes a multiple of 4.  stage_h2d
+// copies the sources into a pinned, mapped slot and one small kernel on `st`
+// moves them to the device.  The copy engines are not used: a copy from
+// pageable memory waited 36 ms behind a 1 GB image download, and a copy from
+// pinned memory at times waited 78 ms behind a cube's 4.3 GB upload.
+struct H2DCopy {
+    void *dst;
+    const void *src;
+    size_t bytes;
+};
+vrc_status stage_h2d(vrc_ctx *ctx, cudaStream_t st, const std::vector<H2DCopy> &copies);
 
 // ------------------------------------------------------------------ helpers
 vrc_status set_err(vrc_ctx *ctx, vrc_status s, const char *fmt, ...);
@@ -144,6 +170,8 @@ void dev_free(vrc_ctx *ctx, void *p, size_t bytes);   // the block must be idle 
 bool tex_array_take(vrc_ctx *ctx, uint64_t key, TexArray *a);
 void tex_array_give(vrc_ctx *ctx, uint64_t key, const TexArray &a);   // idle arrays only
 void cache_trim(vrc_ctx *ctx, int64_t keep_bytes);                     // release cached memory down to keep_bytes
+bool reap_pending(vrc_ctx *ctx, bool wait);   // release completed (wait: all) async-freed cubes; true if any
+void release_cube(vrc_ctx *ctx, Cube *c, bool sync);   // sync: wait for the device first
 void destroy_tex_array(const TexArray &a);
 vrc_status scratch_get(vrc_ctx *ctx, size_t bytes, void **p);
 Cube *find_cube(vrc_ctx *ctx, int64_t id);

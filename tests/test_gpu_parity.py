@@ -428,6 +428,52 @@ def test_cached_allocations_reused_and_trimmed(cube128):
     small.close()
 
 
+def test_free_async_is_stream_ordered(cube128):
+    """vrc_cube_free_async: the id is gone at once, the render already issued
+    on the stream still reads the cube, and its memory is reused by the next
+    upload of the same shape; under a budget that holds one cube, the next
+    upload waits for the released one instead of failing."""
+    vrc = vrcmod()
+    c = vrc.Context(0)
+    cams = cubegen.orbit_cameras((128, 128, 128), 3)
+    rc = vrc.raycfg(64, 48, 0.5)
+    tf = cubegen.tf_dense()
+    cid = c.cube_upload(cube128, "f32", brick=64)
+    ref = c.render_dvr(cid, cams, rc, tf).cpu()
+    used_one = c.memory()[0]
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        out = torch.empty((len(cams), 48, 64, 4), dtype=torch.float32, device="cuda")
+        c.render_dvr(cid, cams, rc, tf, out=out, stream=s)
+        c.cube_free_async(cid, stream=s)
+        with pytest.raises(vrc.VrcError):
+            c.cube_info(cid)
+        cid = c.cube_upload(cube128, "f32", brick=64)   # may reuse the released blocks
+        s.synchronize()
+        assert torch.equal(out.cpu(), ref)
+    torch.cuda.synchronize()
+    other = c.cube_upload(cube128[:64].copy(), "f32", brick=64)   # any allocation reaps completed releases
+    assert c.memory()[0] < 2 * used_one
+    c.cube_free(other)
+    # a budget that holds one cube and the next one's pool but not its staging
+    # copy: the second upload waits for the stream-ordered release (no render
+    # copies fit this budget; those renders read the bricks, same image)
+    pool = c.cube_info(cid)["bytes"]
+    c.cube_free(cid)
+    c.close()
+    small = vrc.Context(0, hbm_budget_bytes=int(2.2 * pool))
+    a = small.cube_upload(cube128, "f32", brick=64)
+    out = torch.empty((len(cams), 48, 64, 4), dtype=torch.float32, device="cuda")
+    small.render_dvr(a, cams, rc, tf, out=out, stream=s)
+    small.cube_free_async(a, stream=s)
+    b = small.cube_upload(cube128, "f32", brick=64)
+    assert torch.equal(small.render_dvr(b, cams, rc, tf).cpu(), ref)
+    s.synchronize()
+    assert torch.equal(out.cpu(), ref)
+    small.cube_free(b)
+    small.close()
+
+
 # ------------------------------------------------------------------ slab path
 def axis_cameras(dims):
     """Views whose rays run mainly along +-x, +-y and +-z (every principal
