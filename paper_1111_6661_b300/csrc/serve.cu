@@ -62,6 +62,10 @@ struct Server {
     int inflight = 0;
     std::vector<std::pair<void *, size_t>> pinned_free;   // reusable pinned buffers
     std::vector<std::pair<void *, size_t>> pinned_all;
+    // batch scratch comes from a pool of its own that keeps freed memory
+    // (the default pool returns it at every synchronisation, and mapping it
+    // again stalls later allocations)
+    cudaMemPool_t pool = nullptr;
 };
 
 namespace {
@@ -116,7 +120,8 @@ bool launch_batch(Server *S, SBatch *B, bool render)
     B->dbytes = batch_bytes(ctx, B->reqs, render);
     if (inject_fire(ctx, VRC_INJECT_ALLOC)) return false;
     if (ctx->used.load() + (int64_t)B->dbytes > ctx->budget) return false;
-    if (cudaMallocAsync(&B->dmem, B->dbytes, B->st) != cudaSuccess) {
+    if ((S->pool ? cudaMallocFromPoolAsync(&B->dmem, B->dbytes, S->pool, B->st)
+                 : cudaMallocAsync(&B->dmem, B->dbytes, B->st)) != cudaSuccess) {
         cudaGetLastError();
         B->dmem = nullptr;
         return false;
@@ -305,6 +310,33 @@ Server *server_get(vrc_ctx *ctx)
             delete S;
             return nullptr;
         }
+        // a device memory pool that keeps up to 1 GiB of freed batch scratch
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        if (cudaMemPoolCreate(&S->pool, &props) == cudaSuccess) {
+            uint64_t keep = (uint64_t)1 << 30;
+            cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            cudaGetLastError();
+            S->pool = nullptr;
+        }
+        // pinned host blocks for the largest batch, one per request that can be
+        // in flight: pinned allocations while serving may wait for the device
+        {
+            const size_t n = (size_t)std::max(ctx->cfg.max_inflight, 1);
+            const size_t full = n * (sizeof(vrc_stats) + 16) + render_hetero_stage_bytes(n) + 256;
+            for (size_t i = 0; i < n; ++i) {
+                void *p = nullptr;
+                if (cudaMallocHost(&p, full) != cudaSuccess) {
+                    cudaGetLastError();
+                    break;
+                }
+                S->pinned_all.push_back({p, full});
+                S->pinned_free.push_back({p, full});
+            }
+        }
         S->th = std::thread(serve_loop, S);
         ctx->server = S;
     }
@@ -332,6 +364,7 @@ void server_stop(vrc_ctx *ctx)
     for (cudaStream_t st : S->streams) cudaStreamSynchronize(st);
     for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
     for (auto &b : S->pinned_all) cudaFreeHost(b.first);
+    if (S->pool) cudaMemPoolDestroy(S->pool);
     delete S;
 }
 
