@@ -70,11 +70,14 @@ def render_source_hash() -> str:
     return h.hexdigest()
 
 
-def render_traffic():
-    """DRAM bytes per launch of the render kernel from the committed ncu
-    summary, or None if the kernel sources changed since it was taken."""
+BINDING_PROFILE = "profiles/k_render_fused_dvr768_1view.md"
+
+
+def profile_values(path: str):
+    """`- key: value` lines of a committed ncu summary, or None if the render
+    kernel's sources changed since it was taken."""
     try:
-        with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as f:
+        with open(os.path.join(ROOT, path)) as f:
             text = f.read()
     except OSError:
         return None
@@ -83,10 +86,26 @@ def render_traffic():
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha256") != render_source_hash():
+    return vals if vals.get("source_sha256") == render_source_hash() else None
+
+
+def render_traffic():
+    """DRAM bytes per launch of the render kernel (one-pass ncu count)."""
+    vals = profile_values(TRAFFIC_PROFILE)
+    try:
+        return float(vals["dram_bytes_per_launch"]) if vals else None
+    except (KeyError, ValueError):
+        return None
+
+
+def render_binding():
+    """The unit that binds the render kernel, from its full ncu capture."""
+    vals = profile_values(BINDING_PROFILE)
+    if not vals:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return {"unit": vals["binding_unit"], "busy_pct": float(vals["binding_unit_busy_pct"]),
+                "issue_active_pct": float(vals["issue_active_pct"]), "source": BINDING_PROFILE}
     except (KeyError, ValueError):
         return None
 
@@ -417,7 +436,8 @@ def run_gpu(args, w):
                 "roofline": {"bound": "alu", "kernel": "k_render_fused (DVR)", "achieved": achieved_tflops,
                              "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp32_peak_tflops,
                              "traffic": render_traffic(), "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
-                             "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz"},
+                             "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
+                             "binding": render_binding()},
                 "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms,
                             "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
