@@ -276,6 +276,16 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
 /* -------------------------------------------------------------- rendering */
 
 /*
+ * Every render call copies its small inputs (cameras turned into per-view job
+ * records, the transfer function) into pinned host memory and a small kernel
+ * on `stream` reads them into device memory, so no copy engine is involved.
+ * Reads of host memory by the device wait behind a large device-to-host copy
+ * already in flight (a render issued after a 1 GB image download had started
+ * began only when the download ended): in a pipeline, issue the next render
+ * before starting to copy the previous images back.
+ */
+
+/*
  * Maximum-intensity projection of n_views views in one persistent launch
  * (batched (view, ray tile) work items).  cams: HOST array of n_views cameras.
  * out: DEVICE float[n_views*H*W].  Stream-ordered; returns after launching.
