@@ -328,6 +328,13 @@ def run_gpu(args, w):
     stats_bytes = info["dims"][0] * info["dims"][1] * info["dims"][2] * (4 if w["storage"] == "f32" else 2)
     stats_gbs = stats_bytes / (stats_ms / 1e3) / 1e9
 
+    # exact median of the same cube (three radix-selection passes; not part of the step)
+    ctx.cube_median(cid)
+    t_med = time.perf_counter()
+    for _ in range(3):
+        ctx.cube_median(cid)
+    median_ms = (time.perf_counter() - t_med) * 1e3 / 3
+
     # the same step with empty-space skipping (identical image): frames/s, and
     # how many of the lattice samples were actually fetched
     skip = None
@@ -439,7 +446,7 @@ def run_gpu(args, w):
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
                              "binding": render_binding()},
                 "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
-                "kernels": {"render_ms": render_ms, "stats_ms": stats_ms,
+                "kernels": {"render_ms": render_ms, "stats_ms": stats_ms, "median_ms": median_ms,
                             "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
                             "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind},
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}

@@ -267,9 +267,11 @@ vrc_status vrc_cube_stats_noalloc(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, 
 /*
  * Median of the finite stored values (Sec. 3: a global task needing all data):
  * the lower median, value of rank floor((n-1)/2) in ascending order.  Exact:
- * a 65536-bin histogram on the ordered bit patterns of the values selects the
- * bin holding the rank, a second pass refines it.  *out is HOST memory; waits
- * for `stream`.  Errors: VRC_E_BADID, VRC_E_NONFINITE.
+ * radix selection on the order-preserving 32-bit keys of the values (-0 and +0
+ * are one value), three passes over the cube counting 12, 10 and 10 key bits
+ * in shared-memory histograms; each pass keeps the keys whose leading bits
+ * match the digits chosen so far.  *out is HOST memory; waits for `stream`.
+ * Errors: VRC_E_BADID, VRC_E_NONFINITE.
  */
 vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *stream);
 

@@ -1,5 +1,5 @@
 // Fused global statistics over resident bricks (min/max, mean, std, histogram)
-// and exact median by two-level radix selection.
+// and exact median by three-pass radix selection.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <float.h>
@@ -328,48 +328,101 @@ __device__ __forceinline__ uint32_t ord_key(float x)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// One radix-selection pass over the finite stored values: keys k = ord_key(x)
+// whose bits above `shift + nbits` equal `prefix` are counted by their digit
+// (k >> shift) & (2^nbits - 1).  Counters live in shared memory per block and
+// are added to the global histogram once per block (a global atomic per voxel
+// collides heavily: noise values share their leading key bits).
 struct SelArgs {
     const uint8_t *pool;
     BrickGeom g;
     const float *scales;
-    uint32_t prefix;       // pass 2: only keys whose high 16 bits equal prefix
-    int pass;              // 1: histogram of high 16 bits; 2: of low 16 bits
-    unsigned int *hist;    // device [65536]
+    const int32_t *bnonfinite;
+    int all_full;
+    int shift, nbits;              // digit of this pass
+    int prefix_all;                // 1: no prefix condition (first pass)
+    uint32_t prefix;               // required value of k >> (shift + nbits)
+    unsigned long long *hist;      // device [2^nbits], zeroed by the caller
 };
 
+constexpr int kSelMaxBins = 4096;
+
 template <int DT>
-__global__ void __launch_bounds__(256) k_select_hist(SelArgs a)
+__global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(SelArgs a)
 {
+    __shared__ uint32_t sh[kSelMaxBins];
     constexpr int VE = DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 8 : 16);
     constexpr int LOG_VE = DT == VRC_F32 ? 2 : (DT == VRC_BF16 ? 3 : 4);
+    const int nb = 1 << a.nbits;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
     const BrickGeom &g = a.g;
+    const int lane = threadIdx.x & 31;
     const int logVPR = g.logB - LOG_VE;
-    const int logVPB = 2 * g.logB + logVPR;
-    const int64_t total = g.nbricks << logVPB;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = v >> logVPB;
-        const int r = (int)(v & ((1ll << logVPB) - 1));
-        const int row = r >> logVPR, c = r & ((1 << logVPR) - 1);
-        const int ly = row & (g.B - 1), lz = row >> g.logB;
-        const int bx = (int)(b % g.nb[0]);
-        const int64_t byz = b / g.nb[0];
-        const int by = (int)(byz % g.nb[1]), bz = (int)(byz / g.nb[1]);
-        const int64_t gx0 = ((int64_t)bx << g.logB) + ((int64_t)c << LOG_VE);
-        if (((int64_t)by << g.logB) + ly >= g.dims[1] || ((int64_t)bz << g.logB) + lz >= g.dims[2] || gx0 >= g.dims[0])
-            continue;
-        const int nvalid = (int)min((int64_t)VE, g.dims[0] - gx0);
-        const int64_t off = (((int64_t)(lz + 1) * g.R + (ly + 1)) * g.P + g.O + ((int64_t)c << LOG_VE)) * g.esize;
-        const uint4 raw = __ldcs(reinterpret_cast<const uint4 *>(a.pool + b * g.brick_bytes + off));
-        float x[VE];
-        decode16<DT>(raw, DT == VRC_FP8E4M3 ? __ldg(a.scales + b) : 1.f, x);
+    const int logRPC = kLogChunk - logVPR;
+    const int logCPB = 2 * g.logB - logRPC;
+    const int64_t total_chunks = g.nbricks << logCPB;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t Pb = (uint32_t)(g.P * g.esize), RPb = (uint32_t)g.R * Pb, Ob = (uint32_t)(g.O * g.esize);
+    const uint32_t dmask = (uint32_t)nb - 1u;
+    const int hshift = a.shift + a.nbits;
+    for (int64_t ch = warp0; ch < total_chunks; ch += nwarps) {
+        const uint32_t b = (uint32_t)(ch >> logCPB);
+        const uint32_t lr0 = ((uint32_t)ch & ((1u << logCPB) - 1)) << logRPC;
+        bool clean;
+        uint32_t bx = 0, by = 0, bz = 0;
+        if (a.all_full) {
+            clean = __ldg(a.bnonfinite + b) == 0;
+        } else {
+            bx = b % (uint32_t)g.nb[0];
+            const uint32_t byz = b / (uint32_t)g.nb[0];
+            by = byz % (uint32_t)g.nb[1];
+            bz = byz / (uint32_t)g.nb[1];
+            clean = ((int64_t)(bx + 1) << g.logB) <= g.dims[0] && ((int64_t)(by + 1) << g.logB) <= g.dims[1] &&
+                    ((int64_t)(bz + 1) << g.logB) <= g.dims[2] && __ldg(a.bnonfinite + b) == 0;
+        }
+        const uint8_t *bp = a.pool + (uint64_t)b * (uint64_t)g.brick_bytes;
+        const float scale = DT == VRC_FP8E4M3 ? __ldg(a.scales + b) : 1.f;
+        uint4 raw[kVecPerLane];
 #pragma unroll
-        for (int e = 0; e < VE; ++e) {
-            if (e >= nvalid || !(fabsf(x[e]) <= FLT_MAX)) continue;
-            const uint32_t k = ord_key(x[e] == 0.f ? 0.f : x[e]);   // -0 and +0 are one value
-            if (a.pass == 1) atomicAdd(&a.hist[k >> 16], 1u);
-            else if ((k >> 16) == a.prefix) atomicAdd(&a.hist[k & 0xffffu], 1u);
+        for (int i = 0; i < kVecPerLane; ++i) {
+            const uint32_t j = lane + 32 * i;
+            const uint32_t lr = lr0 + (j >> logVPR);
+            const uint32_t off = ((lr >> g.logB) + 1) * RPb + ((lr & (g.B - 1)) + 1) * Pb + Ob +
+                                 ((j & ((1u << logVPR) - 1)) << 4);
+            raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + off));
+        }
+#pragma unroll
+        for (int i = 0; i < kVecPerLane; ++i) {
+            float x[VE];
+            decode16<DT>(raw[i], scale, x);
+            int nvalid = VE;
+            if (!clean) {
+                if (a.all_full) {
+                    bx = b % (uint32_t)g.nb[0];
+                    const uint32_t byz = b / (uint32_t)g.nb[0];
+                    by = byz % (uint32_t)g.nb[1];
+                    bz = byz / (uint32_t)g.nb[1];
+                }
+                const uint32_t j = lane + 32 * i;
+                const uint32_t lr = lr0 + (j >> logVPR);
+                const int64_t gx0 = ((int64_t)bx << g.logB) + ((int64_t)(j & ((1u << logVPR) - 1)) << LOG_VE);
+                const int64_t gy = ((int64_t)by << g.logB) + (lr & (g.B - 1)), gz = ((int64_t)bz << g.logB) + (lr >> g.logB);
+                nvalid = (int)min((int64_t)VE, g.dims[0] - gx0);
+                if (gy >= g.dims[1] || gz >= g.dims[2] || nvalid < 0) nvalid = 0;
+            }
+#pragma unroll
+            for (int e = 0; e < VE; ++e) {
+                if (!clean && (e >= nvalid || !(fabsf(x[e]) <= FLT_MAX))) continue;
+                const uint32_t k = ord_key(x[e] == 0.f ? 0.f : x[e]);   // -0 and +0 are one value
+                if (a.prefix_all || (k >> hshift) == a.prefix) atomicAdd(&sh[(k >> a.shift) & dmask], 1u);
+            }
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (sh[i]) atomicAdd(&a.hist[i], (unsigned long long)sh[i]);
 }
 
 int stats_grid(vrc_ctx *ctx) { return ctx->sm_count * 4; }
@@ -513,36 +566,48 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     VRC_CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     void *scr = nullptr;
-    if ((s = scratch_get(ctx, 65536 * sizeof(unsigned int), &scr)) != VRC_OK) return s;
-    unsigned int *dh = (unsigned int *)scr;
-    std::vector<unsigned int> h(65536);
+    if ((s = scratch_get(ctx, kSelMaxBins * sizeof(unsigned long long), &scr)) != VRC_OK) return s;
+    unsigned long long *dh = (unsigned long long *)scr;
+    std::vector<unsigned long long> h(kSelMaxBins);
     SelArgs a;
     a.pool = (const uint8_t *)c->pool;
     a.g = c->g;
     a.scales = c->scales;
+    a.bnonfinite = c->bnonfinite;
+    a.all_full = c->g.dims[0] % c->g.B == 0 && c->g.dims[1] % c->g.B == 0 && c->g.dims[2] % c->g.B == 0;
     a.hist = dh;
-    a.prefix = 0;
-    const int grid = stats_grid(ctx);
-    uint64_t rank = 0, total = 0;
+    int occ = 1;
+    if (c->g.dtype == VRC_F32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_F32>, kStatsThreads, 0);
+    else if (c->g.dtype == VRC_BF16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_BF16>, kStatsThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_FP8E4M3>, kStatsThreads, 0);
+    const int grid = ctx->sm_count * std::max(occ, 1);
+    // three digits of the 32-bit ordered key: 12, 10 and 10 bits
+    const int shifts[3] = {20, 10, 0}, widths[3] = {12, 10, 10};
+    uint64_t rank = 0;
     uint32_t key = 0;
-    for (int pass = 1; pass <= 2; ++pass) {
-        a.pass = pass;
-        VRC_CK(ctx, cudaMemsetAsync(dh, 0, 65536 * sizeof(unsigned int), st));
-        if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, 256, 0, st>>>(a);
-        else if (c->g.dtype == VRC_BF16) k_select_hist<VRC_BF16><<<grid, 256, 0, st>>>(a);
-        else k_select_hist<VRC_FP8E4M3><<<grid, 256, 0, st>>>(a);
+    for (int pass = 0; pass < 3; ++pass) {
+        a.shift = shifts[pass];
+        a.nbits = widths[pass];
+        a.prefix_all = pass == 0;
+        a.prefix = pass == 0 ? 0u : key >> (a.shift + a.nbits);
+        const int nb = 1 << a.nbits;
+        VRC_CK(ctx, cudaMemsetAsync(dh, 0, nb * sizeof(unsigned long long), st));
+        if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(a);
+        else if (c->g.dtype == VRC_BF16) k_select_hist<VRC_BF16><<<grid, kStatsThreads, 0, st>>>(a);
+        else k_select_hist<VRC_FP8E4M3><<<grid, kStatsThreads, 0, st>>>(a);
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
-        VRC_CK(ctx, cudaMemcpyAsync(h.data(), dh, 65536 * sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        VRC_CK(ctx, cudaMemcpyAsync(h.data(), dh, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         VRC_CK(ctx, cudaStreamSynchronize(st));
-        if (pass == 1) {
-            for (int i = 0; i < 65536; ++i) total += h[i];
+        if (pass == 0) {
+            uint64_t total = 0;
+            for (int i = 0; i < nb; ++i) total += h[i];
             if (total == 0) return set_err(ctx, VRC_E_NONFINITE, "cube has no finite voxel");
-            rank = (total - 1) / 2;
+            rank = (total - 1) / 2;   // lower median
         }
         uint64_t acc = 0;
         int sel = -1;
-        for (int i = 0; i < 65536; ++i) {
+        for (int i = 0; i < nb; ++i) {
             if (acc + h[i] > rank) {
                 sel = i;
                 break;
@@ -551,12 +616,7 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
         }
         if (sel < 0) return set_err(ctx, VRC_E_CUDA, "median selection inconsistent");
         rank -= acc;
-        if (pass == 1) {
-            a.prefix = (uint32_t)sel;
-            key = (uint32_t)sel << 16;
-        } else {
-            key |= (uint32_t)sel;
-        }
+        key |= (uint32_t)sel << a.shift;
     }
     const uint32_t u = (key & 0x80000000u) ? (key & 0x7fffffffu) : ~key;
     float f;

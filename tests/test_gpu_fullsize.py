@@ -53,6 +53,13 @@ def test_fullsize_stats(full):
     assert int(h.sum()) == v.size
 
 
+def test_fullsize_median(full):
+    w, v, cams, tf, ctx, cid = full
+    m = ctx.cube_median(cid)
+    k = (v.size - 1) // 2
+    assert m == float(np.partition(v.reshape(-1), k)[k])
+
+
 def test_fullsize_dvr_orbit(full):
     import paper_1111_6661_b300 as vrc
     w, v, cams, tf, ctx, cid = full

@@ -113,6 +113,28 @@ def test_median_exact(ctx, dtype, cube128):
         ctx.cube_free(cid)
 
 
+def test_median_special_values(ctx):
+    """Non-finite voxels are skipped, -0 and +0 are one value, ties and an
+    even count take the lower median, every digit of the key is exercised."""
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal((33, 31, 29)).astype(np.float32)
+    flat = v.reshape(-1)
+    flat[::97] = np.nan
+    flat[5::211] = np.inf
+    flat[7::313] = -np.inf
+    flat[11::17] = -0.0
+    flat[13::19] = 0.0
+    flat[20:40] = flat[41]                       # ties across the median region
+    for B in (16, 32):
+        cid = ctx.cube_upload(v, "f32", brick=B)
+        assert ctx.cube_median(cid) == oracle.median(v)
+        ctx.cube_free(cid)
+    w = np.array([3.0, -1.0, 2.0, 7.0], np.float32).reshape(1, 2, 2)   # even count: lower median 2.0
+    cid = ctx.cube_upload(w, "f32", brick=16)
+    assert ctx.cube_median(cid) == 2.0
+    ctx.cube_free(cid)
+
+
 # ------------------------------------------------------------------ rendering
 def render_check_mip(ctx, v, cid, cams, W, H, step, sampling, dtype="f32", B=0, path="fused"):
     vrc = vrcmod()
