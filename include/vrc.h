@@ -280,7 +280,9 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
 /*
  * Every render call copies its small inputs (cameras turned into per-view job
  * records, the transfer function) into pinned host memory and a small kernel
- * on `stream` reads them into device memory, so no copy engine is involved.
+ * on `stream` reads them into device memory, so no copy engine is involved
+ * (when four earlier calls' inputs are all still waiting on their streams,
+ * plain host-to-device copies are used instead).
  * Reads of host memory by the device wait behind a large device-to-host copy
  * already in flight (a render issued after a 1 GB image download had started
  * began only when the download ended): in a pipeline, issue the next render

@@ -136,10 +136,30 @@ vrc_status stage_h2d(vrc_ctx *ctx, cudaStream_t st, const std::vector<H2DCopy> &
         if (c.src) total += (c.bytes + 255) & ~(size_t)255;
     }
     std::lock_guard<std::mutex> lk(ctx->stage_mu);
-    vrc_ctx::PinnedSlot &s = ctx->stage[ctx->stage_next];
-    ctx->stage_next = (ctx->stage_next + 1) % 4;
+    // a slot whose previous contents have been read (never wait for one: its
+    // stream may be held back by work the caller has yet to issue)
+    vrc_ctx::PinnedSlot *slot = nullptr;
+    for (int k = 0; k < 4 && !slot; ++k) {
+        vrc_ctx::PinnedSlot &c = ctx->stage[(ctx->stage_next + k) % 4];
+        const cudaError_t q = c.ev ? cudaEventQuery(c.ev) : cudaSuccess;
+        if (q == cudaSuccess) {
+            slot = &c;
+            ctx->stage_next = (ctx->stage_next + k + 1) % 4;
+        } else if (q != cudaErrorNotReady) {
+            return cuda_err(ctx, q, "staging slot");
+        }
+    }
+    if (!slot) {
+        // every slot still in flight: plain copies and fills on `st`
+        for (const H2DCopy &c : copies) {
+            if (!c.bytes) continue;
+            if (c.src) VRC_CK(ctx, cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st));
+            else VRC_CK(ctx, cudaMemsetAsync(c.dst, 0, c.bytes, st));
+        }
+        return VRC_OK;
+    }
+    vrc_ctx::PinnedSlot &s = *slot;
     if (!s.ev) VRC_CK(ctx, cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
-    VRC_CK(ctx, cudaEventSynchronize(s.ev));   // this slot's previous contents have been read
     if (s.cap < total) {
         const vrc_status r = slot_alloc(ctx, s, std::max<size_t>(total, (size_t)256 << 10));
         if (r != VRC_OK) return r;

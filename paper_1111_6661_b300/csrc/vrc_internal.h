@@ -150,10 +150,12 @@ struct vrc_ctx {
 
 // One host-to-device copy of a small input (transfer function, job table, work
 // items), or a zero fill when src is null; bytes a multiple of 4.  stage_h2d
-// copies the sources into a pinned, mapped slot and one small kernel on `st`
-// moves them to the device.  The copy engines are not used: a copy from
-// pageable memory waited 36 ms behind a 1 GB image download, and a copy from
-// pinned memory at times waited 78 ms behind a cube's 4.3 GB upload.
+// copies the sources into a pinned, mapped slot whose previous contents have
+// been read and one small kernel on `st` moves them to the device.  The copy
+// engines are not used: a copy from pageable memory waited 36 ms behind a 1 GB
+// image download, and a copy from pinned memory at times waited 78 ms behind a
+// cube's 4.3 GB upload.  With all four slots still in flight it falls back to
+// plain copies and fills on `st` instead of waiting for a slot.
 struct H2DCopy {
     void *dst;
     const void *src;
