@@ -171,6 +171,12 @@ vrc_status vrc_memory(vrc_ctx *ctx, int64_t *used_bytes, int64_t *budget_bytes);
  * largest dimension when that is smaller); each
  * brick keeps a one-voxel clamp-to-edge halo.  The call records per-brick
  * min/max and returns when the cube is resident; src may then be reused.
+ * Resident cubes also get a render copy (one z-layered texture array per
+ * brick, read by the fused renderer's gathers) when it fits the budget with
+ * 2 GiB to spare; without it (or with the environment variable
+ * VRC_NO_TEXTURES set) the cube still renders, through global loads, and a
+ * note goes to stderr.  The host-to-device copy runs on `stream` and overlaps
+ * work on other streams; the packing kernels follow it on `stream`.
  * Errors: VRC_E_INVAL (dims <= 0, bad storage/brick), VRC_E_NOMEM (over budget).
  */
 vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device, int64_t nx, int64_t ny,
