@@ -173,9 +173,9 @@ vrc_status vrc_memory(vrc_ctx *ctx, int64_t *used_bytes, int64_t *budget_bytes);
  * min/max and returns when the cube is resident; src may then be reused.
  * Resident cubes also get a render copy (one z-layered texture array per
  * brick, read by the fused renderer's gathers) when it fits the budget with
- * 2 GiB to spare; without it (or with the environment variable
- * VRC_NO_TEXTURES set) the cube still renders, through global loads, and a
- * note goes to stderr.  The host-to-device copy runs on `stream` and overlaps
+ * 2 GiB to spare.  Without it the cube still renders, through global loads:
+ * when the budget has no room a note goes to stderr, and the environment
+ * variable VRC_NO_TEXTURES skips the copy on purpose.  The host-to-device copy runs on `stream` and overlaps
  * work on other streams; the packing kernels follow it on `stream`.
  * Errors: VRC_E_INVAL (dims <= 0, bad storage/brick), VRC_E_NOMEM (over budget).
  */
