@@ -104,6 +104,26 @@ def test_uniform_alpha_closed_form(alpha):
     assert np.all(r["nsamp"] == n)
 
 
+@pytest.mark.parametrize("alpha,step", [(0.05, 0.5), (0.3, 0.25), (0.6, 1.0)])
+def test_opacity_correction_closed_form(alpha, step):
+    # a sample's opacity is 1-(1-a)^step: n samples at spacing `step` through a
+    # constant cube absorb exactly as n*step unit-spaced samples would
+    v = np.full((16, 4, 4), 1.0, np.float32)
+    tf = cubegen.tf_constant((0.2, 0.5, 1.0), alpha)
+    cam = cubegen.ortho_z_camera((4, 4, 16))
+    r = oracle.render(v, cam, 4, 4, step, "trilinear", "dvr", tf=tf, vmin=0, vmax=2, term=2.0,
+                      opacity_correction=True)
+    n = int(r["nsamp"][0])
+    assert np.all(r["nsamp"] == n) and n == int(round(16 / step))
+    a = np.float64(np.float32(alpha))
+    A = 1 - (1 - a) ** (step * n)
+    assert np.allclose(r["out"][:, 3], A, rtol=0, atol=1e-12)
+    assert np.allclose(r["out"][:, :3], np.array([0.2, 0.5, 1.0], np.float32).astype(np.float64) * A, atol=1e-12)
+    # without the correction the same samples absorb more (step < 1) or the same (step = 1)
+    r0 = oracle.render(v, cam, 4, 4, step, "trilinear", "dvr", tf=tf, vmin=0, vmax=2, term=2.0)
+    assert np.allclose(r0["out"][:, 3], 1 - (1 - a) ** n, atol=1e-12)
+
+
 @pytest.mark.parametrize("alpha", [0.01, 0.05, 0.3])
 def test_termination_index_closed_form(alpha):
     a = float(np.float32(alpha))
