@@ -43,7 +43,8 @@ typedef int32_t vrc_status;
 #define VRC_E_INVAL      -1   /* bad argument (null pointer, size, enum, unknown flag) */
 #define VRC_E_NOMEM      -2   /* HBM budget exceeded or allocation failed */
 #define VRC_E_CUDA       -3   /* a CUDA runtime call failed; vrc_last_error() has text */
-#define VRC_E_TIMEOUT    -4   /* vrc_poll timed out (request is still pending) */
+#define VRC_E_TIMEOUT    -4   /* vrc_poll timed out (request is still pending), or a
+                                 bounded device-side wait gave up */
 #define VRC_E_BADID      -5   /* unknown cube id, ticket or graph handle */
 #define VRC_E_BUSY       -6   /* cube still referenced by queued or running requests */
 #define VRC_E_NONFINITE  -7   /* statistic undefined: the cube has no finite voxel */
@@ -441,10 +442,14 @@ vrc_status vrc_poll(vrc_ctx *ctx, uint64_t ticket, vrc_result *res, int32_t time
 #define VRC_INJECT_ALLOC       1  /* the nth device/pinned allocation fails (VRC_E_NOMEM) */
 #define VRC_INJECT_H2D         2  /* the nth host->device brick copy fails (VRC_E_INJECTED) */
 #define VRC_INJECT_DROP_REQ    3  /* the nth admitted serving request fails (VRC_E_INJECTED) */
+#define VRC_INJECT_SLAB_WAIT   4  /* the nth VRC_PATH_SLAB render issues none of its staging copies:
+                                     its bounded waits run out (about 1 s), the image is unspecified
+                                     and vrc_last_render_samples returns VRC_E_TIMEOUT */
 /*
  * Host-side fault injection for tests: arm failure `what` to fire on its nth
- * occurrence from now (n >= 1); VRC_INJECT_NONE disarms.  Nothing is injected
- * on the GPU.
+ * occurrence from now (n >= 1); VRC_INJECT_NONE disarms.  Nothing faults on
+ * the GPU: VRC_INJECT_SLAB_WAIT only withholds copies that kernels then wait
+ * for with a time limit.
  */
 vrc_status vrc_debug_inject(vrc_ctx *ctx, int32_t what, int64_t nth);
 

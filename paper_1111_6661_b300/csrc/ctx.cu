@@ -467,7 +467,7 @@ vrc_status vrc_memory(vrc_ctx *ctx, int64_t *used_bytes, int64_t *budget_bytes)
 
 vrc_status vrc_debug_inject(vrc_ctx *ctx, int32_t what, int64_t nth)
 {
-    if (!ctx || what < 0 || what > VRC_INJECT_DROP_REQ || (what != VRC_INJECT_NONE && nth < 1)) return VRC_E_INVAL;
+    if (!ctx || what < 0 || what > VRC_INJECT_SLAB_WAIT || (what != VRC_INJECT_NONE && nth < 1)) return VRC_E_INVAL;
     std::lock_guard<std::mutex> lk(ctx->inj_mu);
     ctx->inj_what = what;
     ctx->inj_left = what == VRC_INJECT_NONE ? 0 : nth;

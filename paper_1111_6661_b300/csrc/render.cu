@@ -980,7 +980,8 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     if (slab) {
         const int per_sm = ctas_override > 0 ? ctas_override : slab_occupancy(mode);
         const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
-        slab_launch(c, mode, grid, st, djobs, n_views, total, counter, reinterpret_cast<int *>(dsamples + 2));
+        slab_launch(c, mode, grid, st, djobs, n_views, total, counter, reinterpret_cast<int *>(dsamples + 2),
+                    inject_fire(ctx, VRC_INJECT_SLAB_WAIT));
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
     } else if (!sortlast) {

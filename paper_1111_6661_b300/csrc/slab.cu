@@ -66,6 +66,7 @@ struct HaloView {
     const float *base;      // element (hx, hy, hz) at hz * plane + hy * pitch + hx; voxel v has h = v + 1
     int64_t pitch, plane;
     int32_t nh[3];          // dims + 2
+    int32_t withhold;       // test injection: issue no staging copy (the bounded waits run out)
 };
 
 struct SlabMaps {
@@ -299,6 +300,7 @@ __device__ __forceinline__ void stage(const HaloView &hv, const CUtensorMap *map
     sh.org[0] = org[0];
     sh.org[1] = org[1];
     sh.org[2] = org[2];
+    if (hv.withhold) return;   // nothing arrives on the barrier: every wait for it runs out
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     bar_expect_tx(bar, (uint32_t)(S::elems * sizeof(float)));
     tma_load3(buf, map, org[0], org[1], org[2], bar);
@@ -617,9 +619,10 @@ int slab_occupancy(int mode)
 // Persistent slab launch over (view, 16x16 tile) work items of `jobs` (all of
 // cube c); err: device int set to 1 if a staging wait gave up.
 void slab_launch(const Cube *c, int mode, int grid, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total,
-                 int *counter, int *err)
+                 int *counter, int *err, bool withhold)
 {
     HaloView hv;
+    hv.withhold = withhold ? 1 : 0;
     hv.base = c->halo;
     hv.pitch = c->halo_pitch;
     hv.plane = c->halo_pitch * (c->g.dims[1] + 2);

@@ -225,4 +225,4 @@ vrc_status slab_prepare(vrc_ctx *ctx, Cube *c, cudaStream_t st);
 void slab_release(vrc_ctx *ctx, Cube *c);
 int slab_occupancy(int mode);
 void slab_launch(const Cube *c, int mode, int grid, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total,
-                 int *counter, int *err);
+                 int *counter, int *err, bool withhold);

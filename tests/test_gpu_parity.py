@@ -568,6 +568,29 @@ def test_slab_path_large_tiles_and_steps(ctx, cube128):
     ctx.cube_free(cid)
 
 
+def test_slab_wait_runs_out_and_context_survives(ctx, cube128):
+    """The slab renderer's wait for its staging copy is bounded: with the
+    copies withheld (host-side injection; nothing faults) the render reports
+    VRC_E_TIMEOUT within seconds, and the context renders correctly after."""
+    import time
+    vrc = vrcmod()
+    v = cube128[:64, :64, :64].copy()
+    cid = ctx.cube_upload(v, "f32", brick=32)
+    cams = cubegen.orbit_cameras((64, 64, 64), 2)
+    rc = vrc.raycfg(48, 40, 0.5, "trilinear", path="slab")
+    ref = ctx.render_mip(cid, cams, rc).cpu()
+    ctx.debug_inject("slab_wait", 1)
+    t0 = time.time()
+    ctx.render_mip(cid, cams, rc)
+    with pytest.raises(vrc.VrcError) as err:
+        ctx.last_render_samples()
+    assert err.value.status == -4   # VRC_E_TIMEOUT
+    assert time.time() - t0 < 30
+    assert torch.equal(ctx.render_mip(cid, cams, rc).cpu(), ref)
+    ctx.last_render_samples()
+    ctx.cube_free(cid)
+
+
 def test_slab_path_rejects_what_it_does_not_cover(ctx, cube128):
     vrc = vrcmod()
     v = cube128[:32, :32, :32].copy()
