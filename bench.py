@@ -355,6 +355,26 @@ def run_gpu(args, w):
                 "note": "skip_empty=1: samples whose 8^3 macro-cell is transparent under the TF are not fetched; "
                         "the image is bit-identical"}
 
+    # latency of one view alone: each orbit view rendered by its own call
+    # (n_views = 1), CUDA events around each call, three rounds over the orbit
+    view_ms = []
+    if not args.no_view_latency:
+        ctx.render_dvr(cid, cams[:1], rc, tf, w["term"], out=out[:1])
+        for _ in range(3):
+            for i, cam in enumerate(cams):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ctx.render_dvr(cid, [cam], rc, tf, w["term"], out=out[i:i + 1])
+                e1.record(st)
+                e1.synchronize()
+                view_ms.append(e0.elapsed_time(e1))
+    view_latency = None
+    if view_ms:
+        view_latency = {"p50_ms": float(np.percentile(view_ms, 50)), "p99_ms": float(np.percentile(view_ms, 99)),
+                        "max_ms": float(np.max(view_ms)), "renders": len(view_ms),
+                        "note": "one 1920x1080 view per render call (the orbit's views, 3 rounds), CUDA events; "
+                                "the batched step renders all views in one launch"}
+
     # end to end through the public API with host buffers.  Every step uploads
     # its cube from pinned host memory, computes the statistics, renders the
     # views and copies images and statistics back to pinned host memory.  The
@@ -446,6 +466,7 @@ def run_gpu(args, w):
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
                              "binding": render_binding()},
                 "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
+                "view_latency": view_latency,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms, "median_ms": median_ms,
                             "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
                             "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind},
@@ -690,6 +711,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-skip-variant", action="store_true")
+    ap.add_argument("--no-view-latency", action="store_true")
     ap.add_argument("--path", default="fused", choices=["fused", "slab"], help="render path of the timed step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")

@@ -226,6 +226,21 @@ vrc_status vrc_cube_free_async(vrc_ctx *ctx, int64_t cube_id, void *stream);
 vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t *brick, int32_t *storage,
                          int64_t *n_bricks, int64_t *bytes, float *vmin, float *vmax, int64_t *render_copy_bytes);
 
+/*
+ * Copy the stored form of brick `brick` (x fastest over the brick grid) of a
+ * resident cube into host memory `dst` of at least `dst_bytes` bytes (Sec. 2:
+ * sub-cubes; the quantised storage of the precision form).  Layout: R = B + 2
+ * planes (local z = -1..B) of R rows (local y = -1..B) of P = B + 2*O elements
+ * of esize bytes (4 fp32, 2 bf16 bits, 1 e4m3 code; O = 16 / esize), the
+ * voxel at local x at element O + x of its row: x = -1 and x = B are the
+ * halo, elements before and after them are padding (0).  Halo voxels outside
+ * the cube repeat the nearest edge voxel; FP8 codes use this brick's scale.
+ * Brick bytes = P * R * R * esize.  Synchronous (waits for the device).
+ * Errors: VRC_E_BADID, VRC_E_INVAL (brick out of range, dst NULL, dst_bytes
+ * too small), VRC_E_UNSUPPORTED (streamed cube: its bricks are the caller's).
+ */
+vrc_status vrc_cube_read_brick(vrc_ctx *ctx, int64_t cube_id, int64_t brick, void *dst, int64_t dst_bytes);
+
 /* ------------------------------------------------------------- statistics */
 
 /*

@@ -147,6 +147,20 @@ class Context:
         return dict(dims=tuple(dims), brick=B.value, storage={v: k for k, v in DTYPES.items()}[st.value],
                     n_bricks=nb.value, bytes=by.value, vmin=mn.value, vmax=mx.value, render_copy_bytes=tb.value)
 
+    def cube_read_brick(self, cube_id: int, brick: int) -> np.ndarray:
+        """Stored form of one brick: array (R, R, P) of float32 / uint16 (bf16
+        bits) / uint8 (e4m3 codes), R = B + 2 planes and rows (local -1..B),
+        local x at element O + x of a row (O = 16 / element size)."""
+        info = self.cube_info(cube_id)
+        B = info["brick"]
+        dt = {"f32": np.float32, "bf16": np.uint16, "fp8": np.uint8}[info["storage"]]
+        es = np.dtype(dt).itemsize
+        R, P = B + 2, B + 2 * (16 // es)
+        out = np.empty((R, R, P), dtype=dt)
+        self._check(self._lib.vrc_cube_read_brick(self.h, cube_id, brick, ctypes.c_void_p(out.ctypes.data),
+                                                  out.nbytes))
+        return out
+
     # ------------------------------------------------------------ statistics
     def cube_stats(self, cube_id: int, nbins: int = 0, stream=None):
         out = _vrc.vrc_stats()

@@ -14,8 +14,31 @@
 
 namespace {
 
-constexpr int kScanSplit = 16;   // blocks per brick in the scan pass
-constexpr int kPackSplit = 32;   // blocks per brick in the pack pass
+// Blocks per brick for a pass over the bricks whose blocks (256 threads) each
+// take an equal share of a brick's rows: the split that fills the resident
+// block slots best over whole waves (the smallest such split), at most one
+// block per 64 rows.
+int blocks_per_brick(const vrc_ctx *ctx, const void *kern, int64_t nbricks, int64_t rows_per_brick)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ <= 0) {
+        cudaGetLastError();
+        occ = 4;
+    }
+    const int64_t slots = (int64_t)ctx->sm_count * occ;
+    const int max_split = (int)std::max<int64_t>(1, std::min<int64_t>(256, rows_per_brick / 64));
+    int best = 1;
+    double best_fill = 0.0;
+    for (int s = 1; s <= max_split; ++s) {
+        const int64_t blocks = nbricks * s, waves = (blocks + slots - 1) / slots;
+        const double fill = (double)blocks / (double)(waves * slots);
+        if (fill > best_fill + 1e-9) {
+            best_fill = fill;
+            best = s;
+        }
+    }
+    return best;
+}
 
 struct ScanPartial {
     float mn, mx, absmax;
@@ -26,52 +49,134 @@ struct ScanPartial {
 
 __device__ __forceinline__ int64_t clamp64(int64_t i, int64_t n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
-// Pass 1: per brick, min/max of finite interior source values, absmax of finite
-// values over the stored region (interior + halo, clamp-to-edge), count of
-// non-finite interior voxels.  A warp takes one stored row (B + 2 values) at a
-// time and issues up to 9 loads per lane before it reduces them.
-constexpr int kScanK = 9;   // 32-value loads in flight per lane (a B = 256 row is 258 values)
-__global__ void __launch_bounds__(256, 4) k_brick_scan(const float *__restrict__ src, BrickGeom g,
-                                                       ScanPartial *__restrict__ part)
-{
-    const int64_t b = blockIdx.x;
-    const int split = blockIdx.y;
-    const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
-    const int lane = threadIdx.x & 31;
-    float mn = FLT_MAX, mx = -FLT_MAX, am = 0.f;
+struct ScanAcc {
+    float mn = INFINITY, mx = -INFINITY, am = 0.f, sum = 0.f;
     int nnf = 0, cnt = 0;
-    float sum = 0.f;
-    const int R = g.R;
-    const int nx = (int)g.dims[0], gx0 = bx * g.B - 1 + lane;   // value k of this lane: stored column lane + 32k
-    for (int row = split * (blockDim.x / 32) + threadIdx.x / 32; row < R * R; row += kScanSplit * (blockDim.x / 32)) {
-        const int ly = row % R - 1, lz = row / R - 1;
-        const int64_t gy = (int64_t)by * g.B + ly, gz = (int64_t)bz * g.B + lz;
-        const bool yz_in = ly >= 0 && ly < g.B && lz >= 0 && lz < g.B && gy < g.dims[1] && gz < g.dims[2];
-        const float *rowp = src + (clamp64(gz, g.dims[2]) * g.dims[1] + clamp64(gy, g.dims[1])) * g.dims[0];
-        for (int k0 = 0; k0 < R; k0 += 32 * kScanK) {
-            float x[kScanK];
+
+    // every value finite (checked afterwards through the sum)
+    __device__ __forceinline__ void fast(float x, bool fp8)
+    {
+        mn = fminf(mn, x);
+        mx = fmaxf(mx, x);
+        sum += x;
+        if (fp8) am = fmaxf(am, fabsf(x));
+    }
+    // an interior value of any kind
+    __device__ __forceinline__ void exact(float x)
+    {
+        if (fabsf(x) <= FLT_MAX) {
+            mn = fminf(mn, x);
+            mx = fmaxf(mx, x);
+            sum += x;
+            am = fmaxf(am, fabsf(x));
+            ++cnt;
+        } else {
+            ++nnf;
+        }
+    }
+    // a halo value: it only bounds the FP8 scale
+    __device__ __forceinline__ void halo(float x)
+    {
+        if (fabsf(x) <= FLT_MAX) am = fmaxf(am, fabsf(x));
+    }
+};
+
+// Interior rows [w0, nrows) step nw of one brick: extents (nxb, nyb) of its
+// interior inside the cube, x0 = its first column.  16-byte loads where the
+// rows allow them.  FP8 storage also folds in the row's two halo columns.
+template <bool FP8, bool EXACT>
+__device__ __forceinline__ void scan_rows(const float *__restrict__ src, const BrickGeom &g, int64_t x0, int64_t y0,
+                                          int64_t z0, int nxb, int nyb, int nrows, int w0, int nw, bool vec,
+                                          int lane, ScanAcc &a)
+{
+    const int64_t NX = g.dims[0];
+    for (int r = w0; r < nrows; r += nw) {
+        const int ly = r % nyb, lz = r / nyb;
+        const float *rowp = src + ((z0 + lz) * g.dims[1] + y0 + ly) * NX;
+        if (vec) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(rowp + x0);
+            const int nch = nxb >> 2;
+            for (int c0 = 0; c0 < nch; c0 += 64) {
+                float4 q[2];
 #pragma unroll
-            for (int k = 0; k < kScanK; ++k) x[k] = __ldg(rowp + min(max(gx0 + k0 + 32 * k, 0), nx - 1));
+                for (int k = 0; k < 2; ++k) {
+                    const int c = c0 + lane + 32 * k;
+                    q[k] = c < nch ? __ldg(r4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
 #pragma unroll
-            for (int k = 0; k < kScanK; ++k) {
-                const int lx = lane - 1 + k0 + 32 * k;
-                if (lx > g.B) break;
-                const bool fin = fabsf(x[k]) <= FLT_MAX;
-                if (fin) am = fmaxf(am, fabsf(x[k]));
-                if (yz_in && lx >= 0 && lx < g.B && gx0 + k0 + 32 * k < nx) {
-                    if (fin) {
-                        mn = fminf(mn, x[k]);
-                        mx = fmaxf(mx, x[k]);
-                        sum += x[k];
-                        ++cnt;
-                    } else {
-                        ++nnf;
+                for (int k = 0; k < 2; ++k) {
+                    if (c0 + lane + 32 * k < nch) {
+                        if (EXACT) {
+                            a.exact(q[k].x); a.exact(q[k].y); a.exact(q[k].z); a.exact(q[k].w);
+                        } else {
+                            a.fast(q[k].x, FP8); a.fast(q[k].y, FP8); a.fast(q[k].z, FP8); a.fast(q[k].w, FP8);
+                            a.cnt += 4;
+                        }
                     }
                 }
             }
+        } else {
+            for (int x = lane; x < nxb; x += 32) {
+                const float v = __ldg(rowp + x0 + x);
+                if (EXACT) a.exact(v);
+                else { a.fast(v, FP8); ++a.cnt; }
+            }
+        }
+        if (FP8 && lane == 0) {
+            a.halo(__ldg(rowp + clamp64(x0 - 1, NX)));
+            a.halo(__ldg(rowp + clamp64(x0 + g.B, NX)));
         }
     }
-    double dsum = sum;
+}
+
+// Pass 1: per brick, over its interior voxels inside the cube: min/max, sum
+// and count of the finite values and the count of non-finite ones; for FP8
+// storage also the largest finite magnitude over the whole stored region
+// (interior plus the clamp-to-edge halo), which sets the brick's scale.  The
+// first sweep assumes finite values (three operations per value); a block
+// whose sum comes out non-finite, which any NaN or infinity causes, sweeps
+// its rows again testing every value.  Stored rows and columns past the cube
+// edge repeat interior values and are not read.
+template <bool FP8>
+__global__ void __launch_bounds__(256) k_brick_scan(const float *__restrict__ src, BrickGeom g, int split,
+                                                    ScanPartial *__restrict__ part)
+{
+    const int64_t b = blockIdx.x;
+    const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    const int lane = threadIdx.x & 31;
+    const int64_t x0 = (int64_t)bx * g.B, y0 = (int64_t)by * g.B, z0 = (int64_t)bz * g.B;
+    const int nxb = (int)(g.dims[0] - x0 < g.B ? g.dims[0] - x0 : g.B);
+    const int nyb = (int)(g.dims[1] - y0 < g.B ? g.dims[1] - y0 : g.B);
+    const int nzb = (int)(g.dims[2] - z0 < g.B ? g.dims[2] - z0 : g.B);
+    const int nrows = nyb * nzb;
+    const int w0 = blockIdx.y * (blockDim.x / 32) + threadIdx.x / 32, nw = split * (blockDim.x / 32);
+    const bool vec = (g.dims[0] & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    ScanAcc a;
+    scan_rows<FP8, false>(src, g, x0, y0, z0, nxb, nyb, nrows, w0, nw, vec, lane, a);
+    if (__syncthreads_or(!(fabsf(a.sum) <= FLT_MAX))) {
+        a = ScanAcc();
+        scan_rows<FP8, true>(src, g, x0, y0, z0, nxb, nyb, nrows, w0, nw, vec, lane, a);
+    }
+    if (FP8) {
+        // the halo rows: ly or lz at -1 or B (columns -1..B), 4B + 4 rows
+        const int R = g.R;
+        for (int h = w0; h < 4 * g.B + 4; h += nw) {
+            int ly, lz;
+            if (h < 2 * R) {
+                lz = h < R ? -1 : g.B;
+                ly = h % R - 1;
+            } else {
+                const int j = h - 2 * R;
+                ly = j < g.B ? -1 : g.B;
+                lz = j % g.B;
+            }
+            const float *rowp = src + (clamp64(z0 + lz, g.dims[2]) * g.dims[1] + clamp64(y0 + ly, g.dims[1])) * g.dims[0];
+            for (int x = lane - 1; x <= g.B; x += 32) a.halo(__ldg(rowp + clamp64(x0 + x, g.dims[0])));
+        }
+    }
+    double dsum = a.sum;
+    float mn = a.mn, mx = a.mx, am = a.am;
+    int nnf = a.nnf, cnt = a.cnt;
     for (int o = 16; o; o >>= 1) {
         mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -81,7 +186,7 @@ __global__ void __launch_bounds__(256, 4) k_brick_scan(const float *__restrict__
         dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
     }
     __shared__ ScanPartial sp[8];
-    if ((threadIdx.x & 31) == 0) sp[threadIdx.x / 32] = ScanPartial{mn, mx, am, nnf, dsum, cnt};
+    if (lane == 0) sp[threadIdx.x / 32] = ScanPartial{mn, mx, am, nnf, dsum, cnt};
     __syncthreads();
     if (threadIdx.x == 0) {
         ScanPartial r = sp[0];
@@ -93,14 +198,18 @@ __global__ void __launch_bounds__(256, 4) k_brick_scan(const float *__restrict__
             r.sum += sp[w].sum;
             r.cnt += sp[w].cnt;
         }
-        part[b * kScanSplit + split] = r;
+        part[b * split + blockIdx.y] = r;
     }
+}
+
+__device__ __forceinline__ uint8_t fp8_code(float x, float scale)
+{
+    return (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(x, scale), __NV_SATFINITE, __NV_E4M3);
 }
 
 __device__ __forceinline__ float fp8_round_trip(float x, float scale)
 {
-    const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn(x, scale), __NV_SATFINITE, __NV_E4M3);
-    const __half h = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+    const __half h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)fp8_code(x, scale), __NV_E4M3);
     return __fmul_rn(__half2float(h), scale);
 }
 
@@ -113,14 +222,14 @@ __device__ __forceinline__ float stored_value(float x, int dtype, float scale)
 
 // Per brick: reduce the scan partials, derive the FP8 scale and the stored
 // min/max (rounding is monotone, so stored(min) is the stored minimum).
-__global__ void k_brick_finish(const ScanPartial *__restrict__ part, BrickGeom g, float *scales, float *bmin,
-                               float *bmax, int32_t *bnonfinite, double *bsum)
+__global__ void k_brick_finish(const ScanPartial *__restrict__ part, BrickGeom g, int split, float *scales,
+                               float *bmin, float *bmax, int32_t *bnonfinite, double *bsum)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.nbricks) return;
-    ScanPartial r = part[b * kScanSplit];
-    for (int s = 1; s < kScanSplit; ++s) {
-        const ScanPartial p = part[b * kScanSplit + s];
+    ScanPartial r = part[b * split];
+    for (int s = 1; s < split; ++s) {
+        const ScanPartial p = part[b * split + s];
         r.mn = fminf(r.mn, p.mn);
         r.mx = fmaxf(r.mx, p.mx);
         r.absmax = fmaxf(r.absmax, p.absmax);
@@ -139,40 +248,85 @@ __global__ void k_brick_finish(const ScanPartial *__restrict__ part, BrickGeom g
     bnonfinite[b] = r.nonfinite;
 }
 
+// 16 bytes of stored elements from 16 / esize source values.
+template <int DT> struct Chunk {
+    static constexpr int n = DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 8 : 16);
+};
+
 template <int DT>
-__device__ __forceinline__ void store_elem(void *base, int64_t i, float x, float scale)
+__device__ __forceinline__ uint4 pack_chunk(const float (&x)[Chunk<DT>::n], float scale)
 {
-    if (DT == VRC_F32) {
-        reinterpret_cast<float *>(base)[i] = x;
-    } else if (DT == VRC_BF16) {
-        reinterpret_cast<__nv_bfloat16 *>(base)[i] = __float2bfloat16_rn(x);
-    } else {
-        reinterpret_cast<__nv_fp8_storage_t *>(base)[i] =
-            __nv_cvt_float_to_fp8(__fdiv_rn(x, scale), __NV_SATFINITE, __NV_E4M3);
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (DT == VRC_F32) {
+            w[i] = __float_as_uint(x[i]);
+        } else if (DT == VRC_BF16) {
+            w[i] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * i])) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[2 * i + 1])) << 16);
+        } else {
+            w[i] = (uint32_t)fp8_code(x[4 * i], scale) | ((uint32_t)fp8_code(x[4 * i + 1], scale) << 8) |
+                   ((uint32_t)fp8_code(x[4 * i + 2], scale) << 16) | ((uint32_t)fp8_code(x[4 * i + 3], scale) << 24);
+        }
     }
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Pass 2: write every stored element of every brick (halo = clamp-to-edge,
-// row padding = 0).
+// Pass 2: write every stored row of every brick as 16-byte chunks: the left
+// chunk (padding, then the halo column lx = -1), B * esize / 16 interior
+// chunks, the right chunk (the halo column lx = B, then padding).  Halo rows
+// and columns clamp to the cube edge; padding is 0.  A warp writes one row at
+// a time; interior source values are read as 16-byte vectors where the rows
+// allow them.
 template <int DT>
-__global__ void __launch_bounds__(256) k_brick_pack(const float *__restrict__ src, BrickGeom g,
+__global__ void __launch_bounds__(256) k_brick_pack(const float *__restrict__ src, BrickGeom g, int split,
                                                     const float *__restrict__ scales, void *pool)
 {
+    constexpr int N = Chunk<DT>::n;
     const int64_t b = blockIdx.x;
     const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
     const float scale = scales[b];
     char *bp = reinterpret_cast<char *>(pool) + b * g.brick_bytes;
-    const int R = g.R;
-    for (int row = blockIdx.y * (blockDim.x / 32) + threadIdx.x / 32; row < R * R; row += kPackSplit * (blockDim.x / 32)) {
+    const int R = g.R, lane = threadIdx.x & 31;
+    const int64_t NX = g.dims[0], x0 = (int64_t)bx * g.B;
+    const int nin = g.B / N;
+    const bool vec = (NX & 3) == 0 && x0 + g.B <= NX && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    const int64_t row_bytes = (int64_t)g.P * g.esize;
+    for (int row = blockIdx.y * (blockDim.x / 32) + threadIdx.x / 32; row < R * R; row += split * (blockDim.x / 32)) {
         const int ly = row % R - 1, lz = row / R - 1;
         const int64_t gy = clamp64((int64_t)by * g.B + ly, g.dims[1]), gz = clamp64((int64_t)bz * g.B + lz, g.dims[2]);
-        const float *rowp = src + (gz * g.dims[1] + gy) * g.dims[0];
-        const int64_t rowbase = (int64_t)row * g.P;
-        for (int sx = threadIdx.x % 32; sx < g.P; sx += 32) {
-            const int lx = sx - g.O;
-            float x = 0.f;
-            if (lx >= -1 && lx <= g.B) x = rowp[clamp64((int64_t)bx * g.B + lx, g.dims[0])];
-            store_elem<DT>(bp, rowbase + sx, x, scale);
+        const float *rowp = src + (gz * g.dims[1] + gy) * NX;
+        uint4 *out = reinterpret_cast<uint4 *>(bp + row * row_bytes);
+        // two chunks per lane in flight (a B = 256 fp32 row is 64 chunks)
+        for (int j0 = lane; j0 < nin; j0 += 64) {
+            float x[2][N];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + 32 * h;
+                if (j >= nin) break;
+                if (vec) {
+                    const float4 *p4 = reinterpret_cast<const float4 *>(rowp + x0 + (int64_t)j * N);
+#pragma unroll
+                    for (int m = 0; m < N / 4; ++m) {
+                        const float4 q = __ldg(p4 + m);
+                        x[h][4 * m] = q.x; x[h][4 * m + 1] = q.y; x[h][4 * m + 2] = q.z; x[h][4 * m + 3] = q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < N; ++e) x[h][e] = __ldg(rowp + clamp64(x0 + (int64_t)j * N + e, NX));
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (j0 + 32 * h < nin) out[1 + j0 + 32 * h] = pack_chunk<DT>(x[h], scale);
+        }
+        if (lane < 2) {
+            float x[N];
+#pragma unroll
+            for (int e = 0; e < N; ++e) x[e] = 0.f;
+            if (lane == 0) x[N - 1] = __ldg(rowp + clamp64(x0 - 1, NX));
+            else x[0] = __ldg(rowp + clamp64(x0 + g.B, NX));
+            out[lane == 0 ? 0 : 1 + nin] = pack_chunk<DT>(x, scale);
         }
     }
 }
@@ -221,10 +375,15 @@ void finish_metadata(Cube *c, const std::vector<double> &bsum)
     if (!std::isfinite(c->shift)) c->shift = c->vmin;
 }
 
-// Copy one packed brick (interior + halo) into a layered CUDA array through a
-// surface.  Copy `axis` a stores local voxel l at texel (u, v, layer) =
-// (l[a1]+1, l[a2]+1, l[a]+1) with (a1, a2) = (x, y) for a = z, (y, z) for
-// a = x, (z, x) for a = y.  grid.y = layer.
+// Copy the packed bricks (interior + halo) into their layered CUDA arrays
+// through surfaces: stored element (sx, sy, sz) of brick b goes to texel
+// (sx, sy, layer sz) of array b, i.e. layers along z.  One launch for all
+// bricks.  A warp copies a pair of rows (sy, sy + 1) of one layer at a time:
+// half-warps take the two rows, 16 texels each per store, so that one store
+// covers whole 2-row blocks of the array's tiled layout instead of leaving
+// partly written sectors behind (a warp per row measured 4.2 ms on a 1024^3
+// fp32 cube, with 2x the DRAM reads).  R = B + 2 is even.  The surface
+// handles come from `surfs`.
 // FP8 bricks are copied as binary16 code values (every e4m3 value is exact in
 // binary16), so the texture unit returns them as fp32 with no conversion
 // instructions in the sampler; the per-brick scale is applied after the lerps.
@@ -241,57 +400,92 @@ __device__ __forceinline__ typename TexElem<T>::type tex_value(const uint8_t *br
         return reinterpret_cast<const T *>(brick)[e];
 }
 
+constexpr int kFillK = 9;   // 16-texel steps per lane in flight (a B = 256 row is 258 texels: 17 steps)
 template <typename T>
-__global__ void k_fill_array(const uint8_t *__restrict__ brick, BrickGeom g, int axis, cudaSurfaceObject_t surf)
+__global__ void __launch_bounds__(256) k_fill_copy(const uint8_t *__restrict__ pool, BrickGeom g,
+                                                   const unsigned long long *__restrict__ surfs)
 {
     using E = typename TexElem<T>::type;
-    const int layer = blockIdx.y;
-    const int R = g.R;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R * R; i += gridDim.x * blockDim.x) {
-        const int v = i / R, u = i % R;
-        int sx, sy, sz;   // storage indices (local + 1)
-        if (axis == 2) { sx = u; sy = v; sz = layer; }
-        else if (axis == 0) { sy = u; sz = v; sx = layer; }
-        else { sz = u; sx = v; sy = layer; }
-        const E val = tex_value<T>(brick, ((int64_t)sz * R + sy) * g.P + (g.O - 1) + sx);
-        surf2DLayeredwrite(val, surf, u * (int)sizeof(E), v, layer);
+    const int R = g.R, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const int64_t pairs = (int64_t)R * (R >> 1), total = pairs * g.nbricks;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < total; w += nw) {
+        const int64_t b = w / pairs;
+        const int p = (int)(w - b * pairs);
+        const int layer = p / (R >> 1), v = 2 * (p - layer * (R >> 1)) + half;
+        const uint8_t *brick = pool + b * g.brick_bytes;
+        const cudaSurfaceObject_t surf = surfs[b];
+        const int64_t e0 = ((int64_t)layer * R + v) * g.P + (g.O - 1);
+        for (int u0 = 0; u0 < R; u0 += 16 * kFillK) {
+            E val[kFillK];
+#pragma unroll
+            for (int k = 0; k < kFillK; ++k) {
+                const int u = u0 + hl + 16 * k;
+                val[k] = u < R ? tex_value<T>(brick, e0 + u) : E();
+            }
+#pragma unroll
+            for (int k = 0; k < kFillK; ++k) {
+                const int u = u0 + hl + 16 * k;
+                if (u < R) surf2DLayeredwrite(val[k], surf, u * (int)sizeof(E), v, layer);
+            }
+        }
     }
+}
+
+template <int DT>
+__device__ __forceinline__ float stored_at(const uint8_t *bp, int64_t e, float scale)
+{
+    if (DT == VRC_F32) return reinterpret_cast<const float *>(bp)[e];
+    if (DT == VRC_BF16) return __uint_as_float((uint32_t)reinterpret_cast<const unsigned short *>(bp)[e] << 16);
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)bp[e], __NV_E4M3);
+    return __fmul_rn(__half2float(__half(h)), scale);
 }
 
 // Maximum stored value over local voxels [8l-1, 8l+8]^3 of each 8^3 macro-cell
 // l of each brick (the brick's own copy, so FP8 halos use the brick's scale).
-// NaN voxels never raise the maximum.  One thread per cell.
+// NaN voxels never raise the maximum.  One block per (brick, layer of cells),
+// one thread per stored column sx (local x = sx - 1): the thread takes the
+// maximum over the layer's ten stored planes row by row and folds each row
+// into the cell rows whose windows hold it (stored rows 8c .. 8c+9 form cell
+// row c); the column maxima then reduce over each cell's ten columns in
+// shared memory.
 template <int DT>
 __global__ void k_cell_max(const uint8_t *__restrict__ pool, BrickGeom g, const float *__restrict__ scales,
-                           int ncx, int ncy, int ncz, float *__restrict__ cellmax)
+                           int ncx, int ncy, float *__restrict__ cellmax)
 {
-    const int64_t n = (int64_t)ncx * ncy * ncz;
-    const int cpb = g.B >> 3;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int cx = (int)(i % ncx), cy = (int)((i / ncx) % ncy), cz = (int)(i / ((int64_t)ncx * ncy));
-        const int bx = cx / cpb, by = cy / cpb, bz = cz / cpb;
-        const int64_t b = ((int64_t)bz * g.nb[1] + by) * g.nb[0] + bx;
-        const uint8_t *bp = pool + b * g.brick_bytes;
-        const float scale = scales[b];
-        const int lx0 = (cx % cpb) * 8 - 1, ly0 = (cy % cpb) * 8 - 1, lz0 = (cz % cpb) * 8 - 1;
-        float m = -INFINITY;
-        for (int z = 0; z < 10; ++z)
-            for (int y = 0; y < 10; ++y) {
-                const int64_t row = ((int64_t)(lz0 + z + 1) * g.R + (ly0 + y + 1)) * g.P + g.O + lx0;
-                for (int x = 0; x < 10; ++x) {
-                    float v;
-                    if (DT == VRC_F32) {
-                        v = reinterpret_cast<const float *>(bp)[row + x];
-                    } else if (DT == VRC_BF16) {
-                        v = __uint_as_float((uint32_t)reinterpret_cast<const unsigned short *>(bp)[row + x] << 16);
-                    } else {
-                        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)bp[row + x], __NV_E4M3);
-                        v = __fmul_rn(__half2float(__half(h)), scale);
-                    }
-                    m = fmaxf(m, v);
-                }
+    extern __shared__ float colmax[];   // [cpb][R]
+    const int cpb = g.B >> 3, R = g.R;
+    const int64_t b = blockIdx.x;
+    const int lzc = blockIdx.y, sx = threadIdx.x;
+    const uint8_t *bp = pool + b * g.brick_bytes;
+    const float scale = scales[b];
+    if (sx < R) {
+        float cur = -INFINITY, prev = -INFINITY;
+        for (int sy = 0; sy < R; ++sy) {
+            float m = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+                m = fmaxf(m, stored_at<DT>(bp, ((int64_t)(8 * lzc + k) * R + sy) * g.P + (g.O - 1) + sx, scale));
+            const int c = sy >> 3, q = sy & 7;
+            if (q == 0) {
+                prev = cur;
+                cur = -INFINITY;
             }
-        cellmax[i] = m;
+            if (q <= 1 && c >= 1) {
+                prev = fmaxf(prev, m);
+                if (q == 1) colmax[(c - 1) * R + sx] = prev;
+            }
+            cur = fmaxf(cur, m);
+        }
+    }
+    __syncthreads();
+    const int bx = (int)(b % g.nb[0]), by = (int)((b / g.nb[0]) % g.nb[1]), bz = (int)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    for (int i = threadIdx.x; i < cpb * cpb; i += blockDim.x) {
+        const int cy = i / cpb, cx = i - cy * cpb;
+        float m = -INFINITY;
+#pragma unroll
+        for (int x = 0; x < 10; ++x) m = fmaxf(m, colmax[cy * R + 8 * cx + x]);
+        cellmax[((int64_t)(bz * cpb + lzc) * ncy + (by * cpb + cy)) * ncx + (bx * cpb + cx)] = m;
     }
 }
 
@@ -331,18 +525,24 @@ vrc_status alloc_cellmax(vrc_ctx *ctx, Cube *c)
 vrc_status launch_cellmax(vrc_ctx *ctx, Cube *c, cudaStream_t st)
 {
     const BrickGeom &g = c->g;
-    const int64_t n = (int64_t)c->ncell[0] * c->ncell[1] * c->ncell[2];
-    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 16);
-    if (g.dtype == VRC_F32)
-        k_cell_max<VRC_F32><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0], c->ncell[1],
-                                                  c->ncell[2], c->cellmax);
-    else if (g.dtype == VRC_BF16)
-        k_cell_max<VRC_BF16><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0], c->ncell[1],
-                                                   c->ncell[2], c->cellmax);
-    else
-        k_cell_max<VRC_FP8E4M3><<<grid, 256, 0, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0],
-                                                      c->ncell[1], c->ncell[2], c->cellmax);
-    k_brick_halo_max<<<(unsigned)g.nbricks, 256, 0, st>>>(c->cellmax, g, c->ncell[0], c->ncell[1], g.B / 8, c->bhalo);
+    const int cpb = g.B / 8;
+    const dim3 grid((unsigned)g.nbricks, (unsigned)cpb);
+    const int threads = (g.R + 31) / 32 * 32;
+    const size_t smem = (size_t)cpb * g.R * sizeof(float);
+    auto launch = [&](auto kern) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<grid, threads, smem, st>>>((const uint8_t *)c->pool, g, c->scales, c->ncell[0], c->ncell[1],
+                                          c->cellmax);
+        return cudaGetLastError();
+    };
+    cudaError_t e = g.dtype == VRC_F32    ? launch(k_cell_max<VRC_F32>)
+                    : g.dtype == VRC_BF16 ? launch(k_cell_max<VRC_BF16>)
+                                          : launch(k_cell_max<VRC_FP8E4M3>);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "macro-cell maxima");
+    k_brick_halo_max<<<(unsigned)g.nbricks, 256, 0, st>>>(c->cellmax, g, c->ncell[0], c->ncell[1], cpb, c->bhalo);
     count_launch(ctx, 2);
     VRC_CK(ctx, cudaGetLastError());
     return VRC_OK;
@@ -357,7 +557,7 @@ void release_textures(vrc_ctx *ctx, Cube *c)
 {
     for (const TexArray &a : c->tex_arrays) tex_array_give(ctx, tex_array_key(c->g), a);
     c->tex_arrays.clear();
-    if (c->dtex) dev_free(ctx, c->dtex, 3 * c->g.nbricks * 8);
+    if (c->dtex) dev_free(ctx, c->dtex, 4 * c->g.nbricks * 8);
     c->dtex = nullptr;
     c->tex_axes = 0;
     ctx->used.fetch_sub(c->tex_bytes);
@@ -379,7 +579,7 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
     if (ctx->used.load() + per_copy + reserve > ctx->budget &&
         !(reap_pending(ctx, true) && ctx->used.load() + per_copy + reserve <= ctx->budget))
         return set_err(ctx, VRC_E_NOMEM, "budget: no room for texture copies");
-    vrc_status s = dev_alloc(ctx, (void **)&c->dtex, 3 * g.nbricks * 8);
+    vrc_status s = dev_alloc(ctx, (void **)&c->dtex, 4 * g.nbricks * 8);
     if (s != VRC_OK) return s;
     ctx->used.fetch_add(per_copy);
     c->tex_bytes += per_copy;
@@ -387,7 +587,7 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
                                : (g.dtype == VRC_BF16 ? cudaCreateChannelDesc<unsigned short>()
                                                       : cudaCreateChannelDescHalf());
     const uint64_t key = tex_array_key(g);
-    c->h_tex.assign(3 * g.nbricks, 0ull);
+    c->h_tex.assign(4 * g.nbricks, 0ull);
     for (int64_t b = 0; b < g.nbricks; ++b) {
         if (inject_fire(ctx, VRC_INJECT_ALLOC)) return set_err(ctx, VRC_E_NOMEM, "injected allocation failure");
         TexArray a;
@@ -413,32 +613,30 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
             }
         }
         c->tex_arrays.push_back(a);
-        c->h_tex[2 * g.nbricks + b] = a.tex;   // the z-layered copy
+        c->h_tex[2 * g.nbricks + b] = a.tex;    // the z-layered copy
+        c->h_tex[3 * g.nbricks + b] = a.surf;   // its surface, for the fill
     }
     return VRC_OK;
 }
 
-// Fill the render copy from the packed bricks (one kernel per brick) and
-// upload the table of texture handles (the z copy; x and y entries are 0).
-// (Writing the copy from k_brick_pack instead measured 6.6 ms against 4.9 ms
-// for the two passes on a 1024^3 cube.)
+// Upload the table of texture handles (the z copy; x and y entries are 0)
+// followed by the surface handles, then fill the render copy from the packed
+// bricks in one launch.  (Writing the copy from k_brick_pack instead measured
+// 6.6 ms against 4.9 ms for the two passes on a 1024^3 cube.)
 vrc_status launch_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
 {
     const BrickGeom &g = c->g;
-    const int axis = 2;
-    for (int64_t b = 0; b < g.nbricks; ++b) {
-        const cudaSurfaceObject_t surf = c->tex_arrays[b].surf;
-        const uint8_t *src = (const uint8_t *)c->pool + b * g.brick_bytes;
-        dim3 grid((unsigned)std::min<int64_t>((int64_t)g.R * g.R / 256 + 1, 64), (unsigned)g.R);
-        if (g.dtype == VRC_F32) k_fill_array<float><<<grid, 256, 0, st>>>(src, g, axis, surf);
-        else if (g.dtype == VRC_BF16) k_fill_array<unsigned short><<<grid, 256, 0, st>>>(src, g, axis, surf);
-        else k_fill_array<Fp8AsHalf><<<grid, 256, 0, st>>>(src, g, axis, surf);
-        count_launch(ctx);
-    }
-    VRC_CK(ctx, cudaGetLastError());
-    vrc_status s = stage_h2d(ctx, st, {{c->dtex, c->h_tex.data(), (size_t)8 * 3 * g.nbricks}});
+    vrc_status s = stage_h2d(ctx, st, {{c->dtex, c->h_tex.data(), (size_t)8 * 4 * g.nbricks}});
     if (s != VRC_OK) return s;
-    c->tex_axes |= 1 << axis;
+    const unsigned long long *surfs = reinterpret_cast<const unsigned long long *>(c->dtex) + 3 * g.nbricks;
+    const uint8_t *pool = (const uint8_t *)c->pool;
+    const unsigned grid = (unsigned)ctx->sm_count * 8;
+    if (g.dtype == VRC_F32) k_fill_copy<float><<<grid, 256, 0, st>>>(pool, g, surfs);
+    else if (g.dtype == VRC_BF16) k_fill_copy<unsigned short><<<grid, 256, 0, st>>>(pool, g, surfs);
+    else k_fill_copy<Fp8AsHalf><<<grid, 256, 0, st>>>(pool, g, surfs);
+    count_launch(ctx);
+    VRC_CK(ctx, cudaGetLastError());
+    c->tex_axes |= 1 << 2;
     return VRC_OK;
 }
 
@@ -513,9 +711,12 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
     const size_t src_bytes = (size_t)(nx * ny * nz) * 4;
     if (s == VRC_OK && !src_on_device) s = dev_alloc(ctx, &staging, src_bytes);
     ScanPartial *part = nullptr;
-    const size_t part_bytes = g.nbricks * (kScanSplit * sizeof(ScanPartial) + 16);
+    const int split = blocks_per_brick(ctx, storage == VRC_FP8E4M3 ? (const void *)k_brick_scan<true>
+                                                                   : (const void *)k_brick_scan<false>,
+                                       g.nbricks, (int64_t)g.B * g.B);
+    const size_t part_bytes = g.nbricks * (split * sizeof(ScanPartial) + 16);
     if (s == VRC_OK) s = dev_alloc(ctx, (void **)&part, part_bytes);
-    double *dbsum = part ? reinterpret_cast<double *>(part + g.nbricks * kScanSplit) : nullptr;
+    double *dbsum = part ? reinterpret_cast<double *>(part + g.nbricks * split) : nullptr;
     bool tex = false;
     if (s == VRC_OK && getenv("VRC_NO_TEXTURES") == nullptr) {
         // texture copies are an accelerator: without room for them the cube still renders
@@ -533,13 +734,19 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
         dsrc = (const float *)staging;
     }
     if (s == VRC_OK) {
-        k_brick_scan<<<dim3((unsigned)g.nbricks, kScanSplit), 256, 0, st>>>(dsrc, g, part);
-        k_brick_finish<<<(unsigned)((g.nbricks + 127) / 128), 128, 0, st>>>(part, g, c->scales, c->bmin, c->bmax,
-                                                                            c->bnonfinite, dbsum);
-        dim3 grid((unsigned)g.nbricks, kPackSplit);
-        if (storage == VRC_F32) k_brick_pack<VRC_F32><<<grid, 256, 0, st>>>(dsrc, g, c->scales, c->pool);
-        else if (storage == VRC_BF16) k_brick_pack<VRC_BF16><<<grid, 256, 0, st>>>(dsrc, g, c->scales, c->pool);
-        else k_brick_pack<VRC_FP8E4M3><<<grid, 256, 0, st>>>(dsrc, g, c->scales, c->pool);
+        const dim3 grid((unsigned)g.nbricks, (unsigned)split);
+        if (storage == VRC_FP8E4M3) k_brick_scan<true><<<grid, 256, 0, st>>>(dsrc, g, split, part);
+        else k_brick_scan<false><<<grid, 256, 0, st>>>(dsrc, g, split, part);
+        k_brick_finish<<<(unsigned)((g.nbricks + 127) / 128), 128, 0, st>>>(part, g, split, c->scales, c->bmin,
+                                                                            c->bmax, c->bnonfinite, dbsum);
+        const void *pk = storage == VRC_F32    ? (const void *)k_brick_pack<VRC_F32>
+                         : storage == VRC_BF16 ? (const void *)k_brick_pack<VRC_BF16>
+                                               : (const void *)k_brick_pack<VRC_FP8E4M3>;
+        const int psplit = blocks_per_brick(ctx, pk, g.nbricks, (int64_t)g.R * g.R);
+        const dim3 pgrid((unsigned)g.nbricks, (unsigned)psplit);
+        if (storage == VRC_F32) k_brick_pack<VRC_F32><<<pgrid, 256, 0, st>>>(dsrc, g, psplit, c->scales, c->pool);
+        else if (storage == VRC_BF16) k_brick_pack<VRC_BF16><<<pgrid, 256, 0, st>>>(dsrc, g, psplit, c->scales, c->pool);
+        else k_brick_pack<VRC_FP8E4M3><<<pgrid, 256, 0, st>>>(dsrc, g, psplit, c->scales, c->pool);
         count_launch(ctx, 3);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = cuda_err(ctx, e, "brick pack launch");
@@ -662,6 +869,25 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
     c->has_finite = vmn <= vmx;
     c->vmin = c->has_finite ? vmn : 0.f;
     c->vmax = c->has_finite ? vmx : 0.f;
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_read_brick(vrc_ctx *ctx, int64_t cube_id, int64_t brick, void *dst, int64_t dst_bytes)
+{
+    if (!ctx) return VRC_E_INVAL;
+    if (!dst) return set_err(ctx, VRC_E_INVAL, "dst is NULL");
+    Cube *c = find_cube(ctx, cube_id);
+    if (!c) return VRC_E_BADID;
+    if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "streamed cube: bricks live in host slots");
+    const BrickGeom &g = c->g;
+    if (brick < 0 || brick >= g.nbricks) return set_err(ctx, VRC_E_INVAL, "brick %lld out of range", (long long)brick);
+    if (dst_bytes < g.brick_bytes)
+        return set_err(ctx, VRC_E_INVAL, "dst_bytes %lld < brick bytes %lld", (long long)dst_bytes,
+                       (long long)g.brick_bytes);
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    VRC_CK(ctx, cudaDeviceSynchronize());
+    VRC_CK(ctx, cudaMemcpy(dst, (const char *)c->pool + brick * g.brick_bytes, (size_t)g.brick_bytes,
+                           cudaMemcpyDeviceToHost));
     return VRC_OK;
 }
 

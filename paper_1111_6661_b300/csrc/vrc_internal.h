@@ -80,7 +80,7 @@ struct Cube {
     // read by texture gathers (2x2 texel footprints) in the fused renderer
     std::vector<TexArray> tex_arrays;
     std::vector<unsigned long long> h_tex;   // texture handles staged for the device table
-    unsigned long long *dtex = nullptr;   // device [3][nbricks] texture handles by layer axis (0 where absent)
+    unsigned long long *dtex = nullptr;   // device [4][nbricks]: texture handles by layer axis (0 where absent), then surfaces
     int32_t tex_axes = 0;                 // bit a set: copy layered along axis a exists (only z is built)
     int64_t tex_bytes = 0;
     // maximum stored value of every 8^3 macro-cell plus a one-voxel margin,
