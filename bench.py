@@ -394,9 +394,10 @@ def run_gpu(args, w):
         s_up, s_rd, s_dn = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         rendered = [torch.cuda.Event(), torch.cuda.Event()]
-        # at least 8 steps: the first upload and the last image copy (pipeline
+        # at least 32 steps: the first upload and the last image copy (pipeline
         # fill and drain) stay inside the timed region but do not dominate it
-        e2e_steps = max(8, args.steps)
+        e2e_steps = max(32, args.steps)
+        arrived = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
         ctx.cube_free(cid)
         cid = None
         torch.cuda.synchronize()
@@ -427,6 +428,7 @@ def run_gpu(args, w):
                 host_stats.copy_(dst[b], non_blocking=True)
                 host_hist.copy_(dhi[b], non_blocking=True)
             copied[b].record(s_dn)
+            arrived[i].record(s_dn)
             # every read of cube i is ordered before the copies on s_dn: release
             # it there, so a later upload reuses its memory without a device wait
             ctx.cube_free_async(cubes[i], stream=s_dn)
@@ -436,14 +438,17 @@ def run_gpu(args, w):
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         e2e_s = barrier_max(e2e_s, ws)
+        period = [arrived[i - 1].elapsed_time(arrived[i]) for i in range(1, e2e_steps)]
         e2e = {"value": ws * samples_per_step / e2e_s, "unit": "samples/s",
                "h2d_bytes_per_step": int(v.nbytes + 4096 + 48 * len(cams)),
                "d2h_bytes_per_step": int(host_img[0].numel() * 4 + 8 * w["nbins"] + 64),
                "ms_per_step": 1e3 * e2e_s, "steps": e2e_steps,
+               "steady_ms_per_step": float(np.median(period)),
                "pipeline": "upload of step i+2 overlaps the render of step i+1; images of step i copied back "
                            "while step i+1 renders; each cube released in stream order after its images "
                            "(vrc_cube_free_async), so uploads reuse its memory; timed from the first upload to "
-                           "the last image on the host (fill and drain included)"}
+                           "the last image on the host (fill and drain included); steady_ms_per_step = median interval "
+                           "between consecutive steps' images arriving on the host"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

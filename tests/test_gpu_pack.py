@@ -136,3 +136,26 @@ def test_read_brick_errors(ctx):
         ctx.cube_free(cid)
     with pytest.raises(vrc.VrcError):
         ctx.cube_read_brick(cid, 0)               # freed id
+
+
+def test_largest_brick_edge(ctx):
+    """B = 512 (the largest brick edge): stored bricks bit-exact, and the
+    macro-cell maxima (their pass needs more than 48 KB of shared memory per
+    block at this edge) leave the skip_empty image bit-identical."""
+    import torch
+
+    import paper_1111_6661_b300 as vrc
+    dims = (520, 24, 16)                           # 2 x 1 x 1 bricks, the second one ragged
+    v = cubegen.generate(dims, 3, 46)
+    check_cube(ctx, v, 512, "f32")
+    cid = ctx.cube_upload(v, "f32", brick=512)
+    try:
+        cams = cubegen.orbit_cameras(dims, 2)
+        tf = cubegen.tf_sparse()
+        a = ctx.render_dvr(cid, cams, vrc.raycfg(64, 48, 0.5), tf).cpu()
+        n0 = ctx.last_render_samples()
+        b = ctx.render_dvr(cid, cams, vrc.raycfg(64, 48, 0.5, skip_empty=True), tf).cpu()
+        n1, e1 = ctx.last_render_samples(evaluated=True)
+        assert torch.equal(a, b) and n0 == n1 and e1 < n1
+    finally:
+        ctx.cube_free(cid)
