@@ -507,11 +507,30 @@ def run_precision(args):
     ctx = vrc.Context(0)
     st_ref = oracle.stats(v)
     out = {}
+    pk, pk_kind = peaks()
+    nvox = dims[0] * dims[1] * dims[2]
     for dt in ("f32", "bf16", "fp8"):
+        torch.cuda.synchronize()
+        t_up = time.perf_counter()
         cid = ctx.cube_upload(v, dt, brick=256)
+        upload_s = time.perf_counter() - t_up
         info = ctx.cube_info(cid)
         s, h = ctx.cube_stats(cid, 4096)
-        row = {"stats": {k: s[k] for k in ("min", "max", "mean", "std")}}
+        row = {"stats": {k: s[k] for k in ("min", "max", "mean", "std")}, "upload_s": upload_s}
+        # the statistics pass alone (4096 bins), CUDA events over 5 calls
+        dstats = torch.empty(8, dtype=torch.float64, device="cuda")
+        dhist = torch.empty(4096, dtype=torch.int64, device="cuda")
+        ctx.cube_stats_async(cid, 4096, dstats, dhist)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            ctx.cube_stats_async(cid, 4096, dstats, dhist)
+        e1.record()
+        torch.cuda.synchronize()
+        st_ms = e0.elapsed_time(e1) / 5
+        st_gbs = nvox * {"f32": 4, "bf16": 2, "fp8": 1}[dt] / (st_ms / 1e3) / 1e9
+        row["stats_pass"] = {"ms": st_ms, "voxels_per_s": nvox / (st_ms / 1e3), "stored_hbm_gbs": st_gbs,
+                             "hbm_frac": st_gbs / pk["hbm_gbs"], "hbm_peak_kind": pk_kind}
         row["stats_rel_err_vs_fp32_oracle"] = {k: abs(s[k] - st_ref[k]) / max(abs(st_ref[k]), st_ref["std"])
                                                for k in ("min", "max", "mean", "std")}
         if dt != "f32":

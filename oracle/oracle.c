@@ -156,10 +156,12 @@ float orc_bf16_round(float x)
 
 /* Value of the OCP FP8 E4M3 (finite-only) number nearest to y, ties to even,
  * saturated to +-448.  Spacing: 2^(e-3) for |y| in [2^e, 2^(e+1)), e >= -6;
- * 2^-9 below 2^-6 (subnormals). */
+ * 2^-9 below 2^-6 (subnormals).  The format has no infinity: a non-finite y
+ * (NaN or +-inf) becomes NaN, its only non-finite value, so that a stored
+ * cube keeps its non-finite voxels non-finite (statistics skip them). */
 double orc_e4m3_round(float y)
 {
-    if (isnan(y)) return NAN;
+    if (isnan(y) || isinf(y)) return NAN;
     double a = fabs((double)y);
     if (a == 0.0) return 0.0 * (y < 0 ? -1.0 : 1.0);
     double q;

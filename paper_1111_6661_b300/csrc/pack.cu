@@ -202,8 +202,12 @@ __global__ void __launch_bounds__(256) k_brick_scan(const float *__restrict__ sr
     }
 }
 
+// e4m3 code of x / scale, nearest even, finite values saturated to +-448.
+// E4M3 has no infinity: every non-finite x (NaN or +-inf) is stored as NaN
+// (0x7f), so non-finite voxels stay non-finite in every storage type.
 __device__ __forceinline__ uint8_t fp8_code(float x, float scale)
 {
+    if (!(fabsf(x) <= FLT_MAX)) return 0x7f;
     return (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(x, scale), __NV_SATFINITE, __NV_E4M3);
 }
 

@@ -272,6 +272,112 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_stats(StatsA
     }
 }
 
+// FP8 storage: a voxel's stored value depends only on its brick's scale and
+// its 8-bit code, so the statistics follow exactly from per-brick code counts.
+// Work items are runs of 2^6 chunks (chunks as in k_stats) of one brick,
+// assigned to blocks in a fixed order; a block counts an item's codes in
+// shared memory (one shared-memory increment per voxel and no arithmetic),
+// then thread q turns code q's count k into its share of n or n_nonfinite,
+// the moments in binary64 (k * d and k * d^2 with d = value * dscale; the
+// shift c is 0 for FP8) and the value histogram (the same binary32 bin
+// formula as k_stats, one global add per code present).  One partial per
+// block, merged by k_stats_final like those of k_stats.
+constexpr int kLogCodeChunks = 6;
+__global__ void __launch_bounds__(kStatsThreads) k_stats_codes(StatsArgs a)
+{
+    static_assert(kStatsThreads == 256, "one thread per code");
+    __shared__ uint32_t cnt[256];
+    const BrickGeom &g = a.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int logVPR = g.logB - 4;                     // 16 codes per 16-byte vector
+    const int logRPC = kLogChunk - logVPR;
+    const int logCPB = 2 * g.logB - logRPC;
+    const int lcpi = min(kLogCodeChunks, logCPB);     // chunks per item (log)
+    const int ipb = logCPB - lcpi;                     // items per brick (log)
+    const int64_t items = g.nbricks << ipb;
+    const uint32_t Pb = (uint32_t)g.P, RPb = (uint32_t)g.R * Pb, Ob = (uint32_t)g.O;
+    double s1 = 0.0, s2 = 0.0;
+    unsigned long long n = 0, nnf = 0;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const uint32_t b = (uint32_t)(it >> ipb);
+        const uint32_t c0 = ((uint32_t)it & ((1u << ipb) - 1)) << lcpi;
+        cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t bx = b % (uint32_t)g.nb[0], byz = b / (uint32_t)g.nb[0];
+        const uint32_t by = byz % (uint32_t)g.nb[1], bz = byz / (uint32_t)g.nb[1];
+        const bool clean = ((int64_t)(bx + 1) << g.logB) <= g.dims[0] && ((int64_t)(by + 1) << g.logB) <= g.dims[1] &&
+                           ((int64_t)(bz + 1) << g.logB) <= g.dims[2];
+        const uint8_t *bp = a.pool + (uint64_t)b * (uint64_t)g.brick_bytes;
+        for (uint32_t ch = c0 + warp; ch < c0 + (1u << lcpi); ch += kStatsThreads / 32) {
+            const uint32_t lr0 = ch << logRPC;
+            uint4 raw[kVecPerLane];
+#pragma unroll
+            for (int i = 0; i < kVecPerLane; ++i) {
+                const uint32_t j = lane + 32 * i;
+                const uint32_t lr = lr0 + (j >> logVPR);
+                const uint32_t off = ((lr >> g.logB) + 1) * RPb + ((lr & (g.B - 1)) + 1) * Pb + Ob +
+                                     ((j & ((1u << logVPR) - 1)) << 4);
+                raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + off));
+            }
+#pragma unroll
+            for (int i = 0; i < kVecPerLane; ++i) {
+                int nvalid = 16;
+                if (!clean) {
+                    const uint32_t j = lane + 32 * i;
+                    const uint32_t lr = lr0 + (j >> logVPR);
+                    const int64_t gx0 = ((int64_t)bx << g.logB) + ((int64_t)(j & ((1u << logVPR) - 1)) << 4);
+                    const int64_t gy = ((int64_t)by << g.logB) + (lr & (g.B - 1));
+                    const int64_t gz = ((int64_t)bz << g.logB) + (lr >> g.logB);
+                    nvalid = (int)min((int64_t)16, g.dims[0] - gx0);
+                    if (gy >= g.dims[1] || gz >= g.dims[2] || nvalid < 0) nvalid = 0;
+                }
+                const uint32_t w[4] = {raw[i].x, raw[i].y, raw[i].z, raw[i].w};
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    if (clean || e < nvalid) atomicAdd(&cnt[(w[e >> 2] >> (8 * (e & 3))) & 0xffu], 1u);
+            }
+        }
+        __syncthreads();
+        const uint32_t k = cnt[threadIdx.x];
+        if (k) {
+            const __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)threadIdx.x, __NV_E4M3);
+            const float v = __fmul_rn(__half2float(__half(hr)), __ldg(a.scales + b));
+            if (fabsf(v) <= FLT_MAX) {
+                const double d = (double)v * (double)a.dscale;
+                s1 += (double)k * d;
+                s2 += (double)k * (d * d);
+                n += k;
+                if (a.nbins > 0) {
+                    const float t = __fmul_rn(__fadd_rn(v, -a.vmin), a.hscale);
+                    atomicAdd(&a.hist[max(0, min((int)t, a.nbins - 1))], (unsigned long long)k);
+                }
+            } else {
+                nnf += k;
+            }
+        }
+        __syncthreads();   // the next item zeroes the counters
+    }
+    for (int o = 16; o; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+        nnf += __shfl_xor_sync(0xffffffffu, nnf, o);
+    }
+    __shared__ StatPartial wp[kStatsThreads / 32];
+    if (lane == 0) wp[warp] = StatPartial{s1, s2, n, nnf};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        StatPartial r = wp[0];
+        for (int w = 1; w < kStatsThreads / 32; ++w) {
+            r.s1 += wp[w].s1;
+            r.s2 += wp[w].s2;
+            r.n += wp[w].n;
+            r.nnf += wp[w].nnf;
+        }
+        a.partials[blockIdx.x] = r;
+    }
+}
+
 // Fixed-order merge of the block partials (deterministic for a given grid).
 __global__ void k_stats_final(const StatPartial *__restrict__ p, int nparts, float vmin, float vmax, float shift,
                               float dscale, vrc_stats *out)
@@ -499,9 +605,14 @@ vrc_status stats_launch_with(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *de
     const int hist = nbins == 0 ? 0 : (nbins <= kSmemBinsMax ? 1 : 2);
     const size_t smem = hist == 1 ? sizeof(uint32_t) * (nbins + 1) : 0;
     int used = 0;
-    if (g.dtype == VRC_F32) used = launch_stats<VRC_F32>(a, ctx->sm_count, grid, smem, hist, st);
-    else if (g.dtype == VRC_BF16) used = launch_stats<VRC_BF16>(a, ctx->sm_count, grid, smem, hist, st);
-    else used = launch_stats<VRC_FP8E4M3>(a, ctx->sm_count, grid, smem, hist, st);
+    if (g.dtype == VRC_F32) {
+        used = launch_stats<VRC_F32>(a, ctx->sm_count, grid, smem, hist, st);
+    } else if (g.dtype == VRC_BF16) {
+        used = launch_stats<VRC_BF16>(a, ctx->sm_count, grid, smem, hist, st);
+    } else {
+        k_stats_codes<<<grid, kStatsThreads, 0, st>>>(a);
+        used = grid;
+    }
     k_stats_final<<<1, 256, 0, st>>>(a.partials, used, c->vmin, c->vmax, a.shift, a.dscale, dev_out);
     count_launch(ctx, 2);
     VRC_CK(ctx, cudaGetLastError());

@@ -43,6 +43,24 @@ def test_e4m3_saturates_and_closed_forms():
     assert np.array_equal(oracle.e4m3_round(codes), codes.astype(np.float64))
 
 
+def test_e4m3_has_no_infinity():
+    """E4M3 (finite-only) has NaN as its one non-finite value: NaN and +-inf
+    round to NaN, while finite overflow saturates to +-448.  A stored cube
+    therefore keeps its non-finite voxels non-finite, and they do not set the
+    brick scale."""
+    got = oracle.e4m3_round(np.array([np.nan, np.inf, -np.inf, 3.0e38, -3.0e38], np.float32))
+    assert np.isnan(got[:3]).all() and list(got[3:]) == [448.0, -448.0]
+    v = np.full((4, 4, 4), 2.0, np.float32)
+    v[0, 0, 0], v[1, 2, 3], v[3, 3, 3] = np.inf, -np.inf, np.nan
+    s = oracle.brick_scales(v, 4)
+    assert s[0] == np.float32(2.0) / np.float32(448.0)
+    d = oracle.dequantize(v, "fp8", 4, s)
+    assert np.isnan(d[0, 0, 0]) and np.isnan(d[1, 2, 3]) and np.isnan(d[3, 3, 3])
+    assert np.all(d[np.isfinite(v)] == 2.0)
+    st = oracle.stats(d)
+    assert st["n_nonfinite"] == 3 and st["n"] == 61 and st["mean"] == 2.0
+
+
 def test_fp8_brick_scale_and_dequant():
     rng = np.random.default_rng(5)
     v = (rng.standard_normal((12, 10, 9)) * 7).astype(np.float32)
