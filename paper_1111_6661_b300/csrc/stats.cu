@@ -283,65 +283,99 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_stats(StatsA
 // formula as k_stats, one global add per code present).  One partial per
 // block, merged by k_stats_final like those of k_stats.
 constexpr int kLogCodeChunks = 6;
+
+// Work items of the code-count passes over an FP8 cube: runs of 2^lcpi chunks
+// of one brick (chunks as in k_stats: 256 16-byte vectors of interior rows).
+struct CodeItems {
+    int logVPR, logRPC, lcpi, ipb;
+    int64_t items;
+    uint32_t Pb, RPb, Ob;
+};
+
+__device__ __forceinline__ CodeItems code_items(const BrickGeom &g)
+{
+    CodeItems ci;
+    ci.logVPR = g.logB - 4;                          // 16 codes per vector
+    ci.logRPC = kLogChunk - ci.logVPR;
+    const int logCPB = 2 * g.logB - ci.logRPC;
+    ci.lcpi = min(kLogCodeChunks, logCPB);
+    ci.ipb = logCPB - ci.lcpi;
+    ci.items = g.nbricks << ci.ipb;
+    ci.Pb = (uint32_t)g.P;
+    ci.RPb = (uint32_t)g.R * ci.Pb;
+    ci.Ob = (uint32_t)g.O;
+    return ci;
+}
+
+// Add the codes of item `it` to cnt[256] (interior voxels inside the cube
+// only); returns the item's brick.  Every thread of the block takes part.
+__device__ __forceinline__ uint32_t count_codes(const uint8_t *__restrict__ pool, const BrickGeom &g,
+                                                const CodeItems &ci, int64_t it, uint32_t *cnt)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t b = (uint32_t)(it >> ci.ipb);
+    const uint32_t c0 = ((uint32_t)it & ((1u << ci.ipb) - 1)) << ci.lcpi;
+    const uint32_t bx = b % (uint32_t)g.nb[0], byz = b / (uint32_t)g.nb[0];
+    const uint32_t by = byz % (uint32_t)g.nb[1], bz = byz / (uint32_t)g.nb[1];
+    const bool clean = ((int64_t)(bx + 1) << g.logB) <= g.dims[0] && ((int64_t)(by + 1) << g.logB) <= g.dims[1] &&
+                       ((int64_t)(bz + 1) << g.logB) <= g.dims[2];
+    const uint8_t *bp = pool + (uint64_t)b * (uint64_t)g.brick_bytes;
+    for (uint32_t ch = c0 + warp; ch < c0 + (1u << ci.lcpi); ch += kStatsThreads / 32) {
+        const uint32_t lr0 = ch << ci.logRPC;
+        uint4 raw[kVecPerLane];
+#pragma unroll
+        for (int i = 0; i < kVecPerLane; ++i) {
+            const uint32_t j = lane + 32 * i;
+            const uint32_t lr = lr0 + (j >> ci.logVPR);
+            const uint32_t off = ((lr >> g.logB) + 1) * ci.RPb + ((lr & (g.B - 1)) + 1) * ci.Pb + ci.Ob +
+                                 ((j & ((1u << ci.logVPR) - 1)) << 4);
+            raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + off));
+        }
+#pragma unroll
+        for (int i = 0; i < kVecPerLane; ++i) {
+            int nvalid = 16;
+            if (!clean) {
+                const uint32_t j = lane + 32 * i;
+                const uint32_t lr = lr0 + (j >> ci.logVPR);
+                const int64_t gx0 = ((int64_t)bx << g.logB) + ((int64_t)(j & ((1u << ci.logVPR) - 1)) << 4);
+                const int64_t gy = ((int64_t)by << g.logB) + (lr & (g.B - 1));
+                const int64_t gz = ((int64_t)bz << g.logB) + (lr >> g.logB);
+                nvalid = (int)min((int64_t)16, g.dims[0] - gx0);
+                if (gy >= g.dims[1] || gz >= g.dims[2] || nvalid < 0) nvalid = 0;
+            }
+            const uint32_t w[4] = {raw[i].x, raw[i].y, raw[i].z, raw[i].w};
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                if (clean || e < nvalid) atomicAdd(&cnt[(w[e >> 2] >> (8 * (e & 3))) & 0xffu], 1u);
+        }
+    }
+    return b;
+}
+
+// Stored value of code q of brick b (FP8): fl32(e4m3(q) * scale_b).
+__device__ __forceinline__ float fp8_value(uint32_t q, float scale)
+{
+    const __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3);
+    return __fmul_rn(__half2float(__half(hr)), scale);
+}
+
 __global__ void __launch_bounds__(kStatsThreads) k_stats_codes(StatsArgs a)
 {
     static_assert(kStatsThreads == 256, "one thread per code");
     __shared__ uint32_t cnt[256];
     const BrickGeom &g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int logVPR = g.logB - 4;                     // 16 codes per 16-byte vector
-    const int logRPC = kLogChunk - logVPR;
-    const int logCPB = 2 * g.logB - logRPC;
-    const int lcpi = min(kLogCodeChunks, logCPB);     // chunks per item (log)
-    const int ipb = logCPB - lcpi;                     // items per brick (log)
-    const int64_t items = g.nbricks << ipb;
-    const uint32_t Pb = (uint32_t)g.P, RPb = (uint32_t)g.R * Pb, Ob = (uint32_t)g.O;
+    const CodeItems ci = code_items(g);
     double s1 = 0.0, s2 = 0.0;
     unsigned long long n = 0, nnf = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        const uint32_t b = (uint32_t)(it >> ipb);
-        const uint32_t c0 = ((uint32_t)it & ((1u << ipb) - 1)) << lcpi;
+    for (int64_t it = blockIdx.x; it < ci.items; it += gridDim.x) {
         cnt[threadIdx.x] = 0;
         __syncthreads();
-        const uint32_t bx = b % (uint32_t)g.nb[0], byz = b / (uint32_t)g.nb[0];
-        const uint32_t by = byz % (uint32_t)g.nb[1], bz = byz / (uint32_t)g.nb[1];
-        const bool clean = ((int64_t)(bx + 1) << g.logB) <= g.dims[0] && ((int64_t)(by + 1) << g.logB) <= g.dims[1] &&
-                           ((int64_t)(bz + 1) << g.logB) <= g.dims[2];
-        const uint8_t *bp = a.pool + (uint64_t)b * (uint64_t)g.brick_bytes;
-        for (uint32_t ch = c0 + warp; ch < c0 + (1u << lcpi); ch += kStatsThreads / 32) {
-            const uint32_t lr0 = ch << logRPC;
-            uint4 raw[kVecPerLane];
-#pragma unroll
-            for (int i = 0; i < kVecPerLane; ++i) {
-                const uint32_t j = lane + 32 * i;
-                const uint32_t lr = lr0 + (j >> logVPR);
-                const uint32_t off = ((lr >> g.logB) + 1) * RPb + ((lr & (g.B - 1)) + 1) * Pb + Ob +
-                                     ((j & ((1u << logVPR) - 1)) << 4);
-                raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + off));
-            }
-#pragma unroll
-            for (int i = 0; i < kVecPerLane; ++i) {
-                int nvalid = 16;
-                if (!clean) {
-                    const uint32_t j = lane + 32 * i;
-                    const uint32_t lr = lr0 + (j >> logVPR);
-                    const int64_t gx0 = ((int64_t)bx << g.logB) + ((int64_t)(j & ((1u << logVPR) - 1)) << 4);
-                    const int64_t gy = ((int64_t)by << g.logB) + (lr & (g.B - 1));
-                    const int64_t gz = ((int64_t)bz << g.logB) + (lr >> g.logB);
-                    nvalid = (int)min((int64_t)16, g.dims[0] - gx0);
-                    if (gy >= g.dims[1] || gz >= g.dims[2] || nvalid < 0) nvalid = 0;
-                }
-                const uint32_t w[4] = {raw[i].x, raw[i].y, raw[i].z, raw[i].w};
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    if (clean || e < nvalid) atomicAdd(&cnt[(w[e >> 2] >> (8 * (e & 3))) & 0xffu], 1u);
-            }
-        }
+        const uint32_t b = count_codes(a.pool, g, ci, it, cnt);
         __syncthreads();
         const uint32_t k = cnt[threadIdx.x];
         if (k) {
-            const __half_raw hr = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)threadIdx.x, __NV_E4M3);
-            const float v = __fmul_rn(__half2float(__half(hr)), __ldg(a.scales + b));
+            const float v = fp8_value(threadIdx.x, __ldg(a.scales + b));
             if (fabsf(v) <= FLT_MAX) {
                 const double d = (double)v * (double)a.dscale;
                 s1 += (double)k * d;
@@ -531,6 +565,41 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(
         if (sh[i]) atomicAdd(&a.hist[i], (unsigned long long)sh[i]);
 }
 
+// FP8 median, step 1: table[b * 256 + q] = number of interior voxels of brick
+// b stored with code q (zeroed by the caller).
+__global__ void __launch_bounds__(kStatsThreads) k_code_table(const uint8_t *__restrict__ pool, BrickGeom g,
+                                                             uint32_t *__restrict__ table)
+{
+    __shared__ uint32_t cnt[256];
+    const CodeItems ci = code_items(g);
+    for (int64_t it = blockIdx.x; it < ci.items; it += gridDim.x) {
+        cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t b = count_codes(pool, g, ci, it, cnt);
+        __syncthreads();
+        if (cnt[threadIdx.x]) atomicAdd(&table[(int64_t)b * 256 + threadIdx.x], cnt[threadIdx.x]);
+        __syncthreads();
+    }
+}
+
+// FP8 median, step 2 (one per radix digit): the radix-selection pass of
+// k_select_hist over the (brick, code) entries of the table, each counted
+// with its number of voxels instead of voxel by voxel.
+__global__ void k_select_codes(const uint32_t *__restrict__ table, const float *__restrict__ scales,
+                               int64_t nentries, SelArgs a)
+{
+    const uint32_t dmask = (1u << a.nbits) - 1u;
+    const int hshift = a.shift + a.nbits;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nentries; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = table[e];
+        if (!w) continue;
+        const float v = fp8_value((uint32_t)(e & 255), __ldg(scales + (e >> 8)));
+        if (!(fabsf(v) <= FLT_MAX)) continue;
+        const uint32_t k = ord_key(v == 0.f ? 0.f : v);   // -0 and +0 are one value
+        if (a.prefix_all || (k >> hshift) == a.prefix) atomicAdd(&a.hist[(k >> a.shift) & dmask], (unsigned long long)w);
+    }
+}
+
 int stats_grid(vrc_ctx *ctx) { return ctx->sm_count * 4; }
 
 // Persistent grid: as many blocks as fit on the SMs (at most grid_cap).
@@ -676,9 +745,21 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     if (!out) return VRC_E_INVAL;
     VRC_CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
+    // FP8: one pass counts each brick's codes; the radix passes then run over
+    // the (brick, code) entries with their counts
+    const bool codes = c->g.dtype == VRC_FP8E4M3;
+    const int64_t nentries = codes ? c->g.nbricks * 256 : 0;
     void *scr = nullptr;
-    if ((s = scratch_get(ctx, kSelMaxBins * sizeof(unsigned long long), &scr)) != VRC_OK) return s;
+    if ((s = scratch_get(ctx, kSelMaxBins * sizeof(unsigned long long) + nentries * sizeof(uint32_t), &scr)) != VRC_OK)
+        return s;
     unsigned long long *dh = (unsigned long long *)scr;
+    uint32_t *table = reinterpret_cast<uint32_t *>(dh + kSelMaxBins);
+    if (codes) {
+        VRC_CK(ctx, cudaMemsetAsync(table, 0, nentries * sizeof(uint32_t), st));
+        k_code_table<<<stats_grid(ctx), kStatsThreads, 0, st>>>((const uint8_t *)c->pool, c->g, table);
+        count_launch(ctx);
+        VRC_CK(ctx, cudaGetLastError());
+    }
     std::vector<unsigned long long> h(kSelMaxBins);
     SelArgs a;
     a.pool = (const uint8_t *)c->pool;
@@ -690,7 +771,6 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     int occ = 1;
     if (c->g.dtype == VRC_F32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_F32>, kStatsThreads, 0);
     else if (c->g.dtype == VRC_BF16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_BF16>, kStatsThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_FP8E4M3>, kStatsThreads, 0);
     const int grid = ctx->sm_count * std::max(occ, 1);
     // three digits of the 32-bit ordered key: 12, 10 and 10 bits
     const int shifts[3] = {20, 10, 0}, widths[3] = {12, 10, 10};
@@ -703,9 +783,11 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
         a.prefix = pass == 0 ? 0u : key >> (a.shift + a.nbits);
         const int nb = 1 << a.nbits;
         VRC_CK(ctx, cudaMemsetAsync(dh, 0, nb * sizeof(unsigned long long), st));
-        if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(a);
-        else if (c->g.dtype == VRC_BF16) k_select_hist<VRC_BF16><<<grid, kStatsThreads, 0, st>>>(a);
-        else k_select_hist<VRC_FP8E4M3><<<grid, kStatsThreads, 0, st>>>(a);
+        if (codes)
+            k_select_codes<<<(unsigned)std::min<int64_t>((nentries + 255) / 256, grid), 256, 0, st>>>(
+                table, c->scales, nentries, a);
+        else if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(a);
+        else k_select_hist<VRC_BF16><<<grid, kStatsThreads, 0, st>>>(a);
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
         VRC_CK(ctx, cudaMemcpyAsync(h.data(), dh, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));

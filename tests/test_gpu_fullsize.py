@@ -121,7 +121,7 @@ def test_fullsize_trilinear_mip(full):
 def test_fullsize_precision_storage(full, dtype):
     """The bench cube stored as bf16 / fp8 e4m3 (per-brick scale) in 256^3
     bricks: statistics over all 2^30 stored values against the oracle on the
-    dequantised cube (min/max and histogram exact, mean/std 1e-9), sampled
+    dequantised cube (min/max, histogram and median exact, mean/std 1e-9), sampled
     pixels of DVR and trilinear MIP renders at the fp32 tolerances."""
     import paper_1111_6661_b300 as vrc
     w, v, cams, tf, ctx, _ = full
@@ -135,6 +135,8 @@ def test_fullsize_precision_storage(full, dtype):
         assert abs(s["mean"] - ref["mean"]) <= 1e-9 * max(abs(ref["mean"]), ref["std"])
         assert abs(s["std"] - ref["std"]) <= 1e-9 * ref["std"]
         assert np.array_equal(h, oracle.histogram(dq, ref["min"], ref["max"], 1024))
+        k = (dq.size - 1) // 2
+        assert ctx.cube_median(cid) == float(np.partition(dq.reshape(-1), k)[k])
         del dq
         info = ctx.cube_info(cid)
         W, H = w["W"], w["H"]
