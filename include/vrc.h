@@ -295,7 +295,8 @@ vrc_status vrc_cube_stats_noalloc(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, 
  * match the digits chosen so far.  FP8 cubes take one pass over the cube that
  * counts each brick's 8-bit codes; the three radix passes then run over the
  * (brick, code) entries weighted by their counts (a stored fp8 value depends
- * only on its brick's scale and its code).  *out is HOST memory; waits for
+ * only on its brick's scale and its code).  bf16 keys have 16 significant
+ * bits, so two passes fix them.  *out is HOST memory; waits for
  * `stream`.  Errors: VRC_E_BADID, VRC_E_NONFINITE.
  */
 vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *stream);

@@ -776,7 +776,11 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     const int shifts[3] = {20, 10, 0}, widths[3] = {12, 10, 10};
     uint64_t rank = 0;
     uint32_t key = 0;
-    for (int pass = 0; pass < 3; ++pass) {
+    // bf16 keys carry 16 significant bits (the value's low 16 bits are 0, so the
+    // key's are 0 for positive values and 1 for negative ones): two passes fix
+    // bits 31..10 and with them the value
+    const int npass = c->g.dtype == VRC_BF16 ? 2 : 3;
+    for (int pass = 0; pass < npass; ++pass) {
         a.shift = shifts[pass];
         a.nbits = widths[pass];
         a.prefix_all = pass == 0;
@@ -811,6 +815,7 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
         rank -= acc;
         key |= (uint32_t)sel << a.shift;
     }
+    if (npass == 2) key |= (key & 0x80000000u) ? 0u : 0x3ffu;
     const uint32_t u = (key & 0x80000000u) ? (key & 0x7fffffffu) : ~key;
     float f;
     memcpy(&f, &u, 4);
