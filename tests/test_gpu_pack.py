@@ -60,9 +60,9 @@ def expected_brick(v: np.ndarray, B: int, b: int, dtype: str, scales) -> np.ndar
     return out
 
 
-def check_cube(ctx, v, B, dtype):
+def check_cube(ctx, v, B, dtype, src=None):
     dims = (v.shape[2], v.shape[1], v.shape[0])
-    cid = ctx.cube_upload(v, dtype, brick=B)
+    cid = ctx.cube_upload(v if src is None else src, dtype, brick=B)
     try:
         info = ctx.cube_info(cid)
         scales = oracle.brick_scales(v, B) if dtype == "fp8" else None
@@ -155,6 +155,21 @@ def test_nonfinite_voxels_quantised(ctx, dtype):
         assert np.array_equal(h, oracle.histogram(dq, ref["min"], ref["max"], 64))
     finally:
         ctx.cube_free(cid)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "fp8"])
+def test_device_source_off_16_bytes(ctx, dtype):
+    """A device source whose address is 4 bytes past a 16-byte boundary (a
+    tensor view): rows whose length is a multiple of 4 would allow 16-byte
+    loads, but the address does not, so the passes fall back to element
+    loads.  Same stored bytes as from an aligned source."""
+    import torch
+    v = cubegen.generate((64, 40, 24), 4, 48)
+    flat = torch.zeros(v.size + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(v.reshape(-1)).cuda()
+    src = flat[1:].view(v.shape)
+    assert src.data_ptr() % 16 == 4
+    check_cube(ctx, v, 32, dtype, src=src)
 
 
 def test_read_brick_errors(ctx):
