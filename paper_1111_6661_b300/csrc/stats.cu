@@ -69,7 +69,9 @@ __device__ __forceinline__ void decode16(const uint4 &raw, float scale, float *x
 
 // Measured on the 1024^3 fp32 cube with 4096 bins: 8 vectors in flight per
 // lane at 3 CTAs of 256 per SM (80 registers, no spills) 0.83 ms; 8 at 4 CTAs
-// (64 registers, spills) 0.84 ms; 4 at 4 or 3 CTAs 0.89-0.90 ms.
+// (64 registers, spills) 0.84 ms; 4 at 4 or 3 CTAs 0.89-0.90 ms; the next
+// chunk's 8 vectors loaded before the current chunk is accumulated (2 CTAs
+// per SM) 0.845 ms, with 4 + 4 vectors at 3 CTAs 0.94 ms.
 constexpr int kVecPerLane = 8;                 // 16-byte vectors in flight per lane
 constexpr int kLogChunk = 8;                   // 256 vectors per warp iteration (32 lanes x 8)
 constexpr int kStatsCtasPerSm = 3;
