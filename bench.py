@@ -355,6 +355,36 @@ def run_gpu(args, w):
                 "note": "skip_empty=1: samples whose 8^3 macro-cell is transparent under the TF are not fetched; "
                         "the image is bit-identical"}
 
+    # axis-aligned nearest MIP at native resolution (an orthographic view along
+    # z, NX x NY pixels, step 1: one sample per voxel, each voxel read once):
+    # the ray-casting case that HBM bounds; algorithmic bytes = the stored
+    # bytes of the samples
+    mip_native = None
+    if not args.no_mip_native:
+        import cubegen
+        NX, NY, NZ = w["dims"]
+        cam_n = [cubegen.ortho_z_camera(w["dims"])]
+        rc_n = vrc.raycfg(NX, NY, 1.0, "nearest")
+        img_n = torch.empty((1, NY, NX), dtype=torch.float32, device=dev)
+        ctx.render_mip(cid, cam_n, rc_n, out=img_n)
+        torch.cuda.synchronize()
+        reps = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            ctx.render_mip(cid, cam_n, rc_n, out=img_n)
+        e1.record(st)
+        torch.cuda.synchronize()
+        n_ms = e0.elapsed_time(e1) / reps
+        n_samp = ctx.last_render_samples()
+        n_bytes = n_samp * {"f32": 4, "bf16": 2, "fp8": 1}[w["storage"]]
+        n_gbs = n_bytes / (n_ms / 1e3) / 1e9
+        mip_native = {"ms": n_ms, "samples": n_samp, "samples_per_s": n_samp / (n_ms / 1e3), "hbm_gbs": n_gbs,
+                      "hbm_frac": n_gbs / pk["hbm_gbs"], "hbm_peak_kind": pk_kind,
+                      "note": "orthographic MIP along z at native resolution (%dx%d pixels, step 1, nearest): one "
+                              "sample per voxel, each voxel read once; algorithmic bytes = stored bytes of the "
+                              "samples; cube larger than L2" % (NX, NY)}
+
     # latency of one view alone: each orbit view rendered by its own call
     # (n_views = 1), CUDA events around each call, three rounds over the orbit
     view_ms = []
@@ -471,7 +501,7 @@ def run_gpu(args, w):
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
                              "binding": render_binding()},
                 "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
-                "view_latency": view_latency,
+                "view_latency": view_latency, "mip_native": mip_native,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms, "median_ms": median_ms,
                             "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
                             "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind},
@@ -479,6 +509,50 @@ def run_gpu(args, w):
         print(json.dumps(line), flush=True)
     if cid is not None:
         ctx.cube_free(cid)
+    ctx.close()
+
+
+# ------------------------------------------------- axis-aligned native MIP
+def run_mip_native(args):
+    """Orthographic nearest MIP along z at native resolution (one sample per
+    voxel, each voxel read once) on the 1024^3 bench cube (or --dims): the
+    ray-casting case that HBM bounds.  Samples/s and GB/s of stored bytes."""
+    import torch
+
+    import cubegen
+    import paper_1111_6661_b300 as vrc
+    w = workload("dvr1024")
+    if args.dims:
+        w["dims"] = tuple(args.dims)
+    v = cubegen.generate(w["dims"], w["n_sources"], w["seed"])
+    storage = args.storage
+    ctx = vrc.Context(0)
+    cid = ctx.cube_upload(v, storage, brick=w["brick"])
+    NX, NY, NZ = w["dims"]
+    cam = [cubegen.ortho_z_camera(w["dims"])]
+    rc = vrc.raycfg(NX, NY, 1.0, "nearest")
+    img = torch.empty((1, NY, NX), dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        ctx.render_mip(cid, cam, rc, out=img)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.render_mip(cid, cam, rc, out=img)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n = ctx.last_render_samples()
+    pk, pk_kind = peaks()
+    gbs = n * {"f32": 4, "bf16": 2, "fp8": 1}[storage] / (ms / 1e3) / 1e9
+    print(json.dumps({"metric": "ray samples/s (MIP, nearest, axis-aligned native resolution)",
+                      "value": n / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms, "steps": args.steps,
+                      "warmup": args.warmup, "dtype": storage, "data": "synthetic",
+                      "config": {"workload": "mip_native", "dims": list(w["dims"]), "image": [NX, NY], "step": 1.0,
+                                 "sampling": "nearest", "storage": storage},
+                      "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "hbm_peak_kind": pk_kind}), flush=True)
+    ctx.cube_free(cid)
     ctx.close()
 
 
@@ -736,6 +810,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-skip-variant", action="store_true")
     ap.add_argument("--no-view-latency", action="store_true")
+    ap.add_argument("--no-mip-native", action="store_true")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="mip_native: storage type")
     ap.add_argument("--path", default="fused", choices=["fused", "slab"], help="render path of the timed step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
@@ -753,6 +829,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "mip_native":
+        return run_mip_native(args)
     if args.workload == "ooc":
         return run_ooc(args)
     if args.workload == "serving":

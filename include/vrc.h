@@ -231,7 +231,8 @@ vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t
  * resident cube into host memory `dst` of at least `dst_bytes` bytes (Sec. 2:
  * sub-cubes; the quantised storage of the precision form).  Layout: R = B + 2
  * planes (local z = -1..B) of R rows (local y = -1..B) of P = B + 2*O elements
- * of esize bytes (4 fp32, 2 bf16 bits, 1 e4m3 code; O = 16 / esize), the
+ * of esize bytes (4 fp32, 2 bf16 bits, 1 e4m3 code; O = 32 / esize: rows
+ * start interior voxels on 32-byte boundaries), the
  * voxel at local x at element O + x of its row: x = -1 and x = B are the
  * halo, elements before and after them are padding (0).  Halo voxels outside
  * the cube repeat the nearest edge voxel; FP8 codes use this brick's scale.

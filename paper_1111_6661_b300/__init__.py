@@ -150,12 +150,12 @@ class Context:
     def cube_read_brick(self, cube_id: int, brick: int) -> np.ndarray:
         """Stored form of one brick: array (R, R, P) of float32 / uint16 (bf16
         bits) / uint8 (e4m3 codes), R = B + 2 planes and rows (local -1..B),
-        local x at element O + x of a row (O = 16 / element size)."""
+        local x at element O + x of a row (O = 32 / element size)."""
         info = self.cube_info(cube_id)
         B = info["brick"]
         dt = {"f32": np.float32, "bf16": np.uint16, "fp8": np.uint8}[info["storage"]]
         es = np.dtype(dt).itemsize
-        R, P = B + 2, B + 2 * (16 // es)
+        R, P = B + 2, B + 2 * (32 // es)
         out = np.empty((R, R, P), dtype=dt)
         self._check(self._lib.vrc_cube_read_brick(self.h, cube_id, brick, ctypes.c_void_p(out.ctypes.data),
                                                   out.nbytes))

@@ -290,7 +290,7 @@ Cube *find_cube(vrc_ctx *ctx, int64_t id)
     return it == ctx->cubes.end() ? nullptr : it->second;
 }
 
-bool make_geom(int64_t nx, int64_t ny, int64_t nz, int32_t B, int32_t dtype, BrickGeom *g)
+bool make_geom(int64_t nx, int64_t ny, int64_t nz, int32_t B, int32_t dtype, BrickGeom *g, int32_t align)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0 || nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20)) return false;
     if (dtype < 0 || dtype > 2) return false;
@@ -311,7 +311,7 @@ bool make_geom(int64_t nx, int64_t ny, int64_t nz, int32_t B, int32_t dtype, Bri
     g->esize = dtype == VRC_F32 ? 4 : (dtype == VRC_BF16 ? 2 : 1);
     for (int a = 0; a < 3; ++a) g->nb[a] = (int32_t)((g->dims[a] + B - 1) / B);
     g->nbricks = (int64_t)g->nb[0] * g->nb[1] * g->nb[2];
-    g->O = 16 / g->esize;
+    g->O = align / g->esize;   // the interior of every row starts `align` bytes in
     g->P = B + 2 * g->O;
     g->R = B + 2;
     g->brick_elems = (int64_t)g->P * g->R * g->R;

@@ -276,12 +276,12 @@ __device__ __forceinline__ uint4 pack_chunk(const float (&x)[Chunk<DT>::n], floa
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Pass 2: write every stored row of every brick as 16-byte chunks: the left
-// chunk (padding, then the halo column lx = -1), B * esize / 16 interior
-// chunks, the right chunk (the halo column lx = B, then padding).  Halo rows
-// and columns clamp to the cube edge; padding is 0.  A warp writes one row at
-// a time; interior source values are read as 16-byte vectors where the rows
-// allow them.
+// Pass 2: write every stored row of every brick as 16-byte chunks: L = O *
+// esize / 16 left chunks (padding, then the halo column lx = -1 as the last
+// element), B * esize / 16 interior chunks, L right chunks (the halo column
+// lx = B as the first element, then padding).  Halo rows and columns clamp to
+// the cube edge; padding is 0.  A warp writes one row at a time; interior
+// source values are read as 16-byte vectors where the rows allow them.
 template <int DT>
 __global__ void __launch_bounds__(256) k_brick_pack(const float *__restrict__ src, BrickGeom g, int split,
                                                     const float *__restrict__ scales, void *pool)
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) k_brick_pack(const float *__restrict__ sr
     char *bp = reinterpret_cast<char *>(pool) + b * g.brick_bytes;
     const int R = g.R, lane = threadIdx.x & 31;
     const int64_t NX = g.dims[0], x0 = (int64_t)bx * g.B;
-    const int nin = g.B / N;
+    const int nin = g.B / N, L = g.O / N;
     const bool vec = (NX & 3) == 0 && x0 + g.B <= NX && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
     const int64_t row_bytes = (int64_t)g.P * g.esize;
     for (int row = blockIdx.y * (blockDim.x / 32) + threadIdx.x / 32; row < R * R; row += split * (blockDim.x / 32)) {
@@ -322,15 +322,16 @@ __global__ void __launch_bounds__(256) k_brick_pack(const float *__restrict__ sr
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h)
-                if (j0 + 32 * h < nin) out[1 + j0 + 32 * h] = pack_chunk<DT>(x[h], scale);
+                if (j0 + 32 * h < nin) out[L + j0 + 32 * h] = pack_chunk<DT>(x[h], scale);
         }
-        if (lane < 2) {
+        if (lane < 2 * L) {
+            // lanes 0 .. L-1: left chunks (halo at the end of chunk L-1); lanes L .. 2L-1: right chunks
             float x[N];
 #pragma unroll
             for (int e = 0; e < N; ++e) x[e] = 0.f;
-            if (lane == 0) x[N - 1] = __ldg(rowp + clamp64(x0 - 1, NX));
-            else x[0] = __ldg(rowp + clamp64(x0 + g.B, NX));
-            out[lane == 0 ? 0 : 1 + nin] = pack_chunk<DT>(x, scale);
+            if (lane == L - 1) x[N - 1] = __ldg(rowp + clamp64(x0 - 1, NX));
+            if (lane == L) x[0] = __ldg(rowp + clamp64(x0 + g.B, NX));
+            out[lane < L ? lane : nin + lane] = pack_chunk<DT>(x, scale);
         }
     }
 }
@@ -699,7 +700,7 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
     if (!ctx || !src || !cube_id) return VRC_E_INVAL;
     if (src_on_device != 0 && src_on_device != 1) return set_err(ctx, VRC_E_INVAL, "src_on_device must be 0 or 1");
     BrickGeom g;
-    if (!make_geom(nx, ny, nz, brick, storage, &g))
+    if (!make_geom(nx, ny, nz, brick, storage, &g, 32))
         return set_err(ctx, VRC_E_INVAL, "bad dims/storage/brick (%lld %lld %lld, %d, %d)", (long long)nx,
                        (long long)ny, (long long)nz, storage, brick);
     VRC_CK(ctx, cudaSetDevice(ctx->device));
@@ -779,7 +780,7 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
 {
     if (!ctx || !cube_id) return VRC_E_INVAL;
     BrickGeom g;
-    if (!make_geom(nx, ny, nz, brick, VRC_F32, &g)) return set_err(ctx, VRC_E_INVAL, "bad dims/brick");
+    if (!make_geom(nx, ny, nz, brick, VRC_F32, &g, 16)) return set_err(ctx, VRC_E_INVAL, "bad dims/brick");
     if (n_host_bricks <= 0 || n_host_bricks > g.nbricks) return set_err(ctx, VRC_E_INVAL, "bad n_host_bricks");
     if (ring_bricks < 0 || ring_bricks > 4096) return set_err(ctx, VRC_E_INVAL, "bad ring_bricks");
     if (ring_bricks == 0) ring_bricks = 8;

@@ -150,19 +150,29 @@ __device__ __forceinline__ float nearest_in_brick(const CubeView &cv, const uint
     return DT == VRC_FP8E4M3 ? __fmul_rn(v, scale) : v;
 }
 
+// Voxel (ix, iy, iz) (inside the cube) read from the resident brick holding it.
+template <int DT>
+__device__ __forceinline__ float voxel_resident(const CubeView &cv, int ix, int iy, int iz)
+{
+    const int bx = ix >> cv.logB, by = iy >> cv.logB, bz = iz >> cv.logB;
+    const int b = brick_index(cv, bx, by, bz);
+    const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
+    return nearest_in_brick<DT>(cv, cv.pool + (int64_t)b * cv.brick_bytes, ix, iy, iz, bx << cv.logB, by << cv.logB,
+                                bz << cv.logB, scale);
+}
+
+// Nearest voxel index of coordinate p on an axis of n voxels.
+// (floor and conversion in one round-down conversion: the same integer as
+// (int)floorf(p) for every p, NaN giving 0 in both.)
+__device__ __forceinline__ int nearest_index(float p, int n) { return min(max(__float2int_rd(p), 0), n - 1); }
+
 // Sample at p from the resident brick that contains voxel floor(p).
 template <int SAMPLING, int DT>
 __device__ __forceinline__ float sample_resident(const CubeView &cv, float px, float py, float pz)
 {
     if (SAMPLING == VRC_NEAREST) {
-        const int ix = min(max((int)floorf(px), 0), cv.dims[0] - 1);
-        const int iy = min(max((int)floorf(py), 0), cv.dims[1] - 1);
-        const int iz = min(max((int)floorf(pz), 0), cv.dims[2] - 1);
-        const int bx = ix >> cv.logB, by = iy >> cv.logB, bz = iz >> cv.logB;
-        const int b = brick_index(cv, bx, by, bz);
-        const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
-        return nearest_in_brick<DT>(cv, cv.pool + (int64_t)b * cv.brick_bytes, ix, iy, iz, bx << cv.logB,
-                                    by << cv.logB, bz << cv.logB, scale);
+        return voxel_resident<DT>(cv, nearest_index(px, cv.dims[0]), nearest_index(py, cv.dims[1]),
+                                  nearest_index(pz, cv.dims[2]));
     } else {
         const AxisT ax = axis_tri(px, cv.dims[0]), ay = axis_tri(py, cv.dims[1]), az = axis_tri(pz, cv.dims[2]);
         const int bx = ax.ip >> cv.logB, by = ay.ip >> cv.logB, bz = az.ip >> cv.logB;

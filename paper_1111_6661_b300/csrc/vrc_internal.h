@@ -35,7 +35,11 @@ struct BrickGeom {
     int64_t brick_elems, brick_bytes;
 };
 
-bool make_geom(int64_t nx, int64_t ny, int64_t nz, int32_t B, int32_t dtype, BrickGeom *g);
+// Brick geometry.  Rows hold P = B + 2*O elements: O - 1 padding elements,
+// the halo voxel, B interior voxels, the halo voxel, O - 1 padding elements,
+// with O * esize = align bytes (32 for resident bricks, so that interior rows
+// start on 32-byte sectors; 16 for streamed bricks, which cross the host link).
+bool make_geom(int64_t nx, int64_t ny, int64_t nz, int32_t B, int32_t dtype, BrickGeom *g, int32_t align);
 
 struct vrc_ctx;
 

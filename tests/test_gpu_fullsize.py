@@ -101,6 +101,19 @@ def test_fullsize_dvr_orbit(full):
         assert ctx.last_render_samples() == n_fused
 
 
+def test_fullsize_native_nearest_mip(full):
+    """Orthographic nearest MIP along z at native resolution (1024x1024,
+    step 1): every pixel equals its column maximum, bit for bit, and every
+    voxel is sampled once."""
+    import paper_1111_6661_b300 as vrc
+    w, v, cams, tf, ctx, cid = full
+    NX, NY, NZ = w["dims"]
+    img = ctx.render_mip(cid, [cubegen.ortho_z_camera(w["dims"])], vrc.raycfg(NX, NY, 1.0, "nearest"))
+    torch.cuda.synchronize()
+    assert ctx.last_render_samples() == v.size
+    assert np.array_equal(img[0].cpu().numpy(), v.max(axis=0))
+
+
 def test_fullsize_trilinear_mip(full):
     import paper_1111_6661_b300 as vrc
     w, v, cams, tf, ctx, cid = full

@@ -44,7 +44,7 @@ def expected_brick(v: np.ndarray, B: int, b: int, dtype: str, scales) -> np.ndar
     iy = np.clip(by * B + span, 0, NY - 1)
     iz = np.clip(bz * B + span, 0, NZ - 1)
     blk = v[np.ix_(iz, iy, ix)]
-    O = 16 // ESIZE[dtype]
+    O = 32 // ESIZE[dtype]
     R, P = B + 2, B + 2 * O
     if dtype == "f32":
         out = np.zeros((R, R, P), dtype=np.uint32)
