@@ -104,6 +104,31 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
                 neval += nv;
                 if (nv < kNearU) break;
             }
+        } else if (TEXAXIS < 0 && MODE == 0 && SAMPLING == VRC_NEAREST) {
+            // nearest MIP along any other ray: the same branch-free groups of
+            // kNearU samples (indices clamped, so every load is in bounds);
+            // 8 perspective 1080p views of a 1024^3 cube 21.5 ms against
+            // 26.4 ms one sample at a time
+            for (int k = 0;; k += kNearU) {
+                const float kf = (float)k;
+                float sv[kNearU];
+                int nv = 0;
+#pragma unroll
+                for (int u = 0; u < kNearU; ++u) {
+                    const float tk = __fadd_rn(tin, __fmul_rn(__fadd_rn(kf, (float)u + 0.5f), step));
+                    const bool valid = tk < tout;
+                    const float v = sample_resident<SAMPLING, DT>(J.cv, __fadd_rn(o[0], __fmul_rn(tk, d[0])),
+                                                                  __fadd_rn(o[1], __fmul_rn(tk, d[1])),
+                                                                  __fadd_rn(o[2], __fmul_rn(tk, d[2])));
+                    sv[u] = valid ? v : -FLT_MAX;
+                    nv += valid;
+                }
+#pragma unroll
+                for (int u = 0; u < kNearU; ++u) m = fmaxf(m, sv[u]);
+                nsamp += nv;
+                neval += nv;
+                if (nv < kNearU) break;
+            }
         } else {
 #pragma unroll 1
             for (int k = 0;; ++k) {
