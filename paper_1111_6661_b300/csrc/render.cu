@@ -407,8 +407,10 @@ __device__ __forceinline__ int brick_key_of(const CubeView &cv, const ViewParams
 // the total alpha A_front + (1 - A_front) A_partial reaches term, A_front read
 // from the running image), and write the brick's partial image.  Bricks of one
 // wavefront (equal visibility key) never share a ray, so their partials are
-// disjoint.  `slots` maps item.slot to brick storage.
-template <int MODE, int SAMPLING, int DT>
+// disjoint.  `slots` maps item.slot to brick storage.  TEX: trilinear
+// samples from the brick's texture copy (two gathers, the same texels and
+// weights as the global-load sampler; resident cubes with render copies).
+template <int MODE, int SAMPLING, int DT, bool TEX>
 __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__restrict__ jobs,
                                                             const BrickItem *__restrict__ items, int64_t n_items,
                                                             const uint8_t *slot_base, int64_t slot_bytes,
@@ -435,6 +437,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__res
         const int ox = bx << cv.logB, oy = by << cv.logB, oz = bz << cv.logB;
         const uint8_t *bp = slot_base + (int64_t)it.slot * slot_bytes;
         const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + it.brick) : 1.f;
+        const unsigned long long th =
+            TEX ? __ldg(cv.tex + 2 * (int64_t)cv.nb[0] * cv.nb[1] * cv.nb[2] + it.brick) : 0ull;
         const int bkey = abs(bx - J.vp.ec[0]) + abs(by - J.vp.ec[1]) + abs(bz - J.vp.ec[2]);
         float o[3], d[3], tin, tout;
         const int64_t pix = (int64_t)py * J.vp.W + px;
@@ -490,6 +494,9 @@ __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__res
                         s = nearest_in_brick<DT>(cv, bp, min(max((int)floorf(p[0]), 0), cv.dims[0] - 1),
                                                  min(max((int)floorf(p[1]), 0), cv.dims[1] - 1),
                                                  min(max((int)floorf(p[2]), 0), cv.dims[2] - 1), ox, oy, oz, scale);
+                    } else if (TEX) {
+                        s = tri_tex<DT, 2>(th, axis_tri(p[0], cv.dims[0]), axis_tri(p[1], cv.dims[1]),
+                                           axis_tri(p[2], cv.dims[2]), ox, oy, oz, scale);
                     } else {
                         s = tri_in_brick<DT>(cv, bp, axis_tri(p[0], cv.dims[0]), axis_tri(p[1], cv.dims[1]),
                                              axis_tri(p[2], cv.dims[2]), ox, oy, oz, scale);
@@ -805,30 +812,35 @@ int occupancy(int mode, int sampling, int dt, bool tex, bool skip = false)
     return mode == 0 ? pick_occ2<0>(sampling, dt, tex, skip)() : pick_occ2<1>(sampling, dt, tex, skip)();
 }
 
-template <int MODE, int SAMPLING, int DT>
+template <int MODE, int SAMPLING, int DT, bool TEX>
 void launch_bricks_t(int64_t n, cudaStream_t st, const JobDesc *jobs, const BrickItem *items, const uint8_t *slot_base,
                      int64_t slot_bytes, const float *running, float *partial, unsigned long long *samples)
 {
-    k_render_bricks<MODE, SAMPLING, DT><<<(unsigned)n, kThreads, 0, st>>>(jobs, items, n, slot_base, slot_bytes,
-                                                                         running, partial, samples);
+    k_render_bricks<MODE, SAMPLING, DT, TEX><<<(unsigned)n, kThreads, 0, st>>>(jobs, items, n, slot_base, slot_bytes,
+                                                                              running, partial, samples);
 }
 typedef void (*bricks_fn)(int64_t, cudaStream_t, const JobDesc *, const BrickItem *, const uint8_t *, int64_t,
                           const float *, float *, unsigned long long *);
 template <int MODE>
-bricks_fn pick_bricks2(int sampling, int dt)
+bricks_fn pick_bricks2(int sampling, int dt, bool tex)
 {
     if (sampling == VRC_NEAREST) {
-        if (dt == VRC_F32) return launch_bricks_t<MODE, VRC_NEAREST, VRC_F32>;
-        if (dt == VRC_BF16) return launch_bricks_t<MODE, VRC_NEAREST, VRC_BF16>;
-        return launch_bricks_t<MODE, VRC_NEAREST, VRC_FP8E4M3>;
+        if (dt == VRC_F32) return launch_bricks_t<MODE, VRC_NEAREST, VRC_F32, false>;
+        if (dt == VRC_BF16) return launch_bricks_t<MODE, VRC_NEAREST, VRC_BF16, false>;
+        return launch_bricks_t<MODE, VRC_NEAREST, VRC_FP8E4M3, false>;
     }
-    if (dt == VRC_F32) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_F32>;
-    if (dt == VRC_BF16) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_BF16>;
-    return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_FP8E4M3>;
+    if (tex) {
+        if (dt == VRC_F32) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_F32, true>;
+        if (dt == VRC_BF16) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_BF16, true>;
+        return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_FP8E4M3, true>;
+    }
+    if (dt == VRC_F32) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_F32, false>;
+    if (dt == VRC_BF16) return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_BF16, false>;
+    return launch_bricks_t<MODE, VRC_TRILINEAR, VRC_FP8E4M3, false>;
 }
-bricks_fn pick_bricks(int mode, int sampling, int dt)
+bricks_fn pick_bricks(int mode, int sampling, int dt, bool tex)
 {
-    return mode == 0 ? pick_bricks2<0>(sampling, dt) : pick_bricks2<1>(sampling, dt);
+    return mode == 0 ? pick_bricks2<0>(sampling, dt, tex) : pick_bricks2<1>(sampling, dt, tex);
 }
 
 // Scratch layout helpers: [counter | samples | tf | jobs | items ...]
@@ -1128,7 +1140,8 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
             VRC_CK(ctx, cudaMemsetAsync(partial, 0, sizeof(float) * n, st));
         }
         count_launch(ctx, mode == 0 ? 2 : 0);
-        bricks_fn bf = pick_bricks(mode, rc->sampling, c->g.dtype);
+        // resident bricks with render copies sample them through texture gathers
+        bricks_fn bf = pick_bricks(mode, rc->sampling, c->g.dtype, !zerocopy && !c->streamed && c->dtex != nullptr);
         const int64_t npx = (int64_t)n_views * npix;
         for (size_t w = 0; w + 1 < plan.wave_item_begin.size(); ++w) {
             const int64_t b0 = plan.wave_item_begin[w], b1 = plan.wave_item_begin[w + 1];
@@ -1217,7 +1230,7 @@ vrc_status render_streamed(vrc_ctx *ctx, Cube *c, SortLastPlan &plan, const vrc_
     cudaEventRecord(entry, st);             // earlier work on `st` may still use the ring
     cudaStreamWaitEvent(cs, entry, 0);
     vrc_status status = VRC_OK;
-    bricks_fn bf = pick_bricks(mode, rc.sampling, VRC_F32);
+    bricks_fn bf = pick_bricks(mode, rc.sampling, VRC_F32, false);
     size_t made = 0;
     for (size_t i = 0; i < chunks.size() && status == VRC_OK; ++i) {
         const Chunk &ch = chunks[i];
