@@ -325,7 +325,7 @@ def run_gpu(args, w):
     sm_max = pk.get("sm_max_mhz", 2032.0)
     fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved_tflops = samples_per_step * DVR_FLOPS_PER_SAMPLE / (render_ms / 1e3) / 1e12
-    stats_bytes = info["dims"][0] * info["dims"][1] * info["dims"][2] * (4 if w["storage"] == "f32" else 2)
+    stats_bytes = info["dims"][0] * info["dims"][1] * info["dims"][2] * {"f32": 4, "bf16": 2, "fp8": 1}[w["storage"]]
     stats_gbs = stats_bytes / (stats_ms / 1e3) / 1e9
 
     # exact median of the same cube (three radix-selection passes; not part of the step)
@@ -486,10 +486,12 @@ def run_gpu(args, w):
         cpu = {"value": rate, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{npix} random pixels of {nv} views ({nsamp} samples, {el:.1f} s), FP64 oracle, OpenMP"}
 
+    # the committed captures are of the default step (fp32 cube, fused path, 32 views)
+    profiled = w["name"] == "dvr1024" and w["storage"] == "f32" and args.path == "fused" and len(cams) == 32
     if rank == 0:
         line = {"metric": "ray samples/s (DVR, trilinear)", "value": value, "unit": "samples/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w["storage"],
                 "data": "synthetic",
                 "config": dict(workload_config(w, len(cams)),
                                **{"samples_per_step": samples_per_step, "parallelism": f"replicas{ws}",
@@ -497,9 +499,10 @@ def run_gpu(args, w):
                                   "l2": "inputs larger than L2 (cube bricks %.1f GB > 126 MB)" % (info["bytes"] / 1e9)}),
                 "roofline": {"bound": "alu", "kernel": "k_render_fused (DVR)", "achieved": achieved_tflops,
                              "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / fp32_peak_tflops,
-                             "traffic": render_traffic(), "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
+                             "traffic": render_traffic() if profiled else None,
+                             "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
-                             "binding": render_binding()},
+                             "binding": render_binding() if profiled else None},
                 "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
                 "view_latency": view_latency, "mip_native": mip_native,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms, "median_ms": median_ms,
@@ -525,7 +528,7 @@ def run_mip_native(args):
     if args.dims:
         w["dims"] = tuple(args.dims)
     v = cubegen.generate(w["dims"], w["n_sources"], w["seed"])
-    storage = args.storage
+    storage = args.storage or "f32"
     ctx = vrc.Context(0)
     cid = ctx.cube_upload(v, storage, brick=w["brick"])
     NX, NY, NZ = w["dims"]
@@ -811,8 +814,10 @@ def main():
     ap.add_argument("--no-skip-variant", action="store_true")
     ap.add_argument("--no-view-latency", action="store_true")
     ap.add_argument("--no-mip-native", action="store_true")
-    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"], help="mip_native: storage type")
-    ap.add_argument("--path", default="fused", choices=["fused", "slab"], help="render path of the timed step")
+    ap.add_argument("--storage", default=None, choices=["f32", "bf16", "fp8"],
+                    help="storage type of the cube (default workload: fp32; mip_native: fp32)")
+    ap.add_argument("--path", default="fused", choices=["fused", "slab", "sortlast"],
+                    help="render path of the timed step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
     ap.add_argument("--dims", type=int, nargs=3, default=None, help="precision/ooc: cube dims")
@@ -838,6 +843,8 @@ def main():
     w = workload(args.workload)
     if args.views:
         w["views"] = args.views
+    if args.storage:
+        w["storage"] = args.storage
     if args.dims:   # profiling: a smaller cube of the same recipe (sources scaled with the volume)
         scale = args.dims[0] * args.dims[1] * args.dims[2] / float(np.prod(w["dims"]))
         w["dims"] = tuple(args.dims)
