@@ -605,3 +605,25 @@ def test_slab_path_rejects_what_it_does_not_cover(ctx, cube128):
         with pytest.raises(vrc.VrcError):
             ctx.render_mip(cid, cam, rc)
     ctx.cube_free(cid)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_axis_aligned_nearest_mip_every_direction(ctx, dtype):
+    """Orthographic nearest MIP along +-x, +-y and +-z (rays with two zero
+    direction components take the fixed-index loop), ragged cube and bricks,
+    step 1 and 0.7: every pixel equals the oracle's bit for bit."""
+    v = cubegen.generate((48, 40, 36), 5, 61)
+    dims = (48, 40, 36)
+    B = 16
+    cid = ctx.cube_upload(v, dtype, brick=B)
+    c = [d / 2 for d in dims]
+    cams = []
+    for axis in range(3):
+        for sign in (1.0, -1.0):
+            eye = list(c)
+            eye[axis] = c[axis] - sign * 2 * dims[axis]
+            up = [0.0, 1.0, 0.0] if axis != 1 else [0.0, 0.0, 1.0]
+            cams.append(cubegen.camera("ortho", eye, c, up, ortho_height=float(max(dims))))
+    for step in (1.0, 0.7):
+        render_check_mip(ctx, v, cid, cams, 44, 44, step, "nearest", dtype=dtype, B=B)
+    ctx.cube_free(cid)
