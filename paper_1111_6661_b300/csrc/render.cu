@@ -129,6 +129,49 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
                 neval += nv;
                 if (nv < kNearU) break;
             }
+        } else if (TEXAXIS < 0 && MODE == 1 && SAMPLING == VRC_NEAREST) {
+            // nearest DVR: U samples' loads in flight (indices clamped, so
+            // every load is in bounds), then composited in ray order with the
+            // same termination test; samples past the end or after termination
+            // are loaded but not composited
+            constexpr int U = 4;   // 8 spills at 48 registers
+            bool done = false;
+            for (int k = 0; !done; k += U) {
+                const float kf = (float)k;
+                float sv[U];
+                bool vv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float tk = __fadd_rn(tin, __fmul_rn(__fadd_rn(kf, (float)u + 0.5f), step));
+                    vv[u] = tk < tout;
+                    sv[u] = sample_resident<SAMPLING, DT>(J.cv, __fadd_rn(o[0], __fmul_rn(tk, d[0])),
+                                                          __fadd_rn(o[1], __fmul_rn(tk, d[1])),
+                                                          __fadd_rn(o[2], __fmul_rn(tk, d[2])));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (!vv[u]) {
+                        done = true;
+                        break;
+                    }
+                    ++nsamp;
+                    ++neval;
+                    const float sn = sv[u];
+                    if (sn == sn && !(sn <= J.skip_below)) {
+                        const float4 c = classify(s_tf, sn, J.vmin, J.inv_range);
+                        const float a = opacity(c.w, step, J.opacity_correction);
+                        const float w = (1.f - A) * a;
+                        cr = fmaf(w, c.x, cr);
+                        cg = fmaf(w, c.y, cg);
+                        cb = fmaf(w, c.z, cb);
+                        A += w;
+                    }
+                    if (A >= J.term) {
+                        done = true;
+                        break;
+                    }
+                }
+            }
         } else {
 #pragma unroll 1
             for (int k = 0;; ++k) {
