@@ -185,6 +185,12 @@ def test_read_brick_errors(ctx):
         ctx.cube_free(cid)
     with pytest.raises(vrc.VrcError):
         ctx.cube_read_brick(cid, 0)               # freed id
+    sid = ctx.cube_create_streamed((32, 32, 32), 16, 8)
+    try:
+        with pytest.raises(vrc.VrcError, match="UNSUPPORTED"):
+            ctx.cube_read_brick(sid, 0)           # a streamed cube's bricks live in host slots
+    finally:
+        ctx.cube_free(sid)
 
 
 def test_largest_brick_edge(ctx):
