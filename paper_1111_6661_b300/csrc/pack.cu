@@ -405,7 +405,7 @@ __device__ __forceinline__ typename TexElem<T>::type tex_value(const uint8_t *br
         return reinterpret_cast<const T *>(brick)[e];
 }
 
-constexpr int kFillK = 9;   // 16-texel steps per lane in flight (a B = 256 row is 258 texels: 17 steps)
+constexpr int kFillK = 17;   // 16-texel steps per lane in flight (a B = 256 row is 258 texels: 17 steps)
 template <typename T>
 __global__ void __launch_bounds__(256) k_fill_copy(const uint8_t *__restrict__ pool, BrickGeom g,
                                                    const unsigned long long *__restrict__ surfs)
