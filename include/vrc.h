@@ -204,7 +204,10 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
 vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const float *brick_with_halo);
 
 /* Release a cube.  Waits for the device (the memory may be reused at once).
- * VRC_E_BUSY while serving requests still reference it. */
+ * VRC_E_BUSY while serving requests still reference it.  Like every call
+ * except vrc_submit / vrc_poll, it must not overlap another call on the same
+ * context from another host thread: a statistics or render call in flight on
+ * another thread may still be reading the cube's host-side record. */
 vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id);
 
 /*
@@ -279,7 +282,10 @@ vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vr
  * the call performs no cudaMalloc, cudaFree or other allocation.  Devices whose
  * statistics pass needs more scratch than that are refused with VRC_E_NOMEM.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset by the host
+ * application invalidates the kept address: do not call this entry point on
+ * that device again afterwards.
  * All calls share the array: calls whose work overlaps on the GPU (different
  * streams, or other host threads) race and give wrong results, so serialise
  * them (e.g. one stream).  Nothing in the array needs clearing between calls.

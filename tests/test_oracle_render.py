@@ -245,6 +245,46 @@ def test_composite_over_properties():
     assert np.array_equal(oracle.composite(x, y, "mip"), np.maximum(x, y))
 
 
+def test_composite_over_values():
+    """Sort-last gathering of partial images (Sec. 2) by the premultiplied
+    "over" operator, pinned by value: out = front + (1 - front.A) * back on
+    every channel, alpha included.  Dyadic inputs make every product and sum
+    exact in binary64, so the expected values are exact."""
+    # front colour c=(1, 0.5, 0.25) at alpha a=0.5, back colour c'=(0.5, 1, 0.75) at alpha b=0.25
+    a, b = 0.5, 0.25
+    front = np.array([[1.0 * a, 0.5 * a, 0.25 * a, a]])
+    back = np.array([[0.5 * b, 1.0 * b, 0.75 * b, b]])
+    want = np.array([[0.5 + 0.5 * 0.125, 0.25 + 0.5 * 0.25, 0.125 + 0.5 * 0.1875, 0.5 + 0.5 * 0.25]])
+    assert np.array_equal(oracle.composite(front, back), want)
+    # the back layer shows through in proportion to the front's transparency,
+    # not to the back's own alpha: with an opaque back layer the result's
+    # alpha is 1 whatever the front
+    front2 = np.array([[0.0, 0.0, 0.375, 0.375]])
+    back2 = np.array([[0.25, 0.5, 0.125, 1.0]])
+    assert np.array_equal(oracle.composite(front2, back2), np.array([[0.15625, 0.3125, 0.453125, 1.0]]))
+    # an opaque front hides the back completely
+    opaque = np.array([[0.75, 0.5, 0.25, 1.0]])
+    assert np.array_equal(oracle.composite(opaque, back2), opaque)
+    # the operator is not commutative: swapping the layers changes the colour
+    assert not np.array_equal(oracle.composite(back, front), oracle.composite(front, back))
+    # a chain of n layers of uniform alpha a has total alpha 1 - (1 - a)^n
+    layer = np.array([[0.25, 0.25, 0.25, 0.25]])
+    acc = np.zeros((1, 4))
+    for n in range(1, 6):
+        acc = oracle.composite(acc, layer)
+        assert acc[0, 3] == 1 - 0.75 ** n
+
+
+def test_composite_max_values():
+    """MIP partial images combine by maximum; -FLT_MAX (a ray that missed the
+    brick) is the identity, and ties keep the common value."""
+    f32max = float(np.finfo(np.float32).max)
+    front = np.array([1.5, -f32max, 2.0, -3.0, 7.25])
+    back = np.array([0.5, 4.0, 2.0, -f32max, 7.5])
+    assert np.array_equal(oracle.composite(front, back, "mip"), np.array([1.5, 4.0, 2.0, -3.0, 7.5]))
+    assert np.array_equal(oracle.composite(back, front, "mip"), np.array([1.5, 4.0, 2.0, -3.0, 7.5]))
+
+
 def test_dvr_fragile_window_brackets_result():
     v = cubegen.generate((24, 24, 24), 3, 5)
     cam = cubegen.orbit_cameras((24, 24, 24), 4)[1]

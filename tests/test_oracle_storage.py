@@ -84,3 +84,23 @@ def test_bf16_dequant_is_per_voxel():
     v = rng.standard_normal((5, 6, 7)).astype(np.float32)
     d = oracle.dequantize(v, "bf16", 4)
     assert np.array_equal(d, torch.from_numpy(v).to(torch.bfloat16).float().numpy())
+
+
+def test_fp8_scale_counts_the_halo():
+    """The per-brick FP8 scale is absmax/448 over everything the brick stores,
+    its one-voxel halo included: a magnitude that sits just outside brick 0
+    (in the neighbouring brick's interior, within brick 0's halo) sets brick
+    0's scale, while a brick that neither holds it nor has it in its halo
+    keeps its own interior maximum."""
+    B = 16
+    v = np.full((32, 32, 48), 1.0, np.float32)
+    v[5, 5, B] = 5000.0                 # x = 16: brick 1's interior, brick 0's halo
+    s = oracle.brick_scales(v, B)
+    assert s.size == 3 * 2 * 2
+    assert s[0] == np.float32(5000.0) / np.float32(448.0)   # halo voxel
+    assert s[1] == np.float32(5000.0) / np.float32(448.0)   # interior voxel
+    assert s[2] == np.float32(1.0) / np.float32(448.0)      # x in [32, 48): neither
+    # a brick whose scale came from its halo codes its own voxels on that scale
+    d = oracle.dequantize(v, "fp8", B, s)
+    q = np.float32(oracle.e4m3_round(np.array([np.float32(1.0) / s[0]], np.float32))[0])
+    assert d[0, 0, 0] == np.float32(q * s[0])
