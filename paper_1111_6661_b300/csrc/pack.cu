@@ -389,20 +389,38 @@ void finish_metadata(Cube *c, const std::vector<double> &bsum)
 // partly written sectors behind (a warp per row measured 4.2 ms on a 1024^3
 // fp32 cube, with 2x the DRAM reads).  R = B + 2 is even.  The surface
 // handles come from `surfs`.
-// FP8 bricks are copied as binary16 code values (every e4m3 value is exact in
-// binary16), so the texture unit returns them as fp32 with no conversion
-// instructions in the sampler; the per-brick scale is applied after the lerps.
-struct Fp8AsHalf {};
-template <typename T> struct TexElem { using type = T; };
-template <> struct TexElem<Fp8AsHalf> { using type = unsigned short; };
+// BF16 and FP8 copies pack two stored layers per texel (layer j holds layers
+// j and j + 1, the lower layer in the low bits; B + 1 layers), so that the
+// renderer's single 2x2 gather returns a whole trilinear footprint: BF16 as
+// 32-bit texels of two bf16 bit patterns, FP8 as 16-bit texels of two e4m3
+// codes (the per-brick scale is applied after the lerps).
+struct Bf16Pair {};
+struct Fp8Pair {};
+template <typename T> struct TexElem {
+    using type = T;
+    static constexpr bool pair = false;
+};
+template <> struct TexElem<Bf16Pair> {
+    using type = unsigned int;
+    static constexpr bool pair = true;
+};
+template <> struct TexElem<Fp8Pair> {
+    using type = unsigned short;
+    static constexpr bool pair = true;
+};
 
+// Texel of stored element e (S = elements per stored layer).
 template <typename T>
-__device__ __forceinline__ typename TexElem<T>::type tex_value(const uint8_t *brick, int64_t e)
+__device__ __forceinline__ typename TexElem<T>::type tex_value(const uint8_t *brick, int64_t e, int64_t S)
 {
-    if constexpr (std::is_same<T, Fp8AsHalf>::value)
-        return __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)brick[e], __NV_E4M3).x;
-    else
+    if constexpr (std::is_same<T, Bf16Pair>::value) {
+        const unsigned short *h = reinterpret_cast<const unsigned short *>(brick);
+        return (unsigned int)h[e] | ((unsigned int)h[e + S] << 16);
+    } else if constexpr (std::is_same<T, Fp8Pair>::value) {
+        return (unsigned short)(brick[e] | (brick[e + S] << 8));
+    } else {
         return reinterpret_cast<const T *>(brick)[e];
+    }
 }
 
 constexpr int kFillK = 17;   // 16-texel steps per lane in flight (a B = 256 row is 258 texels: 17 steps)
@@ -412,7 +430,9 @@ __global__ void __launch_bounds__(256) k_fill_copy(const uint8_t *__restrict__ p
 {
     using E = typename TexElem<T>::type;
     const int R = g.R, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
-    const int64_t pairs = (int64_t)R * (R >> 1), total = pairs * g.nbricks;
+    const int NL = TexElem<T>::pair ? R - 1 : R;   // layers of the copy
+    const int64_t S = (int64_t)R * g.P;
+    const int64_t pairs = (int64_t)NL * (R >> 1), total = pairs * g.nbricks;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < total; w += nw) {
         const int64_t b = w / pairs;
@@ -426,7 +446,7 @@ __global__ void __launch_bounds__(256) k_fill_copy(const uint8_t *__restrict__ p
 #pragma unroll
             for (int k = 0; k < kFillK; ++k) {
                 const int u = u0 + hl + 16 * k;
-                val[k] = u < R ? tex_value<T>(brick, e0 + u) : E();
+                val[k] = u < R ? tex_value<T>(brick, e0 + u, S) : E();
             }
 #pragma unroll
             for (int k = 0; k < kFillK; ++k) {
@@ -576,8 +596,11 @@ void release_textures(vrc_ctx *ctx, Cube *c)
 vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
 {
     const BrickGeom &g = c->g;
-    const int64_t tex_esize = g.dtype == VRC_FP8E4M3 ? 2 : g.esize;
-    const int64_t arr_bytes = tex_esize * (int64_t)g.R * g.R * g.R;
+    // fp32: one texel per stored voxel, R layers; bf16 / fp8: two stored
+    // layers per texel (32 / 16 bits), R - 1 layers
+    const int64_t tex_esize = g.dtype == VRC_F32 ? 4 : 2 * g.esize;
+    const int64_t tex_layers = g.dtype == VRC_F32 ? g.R : g.R - 1;
+    const int64_t arr_bytes = tex_esize * (int64_t)g.R * g.R * tex_layers;
     const int64_t per_copy = arr_bytes * g.nbricks + (1 << 20);
     // leave room in the budget for the render scratch of a large multi-view call
     const int64_t reserve = (int64_t)2 << 30;
@@ -589,8 +612,8 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
     ctx->used.fetch_add(per_copy);
     c->tex_bytes += per_copy;
     cudaChannelFormatDesc desc = g.dtype == VRC_F32 ? cudaCreateChannelDesc<float>()
-                               : (g.dtype == VRC_BF16 ? cudaCreateChannelDesc<unsigned short>()
-                                                      : cudaCreateChannelDescHalf());
+                               : (g.dtype == VRC_BF16 ? cudaCreateChannelDesc<unsigned int>()
+                                                      : cudaCreateChannelDesc<unsigned short>());
     const uint64_t key = tex_array_key(g);
     c->h_tex.assign(4 * g.nbricks, 0ull);
     for (int64_t b = 0; b < g.nbricks; ++b) {
@@ -599,7 +622,7 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
         if (!tex_array_take(ctx, key, &a)) {
             cache_trim(ctx, std::max<int64_t>(0, ctx->budget - ctx->used.load()));
             a.bytes = arr_bytes;
-            cudaError_t e = cudaMalloc3DArray(&a.arr, &desc, make_cudaExtent(g.R, g.R, g.R),
+            cudaError_t e = cudaMalloc3DArray(&a.arr, &desc, make_cudaExtent(g.R, g.R, tex_layers),
                                               cudaArrayLayered | cudaArraySurfaceLoadStore);
             cudaResourceDesc rd = {};
             rd.resType = cudaResourceTypeArray;
@@ -637,8 +660,8 @@ vrc_status launch_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
     const uint8_t *pool = (const uint8_t *)c->pool;
     const unsigned grid = (unsigned)ctx->sm_count * 8;
     if (g.dtype == VRC_F32) k_fill_copy<float><<<grid, 256, 0, st>>>(pool, g, surfs);
-    else if (g.dtype == VRC_BF16) k_fill_copy<unsigned short><<<grid, 256, 0, st>>>(pool, g, surfs);
-    else k_fill_copy<Fp8AsHalf><<<grid, 256, 0, st>>>(pool, g, surfs);
+    else if (g.dtype == VRC_BF16) k_fill_copy<Bf16Pair><<<grid, 256, 0, st>>>(pool, g, surfs);
+    else k_fill_copy<Fp8Pair><<<grid, 256, 0, st>>>(pool, g, surfs);
     count_launch(ctx);
     VRC_CK(ctx, cudaGetLastError());
     c->tex_axes |= 1 << 2;

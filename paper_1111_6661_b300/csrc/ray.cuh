@@ -183,88 +183,72 @@ __device__ __forceinline__ float sample_resident(const CubeView &cv, float px, f
     }
 }
 
-// 2x2 texel footprint of layer `layer` of a 2D layered texture, gathered at the
-// integer coordinate (u, v): with point sampling and unnormalised coordinates
-// the footprint is texels (u-1, v-1) .. (u, v) exactly, returned as
-// x = (u-1, v), y = (u, v), z = (u, v-1), w = (u-1, v-1).
-template <int DT>
-__device__ __forceinline__ float4 gather4(unsigned long long tex, int layer, float u, float v)
+// Render copies (one 2D-layered texture per brick, layers along z; local
+// voxel (lx, ly, lz) at texel (lx+1, ly+1) of layer lz+1).  With point sampling
+// and unnormalised coordinates a 2x2 gather at the integer coordinate (u, v)
+// returns texels (u-1, v-1) .. (u, v) exactly, as x = (u-1, v), y = (u, v),
+// z = (u, v-1), w = (u-1, v-1).
+//   fp32: one texel per stored voxel; the 2x2x2 trilinear footprint takes two
+//         gathers, one per layer.
+//   bf16: texel (u, v) of layer j packs the stored voxels of layers j (low 16
+//         bits) and j + 1 (high 16 bits) as one 32-bit texel;
+//   fp8:  it packs their e4m3 codes as one 16-bit texel (layer j in the low
+//         byte).
+// For bf16 and fp8 one gather therefore returns the whole footprint (the
+// copies hold B + 1 layers), and the texture unit moves half the gathers.
+__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t t)
 {
-    float4 r;
-    if (DT == VRC_F32 || DT == VRC_FP8E4M3) {   // fp32 texels, or fp8 codes stored as binary16
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)t, __NV_E4M3);
+    return __half22float2(__half2(h));
+}
+
+// The 2x2 footprints of layers `layer` (g0) and `layer + 1` (g1) at (u, v),
+// as fp32 values (fp8: code values, the brick scale not yet applied).
+template <int DT>
+__device__ __forceinline__ void gather_pair(unsigned long long tex, int layer, float u, float v, float4 &g0, float4 &g1)
+{
+    if (DT == VRC_F32) {
         asm volatile("tld4.r.a2d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
-                     : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                     : "=f"(g0.x), "=f"(g0.y), "=f"(g0.z), "=f"(g0.w)
                      : "l"(tex), "r"(layer), "f"(u), "f"(v));
+        asm volatile("tld4.r.a2d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
+                     : "=f"(g1.x), "=f"(g1.y), "=f"(g1.z), "=f"(g1.w)
+                     : "l"(tex), "r"(layer + 1), "f"(u), "f"(v));
     } else {
         uint32_t a, b, c, d;
         asm volatile("tld4.r.a2d.v4.u32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %7}];"
                      : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
                      : "l"(tex), "r"(layer), "f"(u), "f"(v));
-        r = make_float4(__uint_as_float(a << 16), __uint_as_float(b << 16), __uint_as_float(c << 16),
-                        __uint_as_float(d << 16));   // bf16 bits
+        if (DT == VRC_BF16) {
+            g0 = make_float4(__uint_as_float(a << 16), __uint_as_float(b << 16), __uint_as_float(c << 16),
+                             __uint_as_float(d << 16));
+            g1 = make_float4(__uint_as_float(a & 0xffff0000u), __uint_as_float(b & 0xffff0000u),
+                             __uint_as_float(c & 0xffff0000u), __uint_as_float(d & 0xffff0000u));
+        } else {
+            const float2 fa = e4m3x2_to_float2(a), fb = e4m3x2_to_float2(b), fc = e4m3x2_to_float2(c),
+                         fd = e4m3x2_to_float2(d);
+            g0 = make_float4(fa.x, fb.x, fc.x, fd.x);
+            g1 = make_float4(fa.y, fb.y, fc.y, fd.y);
+        }
     }
-    return r;
 }
 
-// Trilinear sample through two texture gathers from the copy of brick b whose
-// layers run along AXIS (0 x, 1 y, 2 z).  In that copy local voxel l sits at
-// texel (l[a1]+1, l[a2]+1, layer l[AXIS]+1), (a1, a2) = (x, y) / (y, z) / (z, x)
-// for AXIS = z / x / y.  The corner values are regrouped so that the lerps run
-// in x, then y, then z order, as in the global-load sampler.
-template <int DT, int AXIS>
+// Trilinear sample of a brick with origin (ox, oy, oz) from its render copy:
+// footprint (l, l+1) on an axis is gathered at coordinate l + 2 (layer l + 1).
+// The lerps run in x, then y, then z order, as in the global-load sampler, so
+// both give the same value bit for bit.
+template <int DT>
 __device__ __forceinline__ float tri_tex(unsigned long long t, const AxisT &ax, const AxisT &ay, const AxisT &az,
                                          int ox, int oy, int oz, float scale)
 {
-    const int l[3] = {ax.i0 - ox, ay.i0 - oy, az.i0 - oz};
-    constexpr int A1 = AXIS == 2 ? 0 : (AXIS == 0 ? 1 : 2);
-    constexpr int A2 = AXIS == 2 ? 1 : (AXIS == 0 ? 2 : 0);
-    // footprint (l, l+1) on texel axis k is gathered at coordinate l + 2
-    const float4 g0 = gather4<DT>(t, l[AXIS] + 1, (float)(l[A1] + 2), (float)(l[A2] + 2));
-    const float4 g1 = gather4<DT>(t, l[AXIS] + 2, (float)(l[A1] + 2), (float)(l[A2] + 2));
-    // gather order: x = (a1 lo, a2 hi), y = (a1 hi, a2 hi), z = (a1 hi, a2 lo), w = (a1 lo, a2 lo)
-    float v[2][2][2];   // v[dz][dy][dx]
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float4 gg = h ? g1 : g0;
-        const float q[2][2] = {{gg.w, gg.x}, {gg.z, gg.y}};   // q[a1 offset][a2 offset]
-#pragma unroll
-        for (int i1 = 0; i1 < 2; ++i1)
-#pragma unroll
-            for (int i2 = 0; i2 < 2; ++i2) {
-                int d[3];
-                d[AXIS] = h;
-                d[A1] = i1;
-                d[A2] = i2;
-                v[d[2]][d[1]][d[0]] = q[i1][i2];
-            }
-    }
-    const float c00 = fmaf(ax.f, v[0][0][1] - v[0][0][0], v[0][0][0]);
-    const float c10 = fmaf(ax.f, v[0][1][1] - v[0][1][0], v[0][1][0]);
-    const float c01 = fmaf(ax.f, v[1][0][1] - v[1][0][0], v[1][0][0]);
-    const float c11 = fmaf(ax.f, v[1][1][1] - v[1][1][0], v[1][1][0]);
+    float4 g0, g1;
+    gather_pair<DT>(t, az.i0 - oz + 1, (float)(ax.i0 - ox + 2), (float)(ay.i0 - oy + 2), g0, g1);
+    // footprint corners: w = (x0, y0), z = (x1, y0), x = (x0, y1), y = (x1, y1)
+    const float c00 = fmaf(ax.f, g0.z - g0.w, g0.w), c10 = fmaf(ax.f, g0.y - g0.x, g0.x);
+    const float c01 = fmaf(ax.f, g1.z - g1.w, g1.w), c11 = fmaf(ax.f, g1.y - g1.x, g1.x);
     const float c0 = fmaf(ay.f, c10 - c00, c00), c1 = fmaf(ay.f, c11 - c01, c01);
     const float val = fmaf(az.f, c1 - c0, c0);
     return DT == VRC_FP8E4M3 ? val * scale : val;
-}
-
-// Per-ray cache of the current brick's texture handle (bricks change rarely).
-struct TexCache {
-    int b = -1;
-    unsigned long long t = 0;
-};
-
-template <int DT, int AXIS>
-__device__ __forceinline__ float sample_resident_tex(const CubeView &cv, TexCache &tc, float px, float py, float pz)
-{
-    const AxisT ax = axis_tri(px, cv.dims[0]), ay = axis_tri(py, cv.dims[1]), az = axis_tri(pz, cv.dims[2]);
-    const int bx = ax.ip >> cv.logB, by = ay.ip >> cv.logB, bz = az.ip >> cv.logB;
-    const int b = brick_index(cv, bx, by, bz);
-    if (b != tc.b) {
-        tc.b = b;
-        tc.t = __ldg(cv.tex + b);
-    }
-    const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
-    return tri_tex<DT, AXIS>(tc.t, ax, ay, az, bx << cv.logB, by << cv.logB, bz << cv.logB, scale);
 }
 
 // Transfer function: 256 RGBA entries, linear between entries.

@@ -230,8 +230,7 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
                     const int b = (bz * cv.nb[1] + by) * cv.nb[0] + bx;
                     const unsigned long long th = __ldg(tex + b);
                     const float scale = DT == VRC_FP8E4M3 ? __ldg(cv.scales + b) : 1.f;
-                    s = tri_tex<DT, (TEXAXIS < 0 ? 0 : TEXAXIS)>(th, ax, ay, az, bx << cv.logB, by << cv.logB,
-                                                                 bz << cv.logB, scale);
+                    s = tri_tex<DT>(th, ax, ay, az, bx << cv.logB, by << cv.logB, bz << cv.logB, scale);
                 } else {
                     s = sample_resident<SAMPLING, DT>(J.cv, p0, p1, p2);
                 }
@@ -329,8 +328,7 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
             const float u = __fsub_rn(f0, c0), v = __fsub_rn(f1, c1);
             const int layer = (int)f2 - zo;
             if (!kReuse || layer != pl || u != pu || v != pv) {
-                g0 = gather4<DT>(th, layer, u, v);
-                g1 = gather4<DT>(th, layer + 1, u, v);
+                gather_pair<DT>(th, layer, u, v, g0, g1);
                 pl = layer;
                 pu = u;
                 pv = v;
@@ -538,7 +536,7 @@ __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__res
                                                  min(max((int)floorf(p[1]), 0), cv.dims[1] - 1),
                                                  min(max((int)floorf(p[2]), 0), cv.dims[2] - 1), ox, oy, oz, scale);
                     } else if (TEX) {
-                        s = tri_tex<DT, 2>(th, axis_tri(p[0], cv.dims[0]), axis_tri(p[1], cv.dims[1]),
+                        s = tri_tex<DT>(th, axis_tri(p[0], cv.dims[0]), axis_tri(p[1], cv.dims[1]),
                                            axis_tri(p[2], cv.dims[2]), ox, oy, oz, scale);
                     } else {
                         s = tri_in_brick<DT>(cv, bp, axis_tri(p[0], cv.dims[0]), axis_tri(p[1], cv.dims[1]),
