@@ -251,22 +251,44 @@ __device__ __forceinline__ float tri_tex(unsigned long long t, const AxisT &ax, 
     return DT == VRC_FP8E4M3 ? val * scale : val;
 }
 
-// Transfer function: 256 RGBA entries, linear between entries.
+// Transfer function: 256 RGBA entries, linear between entries.  Every
+// operation is rounded on its own (explicit intrinsics, so the compiler cannot
+// contract a product into a later sum differently in different kernels): all
+// renderers give the same colour for the same sample, bit for bit.  The four
+// channel lerps run as packed f32x2 fused multiply-adds (each lane rounds as
+// fmaf does).
 __device__ __forceinline__ float4 classify(const float4 *tf, float s, float vmin, float inv_range)
 {
-    float u = (s - vmin) * inv_range;
+    float u = __fmul_rn(__fsub_rn(s, vmin), inv_range);
     u = fminf(fmaxf(u, 0.f), 1.f);
-    const float x = u * 255.f;
+    const float x = __fmul_rn(u, 255.f);
     const int j = min((int)x, 254);
-    const float f = x - (float)j;
+    const float f = __fsub_rn(x, (float)j);
     const float4 a = tf[j], b = tf[j + 1];
-    return make_float4(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y), fmaf(f, b.z - a.z, a.z),
-                       fmaf(f, b.w - a.w, a.w));
+    const float2 m1 = make_float2(-1.f, -1.f), ff = make_float2(f, f);
+    const float2 a01 = make_float2(a.x, a.y), a23 = make_float2(a.z, a.w);
+    const float2 rg = __ffma2_rn(ff, __ffma2_rn(a01, m1, make_float2(b.x, b.y)), a01);   // a + f (b - a)
+    const float2 ba = __ffma2_rn(ff, __ffma2_rn(a23, m1, make_float2(b.z, b.w)), a23);
+    return make_float4(rg.x, rg.y, ba.x, ba.y);
 }
 
 __device__ __forceinline__ float opacity(float a, float step, int correct)
 {
     return correct ? 1.f - __powf(fmaxf(1.f - a, 0.f), step) : a;
+}
+
+// Front-to-back premultiplied compositing: C += (1 - A) a c, A += (1 - A) a,
+// with w = (1 - A) a rounded once and used for every channel.
+struct OverAcc {
+    float2 rg = make_float2(0.f, 0.f);
+    float b = 0.f, A = 0.f;
+};
+__device__ __forceinline__ void over(OverAcc &acc, const float4 &c, float step, int correct)
+{
+    const float w = __fmul_rn(__fsub_rn(1.f, acc.A), opacity(c.w, step, correct));
+    acc.rg = __ffma2_rn(make_float2(w, w), make_float2(c.x, c.y), acc.rg);
+    acc.b = fmaf(w, c.z, acc.b);
+    acc.A = __fadd_rn(acc.A, w);
 }
 
 // ------------------------------------------------------------------ work items

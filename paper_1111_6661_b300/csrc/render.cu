@@ -30,7 +30,8 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
     const int64_t pix = (int64_t)py * J.vp.W + px;
     const unsigned long long *tex =
         TEXAXIS >= 0 ? J.cv.tex + (int64_t)TEXAXIS * J.cv.nb[0] * J.cv.nb[1] * J.cv.nb[2] : nullptr;
-    float m = -FLT_MAX, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+    float m = -FLT_MAX;
+    OverAcc acc;
     if (hit) {
         const float step = J.step;
         // reciprocals for the macro-cell exit estimate (a guess, verified with
@@ -157,16 +158,9 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
                     ++nsamp;
                     ++neval;
                     const float sn = sv[u];
-                    if (sn == sn && !(sn <= J.skip_below)) {
-                        const float4 c = classify(s_tf, sn, J.vmin, J.inv_range);
-                        const float a = opacity(c.w, step, J.opacity_correction);
-                        const float w = (1.f - A) * a;
-                        cr = fmaf(w, c.x, cr);
-                        cg = fmaf(w, c.y, cg);
-                        cb = fmaf(w, c.z, cb);
-                        A += w;
-                    }
-                    if (A >= J.term) {
+                    if (sn == sn && !(sn <= J.skip_below))
+                        over(acc, classify(s_tf, sn, J.vmin, J.inv_range), step, J.opacity_correction);
+                    if (acc.A >= J.term) {
                         done = true;
                         break;
                     }
@@ -241,69 +235,77 @@ __device__ __forceinline__ void trace_fused(const JobDesc &J, const float4 *s_tf
                 } else {
                     // s <= skip_below gives alpha exactly 0 under the TF: the over step
                     // would add zero, so the lookup is not made (exact)
-                    if (s == s && !(s <= J.skip_below)) {
-                        const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
-                        const float a = opacity(c.w, step, J.opacity_correction);
-                        const float w = (1.f - A) * a;
-                        cr = fmaf(w, c.x, cr);
-                        cg = fmaf(w, c.y, cg);
-                        cb = fmaf(w, c.z, cb);
-                        A += w;
-                    }
-                    if (A >= J.term) break;
+                    if (s == s && !(s <= J.skip_below))
+                        over(acc, classify(s_tf, s, J.vmin, J.inv_range), step, J.opacity_correction);
+                    if (acc.A >= J.term) break;
                 }
             }
         }
     }
     if (MODE == 0) J.out[pix] = m;
-    else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(cr, cg, cb, A);
+    else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(acc.rg.x, acc.rg.y, acc.b, acc.A);
 }
 
 // One ray of the fused path on the texture copies.  A sample belongs to the
 // brick of voxel clamp(floor(p)); along one ray the binary32 positions are
-// monotone on every axis, so the samples of one brick are consecutive and
-// leaving it is decided by one compare per axis against the face the ray moves
-// towards (faces on the cube's border are infinite).  Brick index, texture
-// handle and origin are recomputed only when a sample leaves the brick (one
-// loop, so the lanes of a warp stay in step).  Texel coordinates are formed in
-// binary32 from floor(p - 0.5) (exact small integers): every sample reads the
-// same texels with the same weights as the per-sample lookup of trace_fused.
+// monotone on every axis, so the samples of one brick are consecutive.  When
+// the ray enters a brick, the first sample past the brick (past one of the
+// faces the ray moves towards, faces on the cube's border being infinite, or
+// past the ray's end) is found once, from a slab estimate corrected with the
+// exact binary32 sample positions; each sample then compares one counter
+// (one loop, so the lanes of a warp stay in step).  Texel coordinates are
+// formed in binary32 from floor(p - 0.5) (exact small integers): every sample
+// reads the same texels with the same weights as the per-sample lookup of
+// trace_fused.  Positions, weights and lerps use packed f32x2 instructions
+// where the operands pair up; each lane rounds as the scalar instruction does,
+// so every value is unchanged.
 template <int MODE, int DT>
 __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, int px, int py, uint32_t &nsamp)
 {
     float o[3], d[3], tin, tout;
     const bool hit = ray_setup(J.vp, J.cv.fdims, px, py, o, d, tin, tout);
     const int64_t pix = (int64_t)py * J.vp.W + px;
-    float m = -FLT_MAX, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+    float m = -FLT_MAX;
+    OverAcc acc;
     if (hit) {
         const float step = J.step;
         const CubeView &cv = J.cv;
+        const float2 m1 = make_float2(-1.f, -1.f);
+        // t of the sample whose k + 0.5 is kh, as stated (binary32, every operation rounded)
+        auto t_at = [&](float kh) { return __fadd_rn(tin, __fmul_rn(kh, step)); };
+        const float inv_step = __frcp_rn(step);
+        // samples k = 0 .. n-1 have t_k < tout; kh_end = n + 0.5 (estimate, then exact;
+        // t_k grows with k, and rays hold fewer than 2^22 samples, so kh is exact)
+        float kh_end = fmaxf(ceilf(__fmul_rn(tout - tin, inv_step) - 0.5f), 0.f) + 0.5f;
+        while (kh_end > 0.5f && !(t_at(kh_end - 1.f) < tout)) kh_end -= 1.f;
+        while (t_at(kh_end) < tout) kh_end += 1.f;
         const bool neg0 = d[0] < 0.f, neg1 = d[1] < 0.f, neg2 = d[2] < 0.f;
-        // exit faces; the initial values make the first sample enter its brick
-        float E0 = neg0 ? INFINITY : -INFINITY, E1 = neg1 ? INFINITY : -INFINITY, E2 = neg2 ? INFINITY : -INFINITY;
-        float c0 = 0.f, c1 = 0.f, scale = 1.f;
+        const float id0 = d[0] != 0.f ? __frcp_rn(d[0]) : 0.f, id1 = d[1] != 0.f ? __frcp_rn(d[1]) : 0.f,
+                    id2 = d[2] != 0.f ? __frcp_rn(d[2]) : 0.f;
+        float E0 = 0.f, E1 = 0.f, E2 = 0.f;   // exit faces of the current brick
+        float scale = 1.f, kh_stop = 0.5f;    // kh_stop: first sample past the current brick
+        float2 mc = make_float2(0.f, 0.f);    // -(texel origin) of the brick on x and y
         int zo = 0;
         unsigned long long th = 0;
         // fp32 MIP: texels of the previous sample's 2x2x2 cell, reused when the
         // next sample falls in the same cell (step < 1).  Measured: +7% for fp32
-        // MIP; for DVR and for 2-byte texels the extra live registers cost as
-        // much as the saved gathers or more (bf16 MIP spills and halves).
+        // MIP; for DVR and for packed texels the extra live registers cost as
+        // much as the saved gathers or more.
         constexpr bool kReuse = MODE == 0 && DT == VRC_F32;
         float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
         float pu = -1.f, pv = -1.f;
         int pl = -1;
-        float kh = 0.5f;   // k + 0.5, exact: rays have fewer than 2^22 samples
 #pragma unroll 1
-        for (;;) {
-            const float t = __fadd_rn(tin, __fmul_rn(kh, step));
-            if (!(t < tout)) break;
-            const float p0 = __fadd_rn(o[0], __fmul_rn(t, d[0]));
-            const float p1 = __fadd_rn(o[1], __fmul_rn(t, d[1]));
+        for (float kh = 0.5f; kh < kh_end; kh = __fadd_rn(kh, 1.f)) {
+            // positions as stated: each product and sum rounded on its own (the
+            // scalar intrinsics are never contracted into a fused multiply-add)
+            const float t = t_at(kh);
+            const float2 pxy = make_float2(__fadd_rn(o[0], __fmul_rn(t, d[0])), __fadd_rn(o[1], __fmul_rn(t, d[1])));
             const float p2 = __fadd_rn(o[2], __fmul_rn(t, d[2]));
-            if ((p0 >= E0) != neg0 || (p1 >= E1) != neg1 || (p2 >= E2) != neg2) {
+            if (kh >= kh_stop) {
                 // entering the brick of this sample
-                const int bx = min(max((int)floorf(p0), 0), cv.dims[0] - 1) >> cv.logB;
-                const int by = min(max((int)floorf(p1), 0), cv.dims[1] - 1) >> cv.logB;
+                const int bx = min(max((int)floorf(pxy.x), 0), cv.dims[0] - 1) >> cv.logB;
+                const int by = min(max((int)floorf(pxy.y), 0), cv.dims[1] - 1) >> cv.logB;
                 const int bz = min(max((int)floorf(p2), 0), cv.dims[2] - 1) >> cv.logB;
                 const int b = (bz * cv.nb[1] + by) * cv.nb[0] + bx;
                 th = __ldg(cv.tex + (int64_t)2 * cv.nb[0] * cv.nb[1] * cv.nb[2] + b);
@@ -317,48 +319,75 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
                 E1 = face(by, cv.nb[1], d[1]);
                 E2 = face(bz, cv.nb[2], d[2]);
                 // texel (u, v) = floor(p - 0.5) - origin + 2; layer = floor(p_z - 0.5) - origin_z + 1
-                c0 = (float)((bx << cv.logB) - 2);
-                c1 = (float)((by << cv.logB) - 2);
+                mc = make_float2((float)(2 - (bx << cv.logB)), (float)(2 - (by << cv.logB)));
                 zo = (bz << cv.logB) - 1;
                 pl = -1;   // texel coordinates are local to the brick
+                // first sample past the brick: the nearest finite exit face gives
+                // an estimate, the exact positions correct it (samples past the
+                // brick form a suffix of the ray)
+                auto past = [&](float khq) {
+                    const float tq = t_at(khq);
+                    const float q0 = __fadd_rn(o[0], __fmul_rn(tq, d[0]));
+                    const float q1 = __fadd_rn(o[1], __fmul_rn(tq, d[1]));
+                    const float q2 = __fadd_rn(o[2], __fmul_rn(tq, d[2]));
+                    return ((q0 >= E0) != neg0) || ((q1 >= E1) != neg1) || ((q2 >= E2) != neg2);
+                };
+                float tf = INFINITY;
+                if (fabsf(E0) < INFINITY) tf = fminf(tf, (E0 - o[0]) * id0);
+                if (fabsf(E1) < INFINITY) tf = fminf(tf, (E1 - o[1]) * id1);
+                if (fabsf(E2) < INFINITY) tf = fminf(tf, (E2 - o[2]) * id2);
+                float ks = fminf(ceilf(__fmul_rn(tf - tin, inv_step) - 0.5f) + 0.5f, kh_end);
+                ks = fmaxf(ks, __fadd_rn(kh, 1.f));
+                while (ks > __fadd_rn(kh, 1.f) && past(ks - 1.f)) ks -= 1.f;
+                while (ks < kh_end && !past(ks)) ks += 1.f;
+                kh_stop = ks;
             }
-            const float q0 = __fsub_rn(p0, 0.5f), q1 = __fsub_rn(p1, 0.5f), q2 = __fsub_rn(p2, 0.5f);
-            const float f0 = floorf(q0), f1 = floorf(q1), f2 = floorf(q2);
-            const float wx = __fsub_rn(q0, f0), wy = __fsub_rn(q1, f1), wz = __fsub_rn(q2, f2);
-            const float u = __fsub_rn(f0, c0), v = __fsub_rn(f1, c1);
+            const float2 qxy = __fadd2_rn(pxy, make_float2(-0.5f, -0.5f));
+            const float q2 = __fsub_rn(p2, 0.5f);
+            const float f0 = floorf(qxy.x), f1 = floorf(qxy.y), f2 = floorf(q2);
+            const float2 fxy = make_float2(f0, f1);
+            const float2 wxy = __ffma2_rn(fxy, m1, qxy);     // q - floor(q), exact
+            const float wz = __fsub_rn(q2, f2);
+            const float2 uv = __fadd2_rn(fxy, mc);
             const int layer = (int)f2 - zo;
-            if (!kReuse || layer != pl || u != pu || v != pv) {
-                gather_pair<DT>(th, layer, u, v, g0, g1);
+            if (!kReuse || layer != pl || uv.x != pu || uv.y != pv) {
+                gather_pair<DT>(th, layer, uv.x, uv.y, g0, g1);
                 pl = layer;
-                pu = u;
-                pv = v;
+                pu = uv.x;
+                pv = uv.y;
             }
-            // gather order: x = (u-1, v), y = (u, v), z = (u, v-1), w = (u-1, v-1)
-            const float c00 = fmaf(wx, g0.z - g0.w, g0.w), c10 = fmaf(wx, g0.y - g0.x, g0.x);
-            const float c01 = fmaf(wx, g1.z - g1.w, g1.w), c11 = fmaf(wx, g1.y - g1.x, g1.x);
-            const float e0 = fmaf(wy, c10 - c00, c00), e1 = fmaf(wy, c11 - c01, c01);
-            float sv = fmaf(wz, e1 - e0, e0);
-            if (DT == VRC_FP8E4M3) sv = sv * scale;
+            // gather order: x = (u-1, v), y = (u, v), z = (u, v-1), w = (u-1, v-1);
+            // lerps in x, then y, then z
+            float sv;
+            if (DT == VRC_F32) {
+                const float c00 = fmaf(wxy.x, g0.z - g0.w, g0.w), c10 = fmaf(wxy.x, g0.y - g0.x, g0.x);
+                const float c01 = fmaf(wxy.x, g1.z - g1.w, g1.w), c11 = fmaf(wxy.x, g1.y - g1.x, g1.x);
+                const float2 C0 = make_float2(c00, c01), C1 = make_float2(c10, c11);
+                const float2 e = __ffma2_rn(make_float2(wxy.y, wxy.y), __ffma2_rn(C0, m1, C1), C0);
+                sv = fmaf(wz, e.y - e.x, e.x);
+            } else {
+                // both layers of a texel pair come from one texel: lerp the two layers at once
+                const float2 wx2 = make_float2(wxy.x, wxy.x);
+                const float2 L0 = make_float2(g0.w, g1.w), H0 = make_float2(g0.z, g1.z);
+                const float2 L1 = make_float2(g0.x, g1.x), H1 = make_float2(g0.y, g1.y);
+                const float2 C0 = __ffma2_rn(wx2, __ffma2_rn(L0, m1, H0), L0);   // (c00, c01)
+                const float2 C1 = __ffma2_rn(wx2, __ffma2_rn(L1, m1, H1), L1);   // (c10, c11)
+                const float2 e = __ffma2_rn(make_float2(wxy.y, wxy.y), __ffma2_rn(C0, m1, C1), C0);
+                sv = fmaf(wz, e.y - e.x, e.x);
+                if (DT == VRC_FP8E4M3) sv = sv * scale;
+            }
             ++nsamp;
             if (MODE == 0) {
                 m = fmaxf(m, sv);
             } else {
-                if (sv > J.skip_below) {   // false for NaN
-                    const float4 c = classify(s_tf, sv, J.vmin, J.inv_range);
-                    const float a = opacity(c.w, step, J.opacity_correction);
-                    const float w = (1.f - A) * a;
-                    cr = fmaf(w, c.x, cr);
-                    cg = fmaf(w, c.y, cg);
-                    cb = fmaf(w, c.z, cb);
-                    A += w;
-                }
-                if (A >= J.term) break;
+                if (sv > J.skip_below)   // false for NaN
+                    over(acc, classify(s_tf, sv, J.vmin, J.inv_range), step, J.opacity_correction);
+                if (acc.A >= J.term) break;
             }
-            kh = __fadd_rn(kh, 1.f);
         }
     }
     if (MODE == 0) J.out[pix] = m;
-    else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(cr, cg, cb, A);
+    else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(acc.rg.x, acc.rg.y, acc.b, acc.A);
 }
 
 // Fused path, persistent: CTAs pull (job, tile) items from an atomic counter.
@@ -525,7 +554,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__res
             }
             if (found) {
                 while (k > 0 && member(cv, o, d, sample_t(tin, k - 1, J.step), bx, by, bz, p)) --k;
-                float m = -FLT_MAX, cr = 0.f, cg = 0.f, cb = 0.f, A = 0.f;
+                float m = -FLT_MAX;
+                OverAcc acc;
                 for (;; ++k) {
                     const float tk = sample_t(tin, k, J.step);
                     if (!(tk < tout)) break;
@@ -546,20 +576,12 @@ __global__ void __launch_bounds__(kThreads) k_render_bricks(const JobDesc *__res
                     if (MODE == 0) {
                         m = fmaxf(m, s);
                     } else {
-                        if (s == s) {
-                            const float4 c = classify(s_tf, s, J.vmin, J.inv_range);
-                            const float a = opacity(c.w, J.step, J.opacity_correction);
-                            const float w = (1.f - A) * a;
-                            cr = fmaf(w, c.x, cr);
-                            cg = fmaf(w, c.y, cg);
-                            cb = fmaf(w, c.z, cb);
-                            A += w;
-                        }
-                        if (fmaf(1.f - afront, A, afront) >= J.term) break;
+                        if (s == s) over(acc, classify(s_tf, s, J.vmin, J.inv_range), J.step, J.opacity_correction);
+                        if (fmaf(1.f - afront, acc.A, afront) >= J.term) break;
                     }
                 }
                 if (MODE == 0) partial[gpix] = m;
-                else reinterpret_cast<float4 *>(partial)[gpix] = make_float4(cr, cg, cb, A);
+                else reinterpret_cast<float4 *>(partial)[gpix] = make_float4(acc.rg.x, acc.rg.y, acc.b, acc.A);
             }
         }
     }

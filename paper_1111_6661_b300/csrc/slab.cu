@@ -188,13 +188,13 @@ __device__ __forceinline__ bool composite(const Par &P, const float4 *s_tf, RayS
         return true;
     }
     if (sv > P.skip_below) {   // false for NaN: alpha exactly 0 below the TF's transparent threshold
+        // the arithmetic of over() in ray.cuh: w rounded once, fused channel updates
         const float4 c = classify(s_tf, sv, P.vmin, P.inv_range);
-        const float a = opacity(c.w, P.step, P.opc);
-        const float w = (1.f - r.A) * a;
+        const float w = __fmul_rn(__fsub_rn(1.f, r.A), opacity(c.w, P.step, P.opc));
         r.cr = fmaf(w, c.x, r.cr);
         r.cg = fmaf(w, c.y, r.cg);
         r.cb = fmaf(w, c.z, r.cb);
-        r.A += w;
+        r.A = __fadd_rn(r.A, w);
     }
     return !(r.A >= P.term);
 }
