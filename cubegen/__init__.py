@@ -48,6 +48,8 @@ def _load():
             lib.cg_sources.restype = None
             lib.cg_noise.argtypes = [u64, u64]
             lib.cg_noise.restype = ctypes.c_double
+            lib.cg_brick_source.argtypes = [ctypes.c_void_p, i64, i32, i32, i32, ctypes.c_void_p]
+            lib.cg_brick_source.restype = i32
             _lib = lib
     return _lib
 
@@ -211,3 +213,40 @@ def serving_stream(seed: int = 5, rate_hz: float = 200.0, duration_s: float = 60
         reqs.append(dict(t=t, kind=kind, cube=int(rng.integers(0, n_cubes)), width=w, height=h,
                          view_seed=int(rng.integers(0, 2**31)), tf_seed=int(rng.integers(0, 2**31))))
     return dict(cubes=cubes, requests=reqs)
+
+
+class CgCube(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("n_sources", ctypes.c_int32), ("B", ctypes.c_int32), ("calls", ctypes.c_int64)]
+
+
+class BrickSource:
+    """C brick provider of a generated cube for out-of-core uploads.
+
+    ``fn`` is the address of ``cg_brick_source`` (int32 (*)(void *user, int64
+    brick, int32 bx, int32 by, int32 bz, float *dst)), ``user`` the address of
+    its cube record; the object must outlive every use of the pair.  ``calls``
+    counts the bricks generated so far.  Generating through it needs no Python
+    per brick.
+    """
+
+    def __init__(self, dims, n_sources: int, seed: int, brick: int):
+        lib = _load()
+        self.rec = CgCube(int(dims[0]), int(dims[1]), int(dims[2]), int(seed), int(n_sources), int(brick), 0)
+        self.fn = ctypes.cast(lib.cg_brick_source, ctypes.c_void_p).value
+        self.user = ctypes.addressof(self.rec)
+
+    @property
+    def calls(self) -> int:
+        return int(self.rec.calls)
+
+    def brick(self, b: int, nb) -> np.ndarray:
+        """Brick b with halo as a (B+2)^3 float32 array (z, y, x)."""
+        R = self.rec.B + 2
+        out = np.empty((R, R, R), dtype=np.float32)
+        bx, by, bz = b % nb[0], (b // nb[0]) % nb[1], b // (nb[0] * nb[1])
+        rc = _load().cg_brick_source(self.user, b, bx, by, bz, out.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"cubegen: brick {b} failed")
+        return out
+

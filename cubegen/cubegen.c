@@ -151,3 +151,64 @@ int cg_generate_box(int64_t nx, int64_t ny, int64_t nz, uint64_t seed, int32_t n
     free(src);
     return failed ? -1 : 0;
 }
+
+/*
+ * Brick provider for out-of-core cubes: brick (bx, by, bz) of edge B with its
+ * one-voxel halo, (B+2)^3 floats x fastest, covering voxels [b*B-1, b*B+B] of
+ * each axis, positions outside the cube taking the value of the nearest voxel
+ * inside it (clamp to edge).  `user` points to a cg_cube record; its `calls`
+ * field counts the bricks generated.  Returns 0, or -1 when generation fails.
+ */
+typedef struct {
+    int64_t nx, ny, nz;
+    uint64_t seed;
+    int32_t n_sources, B;
+    int64_t calls;
+} cg_cube;
+
+int32_t cg_brick_source(void *user, int64_t brick, int32_t bx, int32_t by, int32_t bz, float *dst)
+{
+    (void)brick;
+    cg_cube *c = (cg_cube *)user;
+    const int64_t B = c->B, R = B + 2;
+    const int64_t lo[3] = {(int64_t)bx * B - 1, (int64_t)by * B - 1, (int64_t)bz * B - 1};
+    const int64_t n[3] = {c->nx, c->ny, c->nz};
+    int64_t a[3], e[3];
+    int inside = 1;
+    for (int k = 0; k < 3; ++k) {
+        a[k] = lo[k] < 0 ? 0 : lo[k];
+        e[k] = lo[k] + R > n[k] ? n[k] : lo[k] + R;
+        if (a[k] != lo[k] || e[k] != lo[k] + R) inside = 0;
+        if (a[k] >= e[k]) return -1;
+    }
+    c->calls++;
+    if (inside)
+        return cg_generate_box(c->nx, c->ny, c->nz, c->seed, c->n_sources, a[0], a[1], a[2], R, R, R, dst) ? -1 : 0;
+    /* border brick: generate the part inside the cube, then spread it with
+       clamped indices */
+    const int64_t sx = e[0] - a[0], sy = e[1] - a[1], sz = e[2] - a[2];
+    float *tmp = (float *)malloc(sizeof(float) * (size_t)(sx * sy * sz));
+    if (!tmp) return -1;
+    if (cg_generate_box(c->nx, c->ny, c->nz, c->seed, c->n_sources, a[0], a[1], a[2], sx, sy, sz, tmp)) {
+        free(tmp);
+        return -1;
+    }
+    for (int64_t z = 0; z < R; ++z) {
+        int64_t gz = lo[2] + z;
+        gz = gz < a[2] ? a[2] : (gz >= e[2] ? e[2] - 1 : gz);
+        for (int64_t y = 0; y < R; ++y) {
+            int64_t gy = lo[1] + y;
+            gy = gy < a[1] ? a[1] : (gy >= e[1] ? e[1] - 1 : gy);
+            const float *row = tmp + ((gz - a[2]) * sy + (gy - a[1])) * sx;
+            float *out = dst + (z * R + y) * R;
+            for (int64_t x = 0; x < R; ++x) {
+                int64_t gx = lo[0] + x;
+                gx = gx < a[0] ? a[0] : (gx >= e[0] ? e[0] - 1 : gx);
+                out[x] = row[gx - a[0]];
+            }
+        }
+    }
+    free(tmp);
+    return 0;
+}
+

@@ -50,6 +50,7 @@ typedef int32_t vrc_status;
 #define VRC_E_NONFINITE  -7   /* statistic undefined: the cube has no finite voxel */
 #define VRC_E_INJECTED   -8   /* failure produced by vrc_debug_inject (tests) */
 #define VRC_E_UNSUPPORTED -9  /* operation not available for this cube kind / dtype */
+#define VRC_E_SOURCE     -10  /* the brick provider of an out-of-core cube reported a failure */
 
 typedef enum { VRC_F32 = 0, VRC_BF16 = 1, VRC_FP8E4M3 = 2 } vrc_dtype;
 
@@ -196,6 +197,41 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
                                     int64_t n_host_bricks, int32_t ring_bricks, int64_t *cube_id);
 
 /*
+ * Brick provider of an out-of-core cube (Sec. 2: cubes larger than memory,
+ * read sub-cube by sub-cube).  Writes brick `brick` = (bx, by, bz) (index
+ * (bz*nby + by)*nbx + bx) with its one-voxel halo into dst: (B+2)^3 floats,
+ * x fastest, covering voxels [b*B-1, b*B+B] of each axis, the clamp-to-edge
+ * value outside the cube.  dst is host memory owned by the library, valid
+ * for the duration of the call.  Returns 0 on success; any other value makes
+ * the calling library operation fail with VRC_E_SOURCE.  Called on the thread
+ * of the library call that needs the brick, never concurrently for one cube.
+ */
+typedef int32_t (*vrc_brick_source_fn)(void *user, int64_t brick, int32_t bx, int32_t by, int32_t bz, float *dst);
+
+/*
+ * Out-of-core float32 cube whose bricks come from a provider (Sec. 2: cubes
+ * larger than the memory of one node, streamed to the GPU on side streams).
+ * The call asks `source` for every brick once, in index order, to record each
+ * brick's minimum and maximum (the transfer-function range, brick culling),
+ * the sums that centre the statistics and its non-finite voxels; it returns
+ * when all bricks have been seen.  n_host_bricks pinned host slots (1 ..
+ * number of bricks) cache provided bricks: brick b lives in slot
+ * b % n_host_bricks.  Renders, statistics and the median stream the bricks
+ * they need through ring_bricks device slots (0 = 8; at least 2; charged to
+ * the budget) and call `source` again, on the calling thread, for every brick
+ * whose slot holds another brick (after the slot's previous copy to the
+ * device has completed); with n_host_bricks = number of bricks the provider
+ * is called once per brick only.  The zero-copy path needs every brick cached
+ * (n_host_bricks = number of bricks).  `user` is passed through and must stay
+ * valid until the cube is freed.
+ * Errors: VRC_E_INVAL, VRC_E_NOMEM (pinned or device allocation failed),
+ * VRC_E_SOURCE (the provider failed; no cube is created).
+ */
+vrc_status vrc_cube_upload_streamed(vrc_ctx *ctx, vrc_brick_source_fn source, void *user, int64_t nx, int64_t ny,
+                                    int64_t nz, int32_t brick, int64_t n_host_bricks, int32_t ring_bricks,
+                                    int64_t *cube_id);
+
+/*
  * Fill host slot `slot` of a streamed cube with one brick given as
  * (B+2)^3 floats, x fastest, covering voxels [b*B-1, b*B+B] of each axis with
  * clamp-to-edge values outside the cube.  Host memory, copied; records the
@@ -248,16 +284,24 @@ vrc_status vrc_cube_read_brick(vrc_ctx *ctx, int64_t cube_id, int64_t brick, voi
 /* ------------------------------------------------------------- statistics */
 
 /*
- * Global statistics in one fused pass over the resident bricks (Abstract:
- * min/max and histogram; Sec. 3: standard deviation): min and max (recorded at
- * upload), n, mean and population std (binary64 block partials, fixed-order
- * final merge), n_nonfinite, and, when nbins > 0, hist[nbins] counts over
- * [min, max] with the binary32 bin formula
+ * Global statistics in one fused pass over the bricks (Abstract: min/max and
+ * histogram; Sec. 3: standard deviation): min and max (recorded at upload),
+ * n, mean and population std (binary64 block partials, fixed-order final
+ * merge), n_nonfinite, and, when nbins > 0, hist[nbins] counts over [min,
+ * max] with the binary32 bin formula
  *   range = fl(max - min), scale = fl(nbins / range),
  *   bin = trunc(fl(fl(x - min) * scale)) clamped to [0, nbins-1]
  *   (range == 0: every value in bin 0).
  * out and hist are HOST memory; the call waits for `stream`.  nbins <= 65536.
- * Errors: VRC_E_BADID, VRC_E_INVAL, VRC_E_NONFINITE (no finite voxel).
+ * Out-of-core cubes (Sec. 3: min/max accumulate sub-cube by sub-cube; std
+ * needs all data) take the same pass chunk by chunk: runs of consecutive
+ * bricks are copied through the cube's device ring (bricks that are not in
+ * the host cache are provided first) and each chunk's pass writes its own
+ * block partials, merged in a fixed order at the end; min, max and every
+ * histogram count equal those of the same cube uploaded resident, mean and
+ * std agree to rounding.
+ * Errors: VRC_E_BADID, VRC_E_INVAL, VRC_E_NONFINITE (no finite voxel),
+ * VRC_E_SOURCE (out-of-core cube: the provider failed).
  */
 vrc_status vrc_cube_stats(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stats *out, uint64_t *hist,
                           void *stream);
@@ -265,8 +309,9 @@ vrc_status vrc_cube_stats(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stat
 /*
  * Asynchronous form: writes a vrc_stats record to DEVICE memory dev_out and
  * counts to DEVICE memory dev_hist[nbins] (may be NULL when nbins == 0),
- * stream-ordered; nothing waits.  dev_out->n == 0 flags a cube without finite
- * voxels.
+ * stream-ordered; nothing waits (out-of-core cubes: the call returns when
+ * every chunk's copy and pass has been issued).  dev_out->n == 0 flags a cube
+ * without finite voxels.
  */
 vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stats *dev_out,
                                 uint64_t *dev_hist, void *stream);
@@ -277,7 +322,8 @@ vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vr
  * latency-bound interactive or serving loop, where cudaMalloc/cudaFree may
  * stall the whole device, or a plug-in inside an application that keeps the
  * device memory in its own pool).  Same inputs, outputs and errors as
- * vrc_cube_stats_async; the pass's block partials go to one static device
+ * vrc_cube_stats_async, for resident cubes (out-of-core cubes stream through
+ * their device ring: VRC_E_UNSUPPORTED here); the pass's block partials go to one static device
  * array of 64 KiB that the library holds on every device that loads it, so
  * the call performs no cudaMalloc, cudaFree or other allocation.  Devices whose
  * statistics pass needs more scratch than that are refused with VRC_E_NOMEM.
@@ -303,8 +349,9 @@ vrc_status vrc_cube_stats_noalloc(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, 
  * counts each brick's 8-bit codes; the three radix passes then run over the
  * (brick, code) entries weighted by their counts (a stored fp8 value depends
  * only on its brick's scale and its code).  bf16 keys have 16 significant
- * bits, so two passes fix them.  *out is HOST memory; waits for
- * `stream`.  Errors: VRC_E_BADID, VRC_E_NONFINITE.
+ * bits, so two passes fix them.  Out-of-core cubes stream their bricks
+ * through the device ring once per pass.  *out is HOST memory; waits for
+ * `stream`.  Errors: VRC_E_BADID, VRC_E_NONFINITE, VRC_E_SOURCE.
  */
 vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *stream);
 

@@ -126,6 +126,36 @@ class Context:
                                                        ring_bricks, ctypes.byref(cid)))
         return cid.value
 
+    def cube_upload_streamed(self, dims, brick: int, source, n_host_bricks: int, ring_bricks: int = 0) -> int:
+        """Out-of-core cube whose bricks come from `source`: either a pair
+        (C function address, user address) of a vrc_brick_source_fn, or a
+        Python callable (brick, bx, by, bz) -> float32 array of (B+2)^3 values
+        (z, y, x) holding the brick and its clamp-to-edge halo."""
+        if callable(source):
+            R = int(brick) + 2
+
+            def _cb(user, b, bx, by, bz, dst, _f=source):
+                try:
+                    a = np.ctypeslib.as_array(dst, shape=(R * R * R,))
+                    a[:] = np.asarray(_f(int(b), int(bx), int(by), int(bz)), dtype=np.float32).reshape(-1)
+                    return 0
+                except Exception:   # reported to the library as a provider failure
+                    return 1
+            fn = _vrc.BRICK_SOURCE_FN(_cb)
+            fn_ptr, user = ctypes.cast(fn, ctypes.c_void_p), None
+        else:
+            fn, (fn_ptr, user) = source, source
+        cid = ctypes.c_int64()
+        self._check(self._lib.vrc_cube_upload_streamed(self.h, ctypes.c_void_p(fn_ptr.value if hasattr(fn_ptr, "value")
+                                                                               else fn_ptr),
+                                                       ctypes.c_void_p(user), dims[0], dims[1], dims[2], brick,
+                                                       n_host_bricks, ring_bricks, ctypes.byref(cid)))
+        # the provider (and its closure) must outlive the cube
+        if not hasattr(self, "_sources"):
+            self._sources = {}
+        self._sources[cid.value] = fn
+        return cid.value
+
     def cube_put_brick(self, cube_id: int, slot: int, brick_with_halo: np.ndarray):
         b = np.ascontiguousarray(brick_with_halo, dtype=np.float32)
         self._check(self._lib.vrc_cube_put_brick(self.h, cube_id, slot, b.ctypes.data))

@@ -13,7 +13,7 @@ c_i32, c_i64, c_u64, c_f32, c_f64, c_p = (ctypes.c_int32, ctypes.c_int64, ctypes
 VRC_OK, VRC_PENDING = 0, 1
 STATUS = {0: "VRC_OK", 1: "VRC_PENDING", -1: "VRC_E_INVAL", -2: "VRC_E_NOMEM", -3: "VRC_E_CUDA",
           -4: "VRC_E_TIMEOUT", -5: "VRC_E_BADID", -6: "VRC_E_BUSY", -7: "VRC_E_NONFINITE", -8: "VRC_E_INJECTED",
-          -9: "VRC_E_UNSUPPORTED"}
+          -9: "VRC_E_UNSUPPORTED", -10: "VRC_E_SOURCE"}
 DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
 SAMPLING = {"nearest": 0, "trilinear": 1}
 PATHS = {"fused": 0, "sortlast": 1, "fused_ldg": 2, "zerocopy": 3, "slab": 4}
@@ -56,6 +56,9 @@ class vrc_result(ctypes.Structure):
                 ("latency_ms", c_f64), ("samples", c_u64)]
 
 
+# vrc_brick_source_fn: int32 (*)(void *user, int64 brick, int32 bx, int32 by, int32 bz, float *dst)
+BRICK_SOURCE_FN = ctypes.CFUNCTYPE(c_i32, c_p, c_i64, c_i32, c_i32, c_i32, ctypes.POINTER(c_f32))
+
 # name -> (restype, argtypes); mirrors include/vrc.h
 PROTOTYPES = {
     "vrc_create": (c_i32, [ctypes.POINTER(c_p), ctypes.POINTER(vrc_config)]),
@@ -66,6 +69,8 @@ PROTOTYPES = {
     "vrc_cube_upload": (c_i32, [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i32, c_i32, c_p, ctypes.POINTER(c_i64)]),
     "vrc_cube_create_streamed": (c_i32, [c_p, c_i64, c_i64, c_i64, c_i32, c_i64, c_i32, ctypes.POINTER(c_i64)]),
     "vrc_cube_put_brick": (c_i32, [c_p, c_i64, c_i64, c_p]),
+    "vrc_cube_upload_streamed": (c_i32, [c_p, c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i64, c_i32,
+                                         ctypes.POINTER(c_i64)]),
     "vrc_cube_read_brick": (c_i32, [c_p, c_i64, c_i64, c_p, c_i64]),
     "vrc_cube_free": (c_i32, [c_p, c_i64]),
     "vrc_cube_free_async": (c_i32, [c_p, c_i64, c_p]),

@@ -688,6 +688,8 @@ void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
     if (c->bnonfinite) dev_free(ctx, c->bnonfinite, g.nbricks * 4);
     if (c->bhalo) dev_free(ctx, c->bhalo, g.nbricks * 4);
     if (c->host_pool) cudaFreeHost(c->host_pool);
+    for (cudaEvent_t e : c->slot_ev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -711,6 +713,94 @@ int64_t register_cube(vrc_ctx *ctx, Cube *c)
     c->id = ctx->next_id++;
     ctx->cubes[c->id] = c;
     return c->id;
+}
+
+// Extrema and sums of one host brick (Sec. 2: sub-cubes of a cube larger
+// than memory): interior voxels inside the cube, plus the largest value a
+// sample can read (halo included) for brick culling.
+struct BrickMeta {
+    float mn = FLT_MAX, mx = -FLT_MAX, hmx = -INFINITY;
+    int32_t nnf = 0;
+    double sum = 0.0;
+    int64_t cnt = 0;
+};
+
+// Repack brick `bw` ((B+2)^3 floats, x fastest) into host slot `slot` (rows of
+// P elements, the halo voxel at element O-1) and measure it.
+void pack_host_slot(Cube *c, int64_t slot, const float *bw, BrickMeta *m)
+{
+    const BrickGeom &g = c->g;
+    const int R = g.R;
+    float *dst = reinterpret_cast<float *>((char *)c->host_pool + slot * g.brick_bytes);
+    for (int zr = 0; zr < R; ++zr)
+        for (int yr = 0; yr < R; ++yr) {
+            float *row = dst + ((int64_t)zr * R + yr) * g.P;
+            const float *in = bw + ((int64_t)zr * R + yr) * R;
+            std::memset(row, 0, sizeof(float) * g.P);
+            std::memcpy(row + g.O - 1, in, sizeof(float) * R);
+            if (!m) continue;
+            for (int x = 0; x < R; ++x) m->hmx = std::fmax(m->hmx, in[x]);   // NaN ignored, +inf kept
+            if (zr >= 1 && zr <= g.B && yr >= 1 && yr <= g.B)
+                for (int x = 1; x <= g.B; ++x) {
+                    const float v = in[x];
+                    if (std::isfinite(v)) {
+                        m->mn = std::fmin(m->mn, v);
+                        m->mx = std::fmax(m->mx, v);
+                        m->sum += v;
+                        ++m->cnt;
+                    } else {
+                        ++m->nnf;
+                    }
+                }
+        }
+}
+
+// Record brick b's measurements.  For a brick on the cube's far border the
+// measured B^3 interior includes positions past the cube, which repeat edge
+// voxels: the extrema are unchanged, the sum only centres the statistics, and
+// the non-finite count only steers the statistics pass to its checked path
+// (the pass counts non-finite voxels itself, inside the cube).
+void set_brick_meta(Cube *c, int64_t b, const BrickMeta &m)
+{
+    c->h_bmin[b] = m.mn;
+    c->h_bmax[b] = m.mx;
+    c->h_bnonfinite[b] = m.nnf;
+    c->h_bhalo_max[b] = m.hmx;
+    c->h_bsum[b] = m.sum;
+    c->h_bcnt[b] = m.cnt;
+}
+
+// Cube extrema and the statistics centre from the per-brick records.
+void finish_streamed_meta(Cube *c)
+{
+    float vmn = FLT_MAX, vmx = -FLT_MAX;
+    double sum = 0.0;
+    int64_t cnt = 0;
+    for (int64_t b = 0; b < c->g.nbricks; ++b) {
+        if (c->h_bmin[b] <= c->h_bmax[b]) {
+            vmn = std::fmin(vmn, c->h_bmin[b]);
+            vmx = std::fmax(vmx, c->h_bmax[b]);
+        }
+        sum += c->h_bsum[b];
+        cnt += c->h_bcnt[b];
+    }
+    c->has_finite = vmn <= vmx;
+    c->vmin = c->has_finite ? vmn : 0.f;
+    c->vmax = c->has_finite ? vmx : 0.f;
+    c->shift = cnt ? (float)(sum / (double)cnt) : 0.f;
+    if (!std::isfinite(c->shift)) c->shift = c->vmin;
+}
+
+// Ask the provider for brick b into c->source_buf.
+vrc_status call_source(vrc_ctx *ctx, Cube *c, int64_t b)
+{
+    const BrickGeom &g = c->g;
+    const int32_t bx = (int32_t)(b % g.nb[0]), by = (int32_t)((b / g.nb[0]) % g.nb[1]),
+                  bz = (int32_t)(b / ((int64_t)g.nb[0] * g.nb[1]));
+    ++c->source_calls;
+    const int32_t rc = c->source(c->source_user, b, bx, by, bz, c->source_buf.data());
+    if (rc != 0) return set_err(ctx, VRC_E_SOURCE, "brick provider failed on brick %lld (returned %d)", (long long)b, rc);
+    return VRC_OK;
 }
 
 }  // namespace
@@ -839,6 +929,8 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
     c->h_bmax.assign(g.nbricks, -FLT_MAX);
     c->h_bnonfinite.assign(g.nbricks, 0);
     c->h_bhalo_max.assign(g.nbricks, -INFINITY);
+    c->h_bsum.assign(g.nbricks, 0.0);
+    c->h_bcnt.assign(g.nbricks, 0);
     std::vector<float> ones(g.nbricks, 1.f);
     cudaMemcpy(c->scales, ones.data(), g.nbricks * 4, cudaMemcpyHostToDevice);
     c->charged = (int64_t)ring_bricks * g.brick_bytes;
@@ -852,51 +944,63 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
     Cube *c = find_cube(ctx, cube_id);
     if (!c) return VRC_E_BADID;
     if (!c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "cube is resident, not streamed");
+    if (c->source) return set_err(ctx, VRC_E_UNSUPPORTED, "cube takes its bricks from its provider");
     if (slot < 0 || slot >= c->n_host) return set_err(ctx, VRC_E_INVAL, "slot out of range");
-    const BrickGeom &g = c->g;
-    const int R = g.R;
-    float *dst = reinterpret_cast<float *>((char *)c->host_pool + slot * g.brick_bytes);
-    float mn = FLT_MAX, mx = -FLT_MAX, hmx = -INFINITY;
-    int32_t nnf = 0;
-    for (int zr = 0; zr < R; ++zr)
-        for (int yr = 0; yr < R; ++yr) {
-            float *row = dst + ((int64_t)zr * R + yr) * g.P;
-            const float *in = bw + ((int64_t)zr * R + yr) * R;
-            std::memset(row, 0, sizeof(float) * g.P);
-            std::memcpy(row + g.O - 1, in, sizeof(float) * R);
-            for (int x = 0; x < R; ++x) hmx = std::fmax(hmx, in[x]);   // NaN ignored, +inf kept
-            if (zr >= 1 && zr <= g.B && yr >= 1 && yr <= g.B)
-                for (int x = 1; x <= g.B; ++x) {
-                    float v = in[x];
-                    if (std::isfinite(v)) {
-                        mn = std::fmin(mn, v);
-                        mx = std::fmax(mx, v);
-                    } else {
-                        ++nnf;
-                    }
-                }
-        }
+    BrickMeta m;
+    pack_host_slot(c, slot, bw, &m);
     if (!c->host_filled[slot]) {
         c->host_filled[slot] = 1;
         ++c->n_filled;
     }
     // every logical brick aliased to this slot gets its extrema
-    for (int64_t b = slot; b < g.nbricks; b += c->n_host) {
-        c->h_bmin[b] = mn;
-        c->h_bmax[b] = mx;
-        c->h_bnonfinite[b] = nnf;
-        c->h_bhalo_max[b] = hmx;
-    }
-    float vmn = FLT_MAX, vmx = -FLT_MAX;
-    for (int64_t b = 0; b < g.nbricks; ++b) {
-        if (c->h_bmin[b] <= c->h_bmax[b]) {
-            vmn = std::fmin(vmn, c->h_bmin[b]);
-            vmx = std::fmax(vmx, c->h_bmax[b]);
+    for (int64_t b = slot; b < c->g.nbricks; b += c->n_host) set_brick_meta(c, b, m);
+    finish_streamed_meta(c);
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_upload_streamed(vrc_ctx *ctx, vrc_brick_source_fn source, void *user, int64_t nx, int64_t ny,
+                                    int64_t nz, int32_t brick, int64_t n_host_bricks, int32_t ring_bricks,
+                                    int64_t *cube_id)
+{
+    if (!ctx || !cube_id) return VRC_E_INVAL;
+    if (!source) return set_err(ctx, VRC_E_INVAL, "null brick provider");
+    int64_t id = 0;
+    vrc_status s = vrc_cube_create_streamed(ctx, nx, ny, nz, brick, n_host_bricks, ring_bricks, &id);
+    if (s != VRC_OK) return s;
+    Cube *c = find_cube(ctx, id);
+    c->source = source;
+    c->source_user = user;
+    const BrickGeom &g = c->g;
+    c->slot_brick.assign(c->n_host, -1);
+    c->slot_ev.assign(c->n_host, nullptr);
+    c->slot_ev_live.assign(c->n_host, 0);
+    c->source_buf.resize((size_t)g.R * g.R * g.R);
+    for (int64_t sl = 0; sl < c->n_host && s == VRC_OK; ++sl) {
+        const cudaError_t e = cudaEventCreateWithFlags(&c->slot_ev[sl], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            c->slot_ev[sl] = nullptr;
+            s = cuda_err(ctx, e, "slot event");
         }
     }
-    c->has_finite = vmn <= vmx;
-    c->vmin = c->has_finite ? vmn : 0.f;
-    c->vmax = c->has_finite ? vmx : 0.f;
+    // every brick once, in index order: extrema, sums and non-finite counts;
+    // the host cache keeps the last brick of each slot
+    for (int64_t b = 0; b < g.nbricks && s == VRC_OK; ++b) {
+        const int64_t slot = b % c->n_host;
+        BrickMeta m;
+        s = call_source(ctx, c, b);
+        if (s != VRC_OK) break;
+        pack_host_slot(c, slot, c->source_buf.data(), &m);
+        c->slot_brick[slot] = b;
+        set_brick_meta(c, b, m);
+    }
+    if (s != VRC_OK) {
+        vrc_cube_free(ctx, id);
+        return s;
+    }
+    c->host_filled.assign(c->n_host, 1);
+    c->n_filled = c->n_host;
+    finish_streamed_meta(c);
+    *cube_id = id;
     return VRC_OK;
 }
 
@@ -984,3 +1088,52 @@ vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ out-of-core
+
+vrc_status host_brick(vrc_ctx *ctx, Cube *c, int64_t brick, int64_t *slot)
+{
+    const int64_t sl = brick % c->n_host;
+    *slot = sl;
+    if (!c->source || c->slot_brick[sl] == brick) return VRC_OK;
+    // another brick lives in the slot: its last copy to the device must be done
+    if (c->slot_ev_live[sl]) {
+        const cudaError_t e = cudaEventSynchronize(c->slot_ev[sl]);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "host slot reuse");
+        c->slot_ev_live[sl] = 0;
+    }
+    c->slot_brick[sl] = -1;
+    vrc_status s = call_source(ctx, c, brick);
+    if (s != VRC_OK) return s;
+    pack_host_slot(c, sl, c->source_buf.data(), nullptr);
+    c->slot_brick[sl] = brick;
+    return VRC_OK;
+}
+
+vrc_status host_copied(vrc_ctx *ctx, Cube *c, int64_t slot, cudaStream_t st)
+{
+    if (!c->source) return VRC_OK;
+    const cudaError_t e = cudaEventRecord(c->slot_ev[slot], st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "host slot event");
+    c->slot_ev_live[slot] = 1;
+    return VRC_OK;
+}
+
+vrc_status ring_load(vrc_ctx *ctx, Cube *c, int64_t b0, int64_t n, int first, cudaStream_t cs, cudaEvent_t done)
+{
+    const BrickGeom &g = c->g;
+    for (int64_t q = 0; q < n; ++q) {
+        if (inject_fire(ctx, VRC_INJECT_H2D)) return set_err(ctx, VRC_E_INJECTED, "injected host-to-device brick copy failure");
+        int64_t sl = 0;
+        vrc_status s = host_brick(ctx, c, b0 + q, &sl);
+        if (s != VRC_OK) return s;
+        const cudaError_t e = cudaMemcpyAsync((char *)c->ring_pool + (int64_t)(first + q) * g.brick_bytes,
+                                              (const char *)c->host_pool + sl * g.brick_bytes, g.brick_bytes,
+                                              cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "brick H2D");
+        if ((s = host_copied(ctx, c, sl, cs)) != VRC_OK) return s;
+    }
+    const cudaError_t e = cudaEventRecord(done, cs);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "ring event");
+    return VRC_OK;
+}

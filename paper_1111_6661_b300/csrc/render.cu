@@ -1140,6 +1140,9 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     if (c->streamed && c->n_filled < c->n_host)
         return set_err(ctx, VRC_E_INVAL, "streamed cube: %lld of %lld host slots never written",
                        (long long)(c->n_host - c->n_filled), (long long)c->n_host);
+    if (zerocopy && c->source && c->n_host < c->g.nbricks)
+        return set_err(ctx, VRC_E_UNSUPPORTED, "zero-copy rendering reads every brick in place: the host cache "
+                       "must hold all %lld bricks", (long long)c->g.nbricks);
     const float thr = mode == 1 ? transparent_below(c, tf_rgba) : -INFINITY;
     SortLastPlan plan;
     if (sortlast) plan_sortlast(c, jobs, camv, rc->skip_empty && mode == 1 ? thr : -INFINITY, plan);
@@ -1306,7 +1309,9 @@ vrc_status render_streamed(vrc_ctx *ctx, Cube *c, SortLastPlan &plan, const vrc_
                 status = set_err(ctx, VRC_E_INJECTED, "injected host-to-device brick copy failure");
                 break;
             }
-            const int64_t hslot = ch.bricks[q] % c->n_host;
+            // the host slot of the brick (a provider cube refills it when it holds another brick)
+            int64_t hslot = 0;
+            if ((status = host_brick(ctx, c, ch.bricks[q], &hslot)) != VRC_OK) break;
             const char *src = (const char *)c->host_pool + hslot * g.brick_bytes;
             char *dst = (char *)c->ring_pool + (int64_t)(ch.parity * half + q) * g.brick_bytes;
             cudaError_t e = cudaMemcpyAsync(dst, src, g.brick_bytes, cudaMemcpyHostToDevice, cs);
@@ -1314,6 +1319,7 @@ vrc_status render_streamed(vrc_ctx *ctx, Cube *c, SortLastPlan &plan, const vrc_
                 status = cuda_err(ctx, e, "brick H2D");
                 break;
             }
+            if ((status = host_copied(ctx, c, hslot, cs)) != VRC_OK) break;
         }
         if (status != VRC_OK) break;
         cudaEventRecord(ready[i], cs);

@@ -34,6 +34,8 @@ struct StatsArgs {
     int all_full;                  // every brick lies inside the cube (dims are multiples of B)
     unsigned long long *hist;      // device [nbins], zeroed by the caller
     StatPartial *partials;         // device [gridDim.x]
+    int accumulate;                // add to the partials instead of writing them (runs of an out-of-core cube)
+    int64_t brick0, nrun;          // the pool holds bricks brick0 .. brick0 + nrun - 1 of the cube
 };
 
 template <int DT>
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_stats(StatsA
     const int logVPR = g.logB - LOG_VE;
     const int logRPC = kLogChunk - logVPR;     // rows per chunk (divides B*B)
     const int logCPB = 2 * g.logB - logRPC;    // chunks per brick
-    const int64_t total_chunks = g.nbricks << logCPB;
+    const int64_t total_chunks = a.nrun << logCPB;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // byte offsets inside a brick (a brick is below 2^32 bytes): rows of P elements,
@@ -192,7 +194,8 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_stats(StatsA
     acc.q_hi = make_float2(a.kq, a.kq);
     acc.q_lo = make_float2(0.f, 0.f);
     for (int64_t ch = warp0; ch < total_chunks; ch += nwarps) {
-        const uint32_t b = (uint32_t)(ch >> logCPB);
+        const uint32_t pb = (uint32_t)(ch >> logCPB);          // brick slot in the pool
+        const uint32_t b = pb + (uint32_t)a.brick0;            // brick of the cube
         const uint32_t lr0 = ((uint32_t)ch & ((1u << logCPB) - 1)) << logRPC;
         // bricks that lie inside the cube and hold only finite voxels take the
         // unchecked path; their coordinates are needed only otherwise
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_stats(StatsA
             clean = ((int64_t)(bx + 1) << g.logB) <= g.dims[0] && ((int64_t)(by + 1) << g.logB) <= g.dims[1] &&
                     ((int64_t)(bz + 1) << g.logB) <= g.dims[2] && __ldg(a.bnonfinite + b) == 0;
         }
-        const uint8_t *bp = a.pool + (uint64_t)b * (uint64_t)g.brick_bytes;
+        const uint8_t *bp = a.pool + (uint64_t)pb * (uint64_t)g.brick_bytes;
         const float scale = DT == VRC_FP8E4M3 ? __ldg(a.scales + b) : 1.f;
         uint4 raw[kVecPerLane];
         if (one_slice) {
@@ -263,7 +266,15 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_stats(StatsA
             r.n += wp[w].n;
             r.nnf += wp[w].nnf;
         }
-        a.partials[blockIdx.x] = r;
+        if (a.accumulate) {
+            StatPartial &p = a.partials[blockIdx.x];
+            p.s1 += r.s1;
+            p.s2 += r.s2;
+            p.n += r.n;
+            p.nnf += r.nnf;
+        } else {
+            a.partials[blockIdx.x] = r;
+        }
     }
     if (HIST == 1) {
         __syncthreads();
@@ -485,6 +496,7 @@ struct SelArgs {
     int prefix_all;                // 1: no prefix condition (first pass)
     uint32_t prefix;               // required value of k >> (shift + nbits)
     unsigned long long *hist;      // device [2^nbits], zeroed by the caller
+    int64_t brick0, nrun;          // the pool holds bricks brick0 .. brick0 + nrun - 1 of the cube
 };
 
 constexpr int kSelMaxBins = 4096;
@@ -503,14 +515,15 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(
     const int logVPR = g.logB - LOG_VE;
     const int logRPC = kLogChunk - logVPR;
     const int logCPB = 2 * g.logB - logRPC;
-    const int64_t total_chunks = g.nbricks << logCPB;
+    const int64_t total_chunks = a.nrun << logCPB;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t Pb = (uint32_t)(g.P * g.esize), RPb = (uint32_t)g.R * Pb, Ob = (uint32_t)(g.O * g.esize);
     const uint32_t dmask = (uint32_t)nb - 1u;
     const int hshift = a.shift + a.nbits;
     for (int64_t ch = warp0; ch < total_chunks; ch += nwarps) {
-        const uint32_t b = (uint32_t)(ch >> logCPB);
+        const uint32_t pb = (uint32_t)(ch >> logCPB);          // brick slot in the pool
+        const uint32_t b = pb + (uint32_t)a.brick0;            // brick of the cube
         const uint32_t lr0 = ((uint32_t)ch & ((1u << logCPB) - 1)) << logRPC;
         bool clean;
         uint32_t bx = 0, by = 0, bz = 0;
@@ -524,7 +537,7 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(
             clean = ((int64_t)(bx + 1) << g.logB) <= g.dims[0] && ((int64_t)(by + 1) << g.logB) <= g.dims[1] &&
                     ((int64_t)(bz + 1) << g.logB) <= g.dims[2] && __ldg(a.bnonfinite + b) == 0;
         }
-        const uint8_t *bp = a.pool + (uint64_t)b * (uint64_t)g.brick_bytes;
+        const uint8_t *bp = a.pool + (uint64_t)pb * (uint64_t)g.brick_bytes;
         const float scale = DT == VRC_FP8E4M3 ? __ldg(a.scales + b) : 1.f;
         uint4 raw[kVecPerLane];
 #pragma unroll
@@ -633,15 +646,14 @@ int launch_stats(const StatsArgs &a, int sm_count, int grid_cap, size_t smem, in
 
 size_t stats_scratch_bytes(vrc_ctx *ctx) { return sizeof(StatPartial) * (size_t)stats_grid(ctx); }
 
-// Launch the fused statistics pass + final merge on `st`.  dev_hist (nbins
-// counters) is zeroed here; partials is scratch of stats_scratch_bytes().
-vrc_status stats_launch_with(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *dev_out, uint64_t *dev_hist,
-                             void *partials, cudaStream_t st)
+namespace {
+
+// Pass arguments shared by resident and out-of-core cubes.
+StatsArgs make_stats_args(const Cube *c, int32_t nbins, uint64_t *dev_hist, void *partials, const uint8_t *pool)
 {
     const BrickGeom &g = c->g;
-    const int grid = stats_grid(ctx);
     StatsArgs a;
-    a.pool = (const uint8_t *)c->pool;
+    a.pool = pool;
     a.g = g;
     a.scales = c->scales;
     a.vmin = c->vmin;
@@ -672,20 +684,99 @@ vrc_status stats_launch_with(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *de
     a.all_full = g.dims[0] % g.B == 0 && g.dims[1] % g.B == 0 && g.dims[2] % g.B == 0;
     a.hist = (unsigned long long *)dev_hist;
     a.partials = (StatPartial *)partials;
-    if (nbins > 0) VRC_CK(ctx, cudaMemsetAsync(dev_hist, 0, sizeof(uint64_t) * nbins, st));
+    a.accumulate = 0;
+    a.brick0 = 0;
+    a.nrun = g.nbricks;
+    return a;
+}
+
+int launch_stats_dt(vrc_ctx *ctx, const StatsArgs &a, int grid, int nbins, cudaStream_t st)
+{
     const int hist = nbins == 0 ? 0 : (nbins <= kSmemBinsMax ? 1 : 2);
     const size_t smem = hist == 1 ? sizeof(uint32_t) * (nbins + 1) : 0;
-    int used = 0;
-    if (g.dtype == VRC_F32) {
-        used = launch_stats<VRC_F32>(a, ctx->sm_count, grid, smem, hist, st);
-    } else if (g.dtype == VRC_BF16) {
-        used = launch_stats<VRC_BF16>(a, ctx->sm_count, grid, smem, hist, st);
+    if (a.g.dtype == VRC_F32) return launch_stats<VRC_F32>(a, ctx->sm_count, grid, smem, hist, st);
+    if (a.g.dtype == VRC_BF16) return launch_stats<VRC_BF16>(a, ctx->sm_count, grid, smem, hist, st);
+    k_stats_codes<<<grid, kStatsThreads, 0, st>>>(a);
+    return grid;
+}
+
+// Out-of-core cubes: run `pass(pool, brick0, nrun)` over the cube in runs of
+// consecutive bricks copied through the two halves of the device ring; run r
+// loads while run r - 1 is processed (copies on a side stream, Sec. 2: streams
+// overlap I/O).  Bricks not in the host cache are provided on this thread.
+template <class Pass>
+vrc_status for_ring_runs(vrc_ctx *ctx, Cube *c, cudaStream_t st, Pass pass)
+{
+    const int half = c->ring / 2;
+    const int64_t nb = c->g.nbricks;
+    cudaStream_t cs;
+    VRC_CK(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t ev[5] = {};
+    vrc_status s = VRC_OK;
+    for (int i = 0; i < 5 && s == VRC_OK; ++i) {
+        const cudaError_t e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) s = cuda_err(ctx, e, "ring events");
+    }
+    cudaEvent_t *ready = ev, *consumed = ev + 2, entry = ev[4];
+    if (s == VRC_OK) {
+        cudaEventRecord(entry, st);   // earlier work on `st` may still read the ring
+        cudaStreamWaitEvent(cs, entry, 0);
+    }
+    for (int64_t r = 0, b0 = 0; s == VRC_OK && b0 < nb; ++r, b0 += half) {
+        const int h = (int)(r & 1);
+        const int64_t n = std::min<int64_t>(half, nb - b0);
+        if (r >= 2) cudaStreamWaitEvent(cs, consumed[h], 0);   // run r - 2 has left this half
+        if ((s = ring_load(ctx, c, b0, n, h * half, cs, ready[h])) != VRC_OK) break;
+        cudaStreamWaitEvent(st, ready[h], 0);
+        if ((s = pass((const uint8_t *)c->ring_pool + (int64_t)h * half * c->g.brick_bytes, b0, n)) != VRC_OK) break;
+        cudaEventRecord(consumed[h], st);
+    }
+    // the side stream's copies are joined into `st` before anything is released
+    cudaEventRecord(entry, cs);
+    cudaStreamWaitEvent(st, entry, 0);
+    for (int i = 0; i < 5; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    cudaStreamDestroy(cs);
+    return s;
+}
+
+}  // namespace
+
+// Launch the fused statistics pass + final merge on `st`.  dev_hist (nbins
+// counters) is zeroed here; partials is scratch of stats_scratch_bytes().
+vrc_status stats_launch_with(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *dev_out, uint64_t *dev_hist,
+                             void *partials, cudaStream_t st)
+{
+    const int grid = stats_grid(ctx);
+    StatsArgs a = make_stats_args(c, nbins, dev_hist, partials, (const uint8_t *)c->pool);
+    if (nbins > 0) VRC_CK(ctx, cudaMemsetAsync(dev_hist, 0, sizeof(uint64_t) * nbins, st));
+    int used = grid;
+    if (!c->streamed) {
+        used = launch_stats_dt(ctx, a, grid, nbins, st);
+        count_launch(ctx);
     } else {
-        k_stats_codes<<<grid, kStatsThreads, 0, st>>>(a);
+        // per-brick non-finite counts steer the pass; every run adds into one
+        // partial per block (fixed order: block, then run)
+        vrc_status s = stage_h2d(ctx, st, {{c->bnonfinite, c->h_bnonfinite.data(), sizeof(int32_t) * (size_t)c->g.nbricks}});
+        if (s != VRC_OK) return s;
+        VRC_CK(ctx, cudaMemsetAsync(partials, 0, stats_scratch_bytes(ctx), st));
+        a.accumulate = 1;
+        s = for_ring_runs(ctx, c, st, [&](const uint8_t *pool, int64_t b0, int64_t n) {
+            StatsArgs r = a;
+            r.pool = pool;
+            r.brick0 = b0;
+            r.nrun = n;
+            // the same grid for every run: partial i always belongs to block i
+            launch_stats_dt(ctx, r, grid, nbins, st);
+            count_launch(ctx);
+            const cudaError_t e = cudaGetLastError();
+            return e == cudaSuccess ? VRC_OK : cuda_err(ctx, e, "statistics run");
+        });
+        if (s != VRC_OK) return s;
         used = grid;
     }
     k_stats_final<<<1, 256, 0, st>>>(a.partials, used, c->vmin, c->vmax, a.shift, a.dscale, dev_out);
-    count_launch(ctx, 2);
+    count_launch(ctx);
     VRC_CK(ctx, cudaGetLastError());
     return VRC_OK;
 }
@@ -696,7 +787,9 @@ static vrc_status check_stats_args(vrc_ctx *ctx, int64_t cube_id, int32_t nbins,
     if (nbins < 0 || nbins > 65536) return set_err(ctx, VRC_E_INVAL, "nbins must be in [0, 65536]");
     Cube *c = find_cube(ctx, cube_id);
     if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
-    if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "statistics need a resident cube");
+    if (c->streamed && c->n_filled < c->n_host)
+        return set_err(ctx, VRC_E_INVAL, "streamed cube: %lld of %lld host slots never written",
+                       (long long)(c->n_host - c->n_filled), (long long)c->n_host);
     *out = c;
     return VRC_OK;
 }
@@ -770,6 +863,12 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     a.bnonfinite = c->bnonfinite;
     a.all_full = c->g.dims[0] % c->g.B == 0 && c->g.dims[1] % c->g.B == 0 && c->g.dims[2] % c->g.B == 0;
     a.hist = dh;
+    a.brick0 = 0;
+    a.nrun = c->g.nbricks;
+    if (c->streamed &&
+        (s = stage_h2d(ctx, st, {{c->bnonfinite, c->h_bnonfinite.data(), sizeof(int32_t) * (size_t)c->g.nbricks}})) !=
+            VRC_OK)
+        return s;
     int occ = 1;
     if (c->g.dtype == VRC_F32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_F32>, kStatsThreads, 0);
     else if (c->g.dtype == VRC_BF16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_BF16>, kStatsThreads, 0);
@@ -789,12 +888,28 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
         a.prefix = pass == 0 ? 0u : key >> (a.shift + a.nbits);
         const int nb = 1 << a.nbits;
         VRC_CK(ctx, cudaMemsetAsync(dh, 0, nb * sizeof(unsigned long long), st));
-        if (codes)
+        if (codes) {
             k_select_codes<<<(unsigned)std::min<int64_t>((nentries + 255) / 256, grid), 256, 0, st>>>(
                 table, c->scales, nentries, a);
-        else if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(a);
-        else k_select_hist<VRC_BF16><<<grid, kStatsThreads, 0, st>>>(a);
-        count_launch(ctx);
+            count_launch(ctx);
+        } else if (c->streamed) {
+            // out-of-core (float32): the pass runs over the cube run by run through the ring
+            s = for_ring_runs(ctx, c, st, [&](const uint8_t *pool, int64_t b0, int64_t n) {
+                SelArgs r = a;
+                r.pool = pool;
+                r.brick0 = b0;
+                r.nrun = n;
+                k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(r);
+                count_launch(ctx);
+                const cudaError_t e = cudaGetLastError();
+                return e == cudaSuccess ? VRC_OK : cuda_err(ctx, e, "median run");
+            });
+            if (s != VRC_OK) return s;
+        } else {
+            if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(a);
+            else k_select_hist<VRC_BF16><<<grid, kStatsThreads, 0, st>>>(a);
+            count_launch(ctx);
+        }
         VRC_CK(ctx, cudaGetLastError());
         VRC_CK(ctx, cudaMemcpyAsync(h.data(), dh, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         VRC_CK(ctx, cudaStreamSynchronize(st));

@@ -80,6 +80,17 @@ struct Cube {
     void *ring_pool = nullptr;    // device, ring slots
     std::vector<uint8_t> host_filled;
     int64_t n_filled = 0;         // host slots written at least once
+    // out-of-core cubes with a brick provider: host slot s caches brick
+    // slot_brick[s] (-1: none); slot_ev[s] follows the last copy out of slot s
+    vrc_brick_source_fn source = nullptr;
+    void *source_user = nullptr;
+    std::vector<int64_t> slot_brick;
+    std::vector<cudaEvent_t> slot_ev;
+    std::vector<uint8_t> slot_ev_live;
+    std::vector<float> source_buf;      // (B+2)^3 floats handed to the provider
+    uint64_t source_calls = 0;          // provider calls since creation
+    std::vector<double> h_bsum;         // per brick: sum and count of its finite interior values
+    std::vector<int64_t> h_bcnt;
     // render copies of the bricks as 2D layered CUDA arrays (layers along z),
     // read by texture gathers (2x2 texel footprints) in the fused renderer
     std::vector<TexArray> tex_arrays;
@@ -221,6 +232,17 @@ size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs);
 size_t render_hetero_stage_bytes(size_t n_jobs);
 
 void server_stop(vrc_ctx *ctx);
+
+// Out-of-core cubes (pack.cu).  host_brick makes host slot brick % n_host hold
+// brick `brick` (calling the provider when another brick is there, after the
+// slot's previous copy has completed) and returns the slot; host_copied
+// records, on `st`, the end of a copy out of that slot.
+vrc_status host_brick(vrc_ctx *ctx, Cube *c, int64_t brick, int64_t *slot);
+vrc_status host_copied(vrc_ctx *ctx, Cube *c, int64_t slot, cudaStream_t st);
+// Copy bricks [b0, b0 + n) of an out-of-core cube into consecutive device ring
+// slots starting at ring slot `first` (copy stream cs, after `after`); records
+// `done` on cs when the copies are complete.
+vrc_status ring_load(vrc_ctx *ctx, Cube *c, int64_t b0, int64_t n, int first, cudaStream_t cs, cudaEvent_t done);
 
 // Slab renderer (slab.cu).
 struct JobDesc;

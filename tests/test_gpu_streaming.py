@@ -200,3 +200,147 @@ def test_unfilled_streamed_cube_is_rejected(ctx, cube128):
     with pytest.raises(vrc.VrcError, match="INVAL"):
         ctx.render_mip(cid, cubegen.orbit_cameras((32, 32, 32), 1), vrc.raycfg(16, 16, 0.5))
     ctx.cube_free(cid)
+
+
+def _provider(v, B):
+    """Python brick provider over cube v (z, y, x) that counts its calls."""
+    dims = (v.shape[2], v.shape[1], v.shape[0])
+    nb = [(d + B - 1) // B for d in dims]
+    calls = []
+
+    def source(b, bx, by, bz):
+        calls.append(b)
+        assert b == (bz * nb[1] + by) * nb[0] + bx
+        return brick_with_halo(v, B, b, nb)
+    return source, calls
+
+
+def _check_stats_equal(got, ref, hist_got, hist_ref):
+    assert got["min"] == ref["min"] and got["max"] == ref["max"]
+    assert got["n"] == ref["n"] and got["n_nonfinite"] == ref["n_nonfinite"]
+    assert abs(got["mean"] - ref["mean"]) <= 1e-9 * max(abs(ref["mean"]), ref["std"])
+    assert abs(got["std"] - ref["std"]) <= 1e-9 * ref["std"]
+    assert np.array_equal(hist_got, hist_ref)
+
+
+@pytest.mark.parametrize("n_host", [None, 3])
+def test_provider_cube_matches_resident_and_oracle(ctx, cube128, n_host):
+    """Out-of-core cube whose bricks come from a provider (Sec. 2: a cube larger
+    than memory read sub-cube by sub-cube).  With a host cache of every brick
+    the provider is called once per brick; with 3 slots every render and
+    statistics pass asks for bricks again.  Renders, statistics, histogram and
+    median must equal those of the resident cube and the oracle."""
+    import paper_1111_6661_b300 as vrc
+    v = cube128[:64, :48, :80].copy()
+    v[40, 10, 70] = np.nan                   # a non-finite voxel in a border brick
+    dims = (80, 48, 64)
+    source, calls = _provider(v, 16)
+    nb_total = 5 * 3 * 4
+    sid = ctx.cube_upload_streamed(dims, 16, source, n_host or nb_total, 4)
+    assert sorted(calls) == list(range(nb_total))          # one scan of every brick
+    rid = ctx.cube_upload(v, "f32", brick=16)
+    info = ctx.cube_info(sid)
+    fin = v[np.isfinite(v)]
+    assert info["vmin"] == fin.min() and info["vmax"] == fin.max()
+    cams = cubegen.orbit_cameras(dims, 2) + [cubegen.camera("persp", (30.2, 20.5, 31.7), (0, 0, 0), (0, 1, 0),
+                                                            fovy_deg=70)]
+    rc = vrc.raycfg(40, 32, 0.5)
+    n0 = len(calls)
+    a = ctx.render_mip(sid, cams, rc).cpu()
+    assert torch.equal(a, ctx.render_mip(rid, cams, rc).cpu())
+    assert (len(calls) == n0) == (n_host is None)            # cache hits only when every brick fits
+    tf = cubegen.tf_dense()
+    a = ctx.render_dvr(sid, cams, rc, tf).cpu().numpy().reshape(len(cams), -1, 4).astype(np.float64)
+    b = ctx.render_dvr(rid, cams, rc, tf).cpu().numpy().reshape(len(cams), -1, 4)
+    assert np.abs(a - b).max() <= 1e-4
+    for i, cam in enumerate(cams):
+        r = oracle.render(v, cam, 40, 32, 0.5, "trilinear", "dvr", tf=tf, vmin=info["vmin"], vmax=info["vmax"])
+        d = np.abs(a[i] - r["out"]).max(axis=1)
+        ok = (d <= 1e-4) | (r["fragile"] & np.all((a[i] >= r["lo"] - 1e-4) & (a[i] <= r["hi"] + 1e-4), axis=1))
+        assert ok.all()
+    # statistics and the median (Sec. 3) stream the bricks through the ring
+    s, h = ctx.cube_stats(sid, 300)
+    sr, hr = ctx.cube_stats(rid, 300)
+    _check_stats_equal(s, sr, h, hr)
+    ref = oracle.stats(v)
+    _check_stats_equal(s, ref, h, oracle.histogram(v, ref["min"], ref["max"], 300))
+    assert s["n_nonfinite"] == 1
+    m = ctx.cube_median(sid)
+    assert m == ctx.cube_median(rid) == oracle.median(v)
+    ctx.cube_free(sid)
+    ctx.cube_free(rid)
+
+
+def test_cubegen_provider_equals_generated_cube(ctx):
+    """The generator's C brick provider (no Python per brick) builds, brick by
+    brick, the same cube as generating it whole: renders and statistics of the
+    out-of-core cube equal those of the resident upload (ragged dims: border
+    bricks take clamp-to-edge halos)."""
+    import paper_1111_6661_b300 as vrc
+    dims = (70, 45, 33)
+    src = cubegen.BrickSource(dims, 6, 21, 16)
+    sid = ctx.cube_upload_streamed(dims, 16, (src.fn, src.user), 5, 2)
+    nbr = 5 * 3 * 3
+    assert src.calls == nbr
+    v = cubegen.generate(dims, 6, 21)
+    rid = ctx.cube_upload(v, "f32", brick=16)
+    cams = cubegen.orbit_cameras(dims, 2) + [cubegen.ortho_z_camera(dims)]
+    rc = vrc.raycfg(48, 40, 0.5)
+    assert torch.equal(ctx.render_mip(sid, cams, rc).cpu(), ctx.render_mip(rid, cams, rc).cpu())
+    assert src.calls > nbr                                    # 5 host slots: bricks provided again
+    s, h = ctx.cube_stats(sid, 64)
+    sr, hr = ctx.cube_stats(rid, 64)
+    _check_stats_equal(s, sr, h, hr)
+    assert ctx.cube_median(sid) == ctx.cube_median(rid)
+    ctx.cube_free(sid)
+    ctx.cube_free(rid)
+
+
+def test_provider_failure_is_reported(ctx, cube128):
+    """A provider that fails makes the call that needed the brick fail with
+    VRC_E_SOURCE: at creation no cube is made; later, the render or statistics
+    call fails and the context (and the cube) stay usable."""
+    import paper_1111_6661_b300 as vrc
+    v = cube128[:32, :32, :48].copy()
+    dims = (48, 32, 32)
+    source, calls = _provider(v, 16)
+    fail = {"brick": 4}
+
+    def flaky(b, bx, by, bz):
+        if b == fail["brick"]:
+            raise RuntimeError("no such brick")
+        return source(b, bx, by, bz)
+    with pytest.raises(vrc.VrcError, match="SOURCE"):
+        ctx.cube_upload_streamed(dims, 16, flaky, 12, 2)
+    fail["brick"] = -1
+    sid = ctx.cube_upload_streamed(dims, 16, flaky, 2, 2)       # 2 host slots for 12 bricks
+    cams = cubegen.orbit_cameras(dims, 1)
+    rc = vrc.raycfg(24, 24, 0.5)
+    good = ctx.render_mip(sid, cams, rc).cpu()
+    fail["brick"] = 7
+    with pytest.raises(vrc.VrcError, match="SOURCE"):
+        ctx.render_mip(sid, cams, rc)
+    with pytest.raises(vrc.VrcError, match="SOURCE"):
+        ctx.cube_stats(sid, 16)
+    torch.cuda.synchronize()
+    fail["brick"] = -1
+    assert torch.equal(ctx.render_mip(sid, cams, rc).cpu(), good)
+    with pytest.raises(vrc.VrcError, match="UNSUPPORTED"):
+        ctx.cube_put_brick(sid, 0, brick_with_halo(v, 16, 0, (3, 2, 2)))
+    with pytest.raises(vrc.VrcError, match="UNSUPPORTED"):
+        ctx.render_mip(sid, cams, vrc.raycfg(24, 24, 0.5, path="zerocopy"))
+    ctx.cube_free(sid)
+
+
+def test_stats_of_caller_filled_streamed_cube(ctx, cube128):
+    """Statistics of an out-of-core cube whose host slots the caller filled
+    (vrc_cube_put_brick) equal those of the resident cube."""
+    v = cube128[:48, :40, :56].copy()
+    sid, _ = make_streamed(ctx, v, 16, ring=2)
+    rid = ctx.cube_upload(v, "f32", brick=16)
+    s, h = ctx.cube_stats(sid, 4096)
+    sr, hr = ctx.cube_stats(rid, 4096)
+    _check_stats_equal(s, sr, h, hr)
+    assert ctx.cube_median(sid) == ctx.cube_median(rid)
+    ctx.cube_free(sid)
+    ctx.cube_free(rid)
