@@ -655,34 +655,20 @@ def run_precision(args):
 
 
 # ---------------------------------------------------------------- out-of-core form
-def run_ooc(args):
-    """4096x4096x3072 fp32 cube in 256^3 bricks (+halo) streamed from pinned
-    host memory; host RAM holds an aliased pool of K distinct bricks."""
-    import torch
+def host_mem_available() -> int:
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
 
-    import cubegen
-    import paper_1111_6661_b300 as vrc
-    dims = tuple(args.dims) if args.dims else (4096, 4096, 3072)
-    B = 256
-    nb = [(d + B - 1) // B for d in dims]
-    total = nb[0] * nb[1] * nb[2]
-    K = min(total, args.host_bricks)
-    nsrc = max(8, int(96000 * (dims[0] * dims[1] * dims[2]) / (4096 * 4096 * 3072)))
-    ctx = vrc.Context(0)
-    cid = ctx.cube_create_streamed(dims, B, K, args.ring)
-    t0 = time.perf_counter()
-    for slot in range(K):
-        b = slot
-        bx, by, bz = b % nb[0], (b // nb[0]) % nb[1], b // (nb[0] * nb[1])
-        lo = [bx * B - 1, by * B - 1, bz * B - 1]
-        box = [max(0, lo[a]) for a in range(3)]
-        hi = [min(dims[a], lo[a] + B + 2) for a in range(3)]
-        sub = cubegen.generate(dims, nsrc, 4, box=(box[0], box[1], box[2], hi[0] - box[0], hi[1] - box[1],
-                                                    hi[2] - box[2]))
-        pad = [(box[a] - lo[a], lo[a] + B + 2 - hi[a]) for a in (2, 1, 0)]
-        ctx.cube_put_brick(cid, slot, np.pad(sub, pad, mode="edge"))
-    fill_s = time.perf_counter() - t0
-    # host->device link probe: pinned copies of one brick-sized buffer
+
+def link_probe_gbs() -> float:
+    """Host-to-device link: pinned copies of a 1 GiB buffer (CUDA events)."""
+    import torch
     hb = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
     db = torch.empty(hb.shape, dtype=torch.uint8, device="cuda")
     for _ in range(2):
@@ -694,28 +680,119 @@ def run_ooc(args):
         db.copy_(hb, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    link_gbs = 8 * hb.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    gbs = 8 * hb.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9
     del db, hb
+    return gbs
+
+
+def ooc_window_parity(ctx, cid, dims, nsrc, seed, info, tf, x0=1536, y0=1024, win=64):
+    """Orthographic view along z of a win x win window at native resolution,
+    rendered from the out-of-core cube, against the oracle on a generated
+    sub-box holding the window's columns (plus a two-voxel margin) over the
+    full depth: rays along z keep x and y exact, so translating the camera by
+    the sub-box origin gives the same samples."""
+    import torch
+
+    import cubegen
+    import oracle
+    import paper_1111_6661_b300 as vrc
+    cx, cy, nz = x0 + win // 2, y0 + win // 2, dims[2]
+    cam = cubegen.camera("ortho", (cx, cy, -1.0), (cx, cy, float(nz)), (0, 1, 0), ortho_height=float(win))
+    rc = vrc.raycfg(win, win, 0.5, "trilinear")
+    out = {}
+    sub = cubegen.generate(dims, nsrc, seed, box=(x0 - 2, y0 - 2, 0, win + 4, win + 4, nz))
+    cam_s = cubegen.camera("ortho", (cx - (x0 - 2), cy - (y0 - 2), -1.0), (cx - (x0 - 2), cy - (y0 - 2), float(nz)),
+                           (0, 1, 0), ortho_height=float(win))
+    for mode in ("mip", "dvr"):
+        img = ctx.render_mip(cid, [cam], rc) if mode == "mip" else ctx.render_dvr(cid, [cam], rc, tf, 0.99)
+        torch.cuda.synchronize()
+        got = img.cpu().numpy().reshape(win * win, -1).astype(np.float64)
+        r = oracle.render(sub, cam_s, win, win, 0.5, "trilinear", mode, tf=tf, vmin=info["vmin"], vmax=info["vmax"])
+        ref = r["out"].reshape(got.shape)
+        if mode == "mip":
+            err = float((np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)).max())
+            out[mode] = {"max_rel_err": err, "ok": err <= 1e-5}
+        else:
+            d = np.abs(got - ref).max(axis=1)
+            inside = np.all((got >= r["lo"] - 1e-4) & (got <= r["hi"] + 1e-4), axis=1)
+            ok = (d <= 1e-4) | (r["fragile"] & inside)
+            out[mode] = {"max_abs_err": float(d.max()), "fragile_pixels": int(r["fragile"].sum()),
+                         "ok": bool(ok.all())}
+    out["pixels"] = win * win
+    out["window"] = [x0, y0, win]
+    return out
+
+
+def run_ooc(args):
+    """4096x4096x3072 fp32 cube in 256^3 bricks (+halo), out of core.  Default:
+    the bricks come from the seeded generator's C brick provider through a
+    pinned host cache as large as host memory allows (the cube itself, 216 GB
+    with halos, does not fit this machine's host memory); --aliased instead fills a
+    pinned pool of --host-bricks distinct bricks that logical bricks alias."""
+    import torch
+
+    import cubegen
+    import paper_1111_6661_b300 as vrc
+    dims = tuple(args.dims) if args.dims else (4096, 4096, 3072)
+    B = 256
+    nb = [(d + B - 1) // B for d in dims]
+    total = nb[0] * nb[1] * nb[2]
+    nsrc = max(8, int(96000 * (dims[0] * dims[1] * dims[2]) / (4096 * 4096 * 3072)))
+    seed = 4
+    brick_bytes = (B + 2 * 4) * (B + 2) * (B + 2) * 4
+    avail = host_mem_available()
+    ctx = vrc.Context(0)
+    src = None
+    t0 = time.perf_counter()
+    if args.aliased:
+        K = min(total, args.host_bricks)
+        cid = ctx.cube_create_streamed(dims, B, K, args.ring)
+        for slot in range(K):
+            b = slot
+            bx, by, bz = b % nb[0], (b // nb[0]) % nb[1], b // (nb[0] * nb[1])
+            lo = [bx * B - 1, by * B - 1, bz * B - 1]
+            box = [max(0, lo[a]) for a in range(3)]
+            hi = [min(dims[a], lo[a] + B + 2) for a in range(3)]
+            sub = cubegen.generate(dims, nsrc, seed, box=(box[0], box[1], box[2], hi[0] - box[0], hi[1] - box[1],
+                                                          hi[2] - box[2]))
+            pad = [(box[a] - lo[a], lo[a] + B + 2 - hi[a]) for a in (2, 1, 0)]
+            ctx.cube_put_brick(cid, slot, np.pad(sub, pad, mode="edge"))
+    else:
+        # host cache: every brick if it fits, else what 70% of the available
+        # host memory holds (the rest is regenerated on demand)
+        K = total if total * brick_bytes <= 0.7 * avail else max(2, int(0.7 * avail) // brick_bytes)
+        K = min(K, args.host_bricks) if args.host_bricks > 0 else K
+        src = cubegen.BrickSource(dims, nsrc, seed, B)
+        cid = ctx.cube_upload_streamed(dims, B, (src.fn, src.user), K, args.ring)
+    create_s = time.perf_counter() - t0
+    scan_calls = src.calls if src else 0
+    link_gbs = link_probe_gbs()
     cams = cubegen.orbit_cameras(dims, 1)
     rc = vrc.raycfg(1920, 1080, 0.5, "trilinear")
     tf = cubegen.tf_sparse()
     out = torch.empty((1, 1080, 1920, 4), device="cuda")
-    ctx.render_dvr(cid, cams, rc, tf, 0.99, out=out)   # warm-up
-    torch.cuda.synchronize()
-    times = []
-    for _ in range(args.steps):
+    frames = []
+    for f in range(max(1, args.steps)):
+        c0 = src.calls if src else 0
+        w0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         ctx.render_dvr(cid, cams, rc, tf, 0.99, out=out)
         e1.record()
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
+        frames.append({"frame_ms": e0.elapsed_time(e1), "wall_ms": 1e3 * (time.perf_counter() - w0),
+                       "provider_calls": (src.calls - c0) if src else 0})
     nsamp = ctx.last_render_samples()
+    traversed, culled = ctx.last_render_bricks()
     info = ctx.cube_info(cid)
-    brick_bytes = (B + 2 * 4) * (B + 2) * (B + 2) * 4
-    frame_ms = float(np.median(times))
-    streamed = total * brick_bytes
+    streamed = traversed * brick_bytes
+    frame_ms = frames[-1]["frame_ms"]
+    parity = None
+    if not args.aliased and not args.no_parity:
+        parity = ooc_window_parity(ctx, cid, dims, nsrc, seed, info, tf,
+                                   x0=min(1536, dims[0] - 68), y0=min(1024, dims[1] - 68))
     zc = None
-    if args.zerocopy_frames > 0:
+    if args.zerocopy_frames > 0 and (args.aliased or K == total):
         # zero-copy variant: the brick kernels read the mapped pinned slots in place
         ref = out.clone()
         rz = vrc.raycfg(1920, 1080, 0.5, "trilinear", path="zerocopy")
@@ -732,11 +809,17 @@ def run_ooc(args):
               "note": "bricks read in place from mapped pinned host memory; no device ring, no copies"}
     line = {"metric": "out-of-core DVR frame time", "value": frame_ms, "unit": "ms", "higher_is_better": False,
             "workload": f"ooc{dims[0]}x{dims[1]}x{dims[2]}", "bricks": total, "host_slots": K,
-            "ring_bricks": args.ring, "brick_bytes": brick_bytes, "bytes_streamed_per_frame": streamed,
+            "host_mem_available_bytes": avail, "host_pinned_bytes": K * brick_bytes,
+            "mode": "aliased pool" if args.aliased else "brick provider (seeded generator) + host cache",
+            "create_s": create_s, "scan_provider_calls": scan_calls, "frames": frames,
+            "ring_bricks": args.ring, "brick_bytes": brick_bytes, "bricks_traversed": traversed,
+            "bricks_culled": culled, "bytes_streamed_per_frame": streamed,
             "achieved_link_gbs": streamed / (frame_ms / 1e3) / 1e9, "pinned_h2d_probe_gbs": link_gbs,
             "link_bound_frame_ms": streamed / (link_gbs * 1e9) * 1e3, "samples": nsamp,
-            "samples_per_s": nsamp / (frame_ms / 1e3), "host_fill_s": fill_s, "frames": args.steps,
-            "note": "logical brick b reads pinned host slot b % host_slots when host RAM is short",
+            "samples_per_s": nsamp / (frame_ms / 1e3), "parity_window": parity,
+            "note": ("bricks missing from the host cache are generated on the rendering thread before their "
+                     "copies (provider-bound frames)") if not args.aliased else
+                    "logical brick b reads pinned host slot b % host_slots",
             "zero_copy_variant": zc}
     ctx.cube_free(cid)
     ctx.close()
@@ -822,7 +905,10 @@ def main():
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
     ap.add_argument("--dims", type=int, nargs=3, default=None, help="precision/ooc: cube dims")
     ap.add_argument("--error-pixels", type=int, default=4096)
-    ap.add_argument("--host-bricks", type=int, default=512)
+    ap.add_argument("--host-bricks", type=int, default=0,
+                    help="ooc: host slots (aliased pool: default 512; provider cache: 0 = as many as fit)")
+    ap.add_argument("--aliased", action="store_true", help="ooc: caller-filled aliased pool instead of the provider")
+    ap.add_argument("--no-parity", action="store_true", help="ooc: skip the oracle check of a window")
     ap.add_argument("--ring", type=int, default=8)
     ap.add_argument("--zerocopy-frames", type=int, default=1,
                     help="ooc workload: frames timed with the zero-copy path (0 = skip)")
@@ -837,6 +923,8 @@ def main():
     if args.workload == "mip_native":
         return run_mip_native(args)
     if args.workload == "ooc":
+        if args.aliased and args.host_bricks <= 0:
+            args.host_bricks = 512
         return run_ooc(args)
     if args.workload == "serving":
         return run_serving(args)

@@ -215,8 +215,10 @@ typedef int32_t (*vrc_brick_source_fn)(void *user, int64_t brick, int32_t bx, in
  * brick's minimum and maximum (the transfer-function range, brick culling),
  * the sums that centre the statistics and its non-finite voxels; it returns
  * when all bricks have been seen.  n_host_bricks pinned host slots (1 ..
- * number of bricks) cache provided bricks: brick b lives in slot
- * b % n_host_bricks.  Renders, statistics and the median stream the bricks
+ * number of bricks) cache provided bricks: with a slot for every brick, brick
+ * b lives in slot b; otherwise the first n_host_bricks - T bricks keep their
+ * slots and the others share the last T = min(n_host_bricks, 16) slots.
+ * Renders, statistics and the median stream the bricks
  * they need through ring_bricks device slots (0 = 8; at least 2; charged to
  * the budget) and call `source` again, on the calling thread, for every brick
  * whose slot holds another brick (after the slot's previous copy to the

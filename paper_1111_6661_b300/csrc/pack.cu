@@ -12,6 +12,8 @@
 
 #include "vrc_internal.h"
 
+int64_t host_slot(const Cube *c, int64_t b);   // out-of-core host cache (below)
+
 namespace {
 
 // Blocks per brick for a pass over the bricks whose blocks (256 threads) each
@@ -985,7 +987,7 @@ vrc_status vrc_cube_upload_streamed(vrc_ctx *ctx, vrc_brick_source_fn source, vo
     // every brick once, in index order: extrema, sums and non-finite counts;
     // the host cache keeps the last brick of each slot
     for (int64_t b = 0; b < g.nbricks && s == VRC_OK; ++b) {
-        const int64_t slot = b % c->n_host;
+        const int64_t slot = host_slot(c, b);
         BrickMeta m;
         s = call_source(ctx, c, b);
         if (s != VRC_OK) break;
@@ -1091,9 +1093,21 @@ vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t
 
 // ------------------------------------------------------------ out-of-core
 
+// Host slot of brick b.  Caller-filled cubes: b % n_host.  Provider cubes:
+// when the cache holds every brick, slot b; otherwise the first n_host - T
+// bricks keep their slots for good and the others share the last T slots
+// (T = min(n_host, 16)), so a frame that touches every brick provides
+// nbricks - (n_host - T) of them again instead of evicting cached ones.
+int64_t host_slot(const Cube *c, int64_t b)
+{
+    if (!c->source || c->n_host >= c->g.nbricks) return b % c->n_host;
+    const int64_t T = std::min<int64_t>(c->n_host, 16), keep = c->n_host - T;
+    return b < keep ? b : keep + (b - keep) % T;
+}
+
 vrc_status host_brick(vrc_ctx *ctx, Cube *c, int64_t brick, int64_t *slot)
 {
-    const int64_t sl = brick % c->n_host;
+    const int64_t sl = host_slot(c, brick);
     *slot = sl;
     if (!c->source || c->slot_brick[sl] == brick) return VRC_OK;
     // another brick lives in the slot: its last copy to the device must be done

@@ -223,7 +223,7 @@ def _check_stats_equal(got, ref, hist_got, hist_ref):
     assert np.array_equal(hist_got, hist_ref)
 
 
-@pytest.mark.parametrize("n_host", [None, 3])
+@pytest.mark.parametrize("n_host", [None, 3, 20])
 def test_provider_cube_matches_resident_and_oracle(ctx, cube128, n_host):
     """Out-of-core cube whose bricks come from a provider (Sec. 2: a cube larger
     than memory read sub-cube by sub-cube).  With a host cache of every brick
