@@ -495,8 +495,11 @@ typedef struct {
  * number on the GPU is below max_inflight and their scratch fits the budget,
  * groups every admitted render into one heterogeneous persistent launch (each
  * request keeps its own cube, camera, image size and transfer function) on one
- * of n_streams streams, and runs statistics requests on the next stream, so
- * new arrivals overlap work already on the GPU.  The cube must stay allocated
+ * of n_streams streams, and runs statistics requests and render batches of at
+ * most 512 x 512 pixels on a stream of the highest priority.  Larger render
+ * batches run as a series of launches of two waves of tiles each, so a
+ * request that arrives while they are on the GPU is admitted at once and gets
+ * SMs at the next launch boundary instead of after the whole batch.  The cube must stay allocated
  * until the request completes (vrc_cube_free returns VRC_E_BUSY before).
  * Errors at submit: VRC_E_BADID, VRC_E_INVAL; later errors arrive in
  * vrc_result.status.

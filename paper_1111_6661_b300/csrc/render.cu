@@ -1563,30 +1563,39 @@ vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, i
 
 // ------------------------------------------------------------- serving helper
 
+constexpr int kMaxSlices = 1024;   // launches per heterogeneous render batch (each with its own counter)
+
 size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs)
 {
-    return 1024 + 4096 * jobs.size() + sizeof(JobDesc) * jobs.size() + 1024;
+    return 4 * kMaxSlices + 1024 + 4096 * jobs.size() + sizeof(JobDesc) * jobs.size() + 1024;
 }
 
 size_t render_hetero_counter_bytes(size_t n_jobs) { return 16 * n_jobs; }
 
-size_t render_hetero_stage_bytes(size_t n_jobs) { return 4096 * n_jobs + sizeof(JobDesc) * n_jobs + 256; }
+size_t render_hetero_stage_bytes(size_t n_jobs) { return 4096 * n_jobs + sizeof(JobDesc) * n_jobs + 4 * kMaxSlices + 512; }
 
-// One persistent launch over renders of different cubes, image sizes, cameras
-// and transfer functions (all with the same mode/sampling/dtype).  Job i counts
-// its samples into dev_samples[2i] (lattice) and [2i+1] (evaluated), zeroed here.  host_stage: pinned host memory
-// of render_hetero_stage_bytes() used to upload the job table without waiting.
+// Persistent launches over renders of different cubes, image sizes, cameras
+// and transfer functions (all with the same mode/sampling/dtype).  The batch's
+// (job, tile) items are cut into slices of at most `slice_items` (0: one
+// launch), each one launch with its own work counter: requests that arrive
+// while a large batch runs get SMs at the next slice boundary (from a stream
+// of higher priority) instead of after the whole batch; every pixel is
+// computed the same way whichever launch takes its tile.  Job i counts its
+// samples into dev_samples[2i] (lattice) and [2i+1] (evaluated), zeroed here.
+// host_stage: pinned host memory of render_hetero_stage_bytes() used to upload
+// the job table without waiting.
 vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream_t st, void *scratch,
-                         size_t scratch_bytes, unsigned long long *dev_samples, void *host_stage)
+                         size_t scratch_bytes, unsigned long long *dev_samples, void *host_stage, int64_t slice_items)
 {
     if (hj.empty()) return VRC_OK;
     const int mode = hj[0].mode, sampling = hj[0].rc.sampling, dt = hj[0].cube->g.dtype;
     Arena ar{(char *)scratch, 0, scratch_bytes};
-    int *counter = ar.take<int>(1);
+    int *counters = ar.take<int>(kMaxSlices);
     float4 *dtf = ar.take<float4>(256 * hj.size());
     JobDesc *djobs = ar.take<JobDesc>(hj.size());
     float *htf = (float *)host_stage;
     JobDesc *hjobs = (JobDesc *)((char *)host_stage + 4096 * hj.size());
+    int *hcount = (int *)((char *)hjobs + sizeof(JobDesc) * hj.size());
     int64_t total = 0;
     for (size_t i = 0; i < hj.size(); ++i) {
         const HetJob &h = hj[i];
@@ -1599,21 +1608,40 @@ vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream
         total += (int64_t)hjobs[i].tiles_x * hjobs[i].tiles_y;
         if (mode) std::memcpy(htf + 1024 * i, h.tf_host, 4096);
     }
-    VRC_CK(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    VRC_CK(ctx, cudaMemsetAsync(dev_samples, 0, 2 * sizeof(unsigned long long) * hj.size(), st));
-    if (mode) VRC_CK(ctx, cudaMemcpyAsync(dtf, htf, 4096 * hj.size(), cudaMemcpyHostToDevice, st));
-    VRC_CK(ctx, cudaMemcpyAsync(djobs, hjobs, sizeof(JobDesc) * hj.size(), cudaMemcpyHostToDevice, st));
     bool tex = true, skip = true;
     for (size_t i = 0; i < hj.size(); ++i) {
         tex = tex && hj[i].cube->dtex != nullptr;
         skip = skip && hjobs[i].cellmax != nullptr;
     }
     skip = skip && tex;
-    const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * occupancy(mode, sampling, dt, tex, skip), total);
-    pick_fused(mode, sampling, dt, tex, skip)(grid, st, djobs, (int)hj.size(), total, counter);
-    count_launch(ctx);
+    // slices: slice s takes items [begin_s, begin_{s+1}); its counter starts at begin_s
+    int64_t per = slice_items > 0 ? slice_items : total;
+    per = std::max<int64_t>(per, (total + kMaxSlices - 1) / kMaxSlices);
+    const int nslices = (int)((total + per - 1) / per);
+    for (int k = 0; k < nslices; ++k) hcount[k] = (int)(k * per);
+    VRC_CK(ctx, cudaMemcpyAsync(counters, hcount, sizeof(int) * nslices, cudaMemcpyHostToDevice, st));
+    VRC_CK(ctx, cudaMemsetAsync(dev_samples, 0, 2 * sizeof(unsigned long long) * hj.size(), st));
+    if (mode) VRC_CK(ctx, cudaMemcpyAsync(dtf, htf, 4096 * hj.size(), cudaMemcpyHostToDevice, st));
+    VRC_CK(ctx, cudaMemcpyAsync(djobs, hjobs, sizeof(JobDesc) * hj.size(), cudaMemcpyHostToDevice, st));
+    const int per_sm = occupancy(mode, sampling, dt, tex, skip);
+    const fused_fn fn = pick_fused(mode, sampling, dt, tex, skip);
+    for (int k = 0; k < nslices; ++k) {
+        const int64_t end = std::min<int64_t>(total, (int64_t)(k + 1) * per);
+        const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, end - (int64_t)k * per);
+        fn(grid, st, djobs, (int)hj.size(), end, counters + k);
+        count_launch(ctx);
+    }
     VRC_CK(ctx, cudaGetLastError());
     return VRC_OK;
+}
+
+// Tiles per slice of a heterogeneous launch: two waves of persistent CTAs.
+int64_t render_hetero_slice_items(vrc_ctx *ctx, const std::vector<HetJob> &hj)
+{
+    if (hj.empty()) return 0;
+    bool tex = true;
+    for (const HetJob &h : hj) tex = tex && h.cube->dtex != nullptr;
+    return 2 * (int64_t)ctx->sm_count * occupancy(hj[0].mode, hj[0].rc.sampling, hj[0].cube->g.dtype, tex, false);
 }
 
 vrc_status validate_raycfg(vrc_ctx *ctx, const vrc_raycfg *rc) { return check_rc(ctx, rc); }

@@ -56,7 +56,8 @@ struct Server {
     std::deque<SReq *> queue;
     std::map<uint64_t, SReq *> tickets;
     uint64_t next_ticket = 1;
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;   // render batches (normal priority)
+    cudaStream_t urgent = nullptr;        // statistics and small renders (highest priority)
     size_t rr = 0;
     std::vector<SBatch *> running;
     int inflight = 0;
@@ -155,7 +156,10 @@ bool launch_batch(Server *S, SBatch *B, bool render)
         unsigned long long *cnt = (unsigned long long *)((char *)B->dmem + sbytes);
         char *hcnt = (char *)B->hmem + n * sizeof(vrc_stats);
         void *stage = (void *)round256((size_t)(hcnt + 16 * n));
-        s = render_hetero(ctx, jobs, B->st, B->dmem, sbytes, cnt, stage);
+        // batches on the normal streams run in slices, so that later arrivals on
+        // the urgent stream get SMs between them
+        s = render_hetero(ctx, jobs, B->st, B->dmem, sbytes, cnt, stage,
+                          B->st == S->urgent ? 0 : render_hetero_slice_items(ctx, jobs));
         if (s == VRC_OK) cudaMemcpyAsync(hcnt, cnt, 16 * n, cudaMemcpyDeviceToHost, B->st);
     } else {
         const size_t per = ((stats_scratch_bytes(ctx) + 255) & ~(size_t)255) + 256;
@@ -261,7 +265,13 @@ void serve_loop(Server *S)
             for (auto &kv : groups) {
                 SBatch *B = new SBatch();
                 B->reqs = kv.second;
-                B->st = S->streams[S->rr++ % S->streams.size()];
+                // statistics and small renders (at most 512 x 512 pixels in the
+                // batch) take the urgent stream; larger render batches the others
+                int64_t pixels = 0;
+                for (SReq *q : B->reqs)
+                    if (q->r.kind != VRC_REQ_STATS) pixels += (int64_t)q->r.rc.width * q->r.rc.height;
+                const bool urgent = S->urgent && (kv.first < 0 || pixels <= 512 * 512);
+                B->st = urgent ? S->urgent : S->streams[S->rr++ % S->streams.size()];
                 cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
                 lk.unlock();
                 const bool ok = launch_batch(S, B, kv.first >= 0);
@@ -298,13 +308,22 @@ Server *server_get(vrc_ctx *ctx)
         Server *S = new Server();
         S->ctx = ctx;
         cudaSetDevice(ctx->device);
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            least = greatest = 0;
+        }
         for (int i = 0; i < ctx->cfg.n_streams; ++i) {
             cudaStream_t st;
-            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, least) != cudaSuccess) {
                 cudaGetLastError();
                 break;
             }
             S->streams.push_back(st);
+        }
+        if (cudaStreamCreateWithPriority(&S->urgent, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+            cudaGetLastError();
+            S->urgent = nullptr;
         }
         if (S->streams.empty()) {
             delete S;
@@ -361,6 +380,7 @@ void server_stop(vrc_ctx *ctx)
     S->cv_work.notify_all();
     S->th.join();
     for (auto &kv : S->tickets) delete kv.second;
+    if (S->urgent) S->streams.push_back(S->urgent);
     for (cudaStream_t st : S->streams) cudaStreamSynchronize(st);
     for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
     for (auto &b : S->pinned_all) cudaFreeHost(b.first);

@@ -227,7 +227,8 @@ struct HetJob {             // one request inside a heterogeneous launch
     float *out;             // device image
 };
 vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &jobs, cudaStream_t st, void *scratch,
-                         size_t scratch_bytes, unsigned long long *dev_samples, void *host_stage);
+                         size_t scratch_bytes, unsigned long long *dev_samples, void *host_stage, int64_t slice_items);
+int64_t render_hetero_slice_items(vrc_ctx *ctx, const std::vector<HetJob> &jobs);
 size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs);
 size_t render_hetero_stage_bytes(size_t n_jobs);
 

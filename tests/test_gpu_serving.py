@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import cubegen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -18,7 +19,8 @@ def setup():
     specs = [((64, 64, 64), "f32", 16), ((56, 40, 48), "bf16", 16), ((96, 96, 96), "f32", 32)]
     for i, (dims, dt, B) in enumerate(specs):
         v = cubegen.generate(dims, 3, 100 + i)
-        cubes[i] = (ctx.cube_upload(v, dt, brick=B), dims, v)
+        # the values the kernels see: the stored (dequantised) cube
+        cubes[i] = (ctx.cube_upload(v, dt, brick=B), dims, v if dt == "f32" else oracle.dequantize(v, dt))
     yield vrc, ctx, cubes
     ctx.close()
 
@@ -49,6 +51,40 @@ def submit(ctx, r, out):
     return ctx.submit(r["kind"], r["cid"], cam=r["cam"], rc=r["rc"], tf=r["tf"], nbins=r["nbins"], out=out)
 
 
+def check_against_oracle(ctx, cubes, r, out, res):
+    """A served result against the FP64 oracle on the stored cube: statistics
+    (min/max and every count exact, mean/std 1e-9), nearest MIP bit-exact,
+    trilinear MIP 1e-5 relative, DVR 1e-4 per channel (termination-fragile
+    pixels inside the oracle's bracket)."""
+    cid, dims, v = next(c for c in cubes.values() if c[0] == r["cid"])
+    info = ctx.cube_info(cid)
+    if r["kind"] == "stats":
+        ref = oracle.stats(v)
+        got = res["stats"]
+        assert got["min"] == ref["min"] and got["max"] == ref["max"] and got["n"] == ref["n"]
+        assert abs(got["mean"] - ref["mean"]) <= 1e-9 * max(abs(ref["mean"]), ref["std"])
+        assert abs(got["std"] - ref["std"]) <= 1e-9 * ref["std"]
+        h = out.cpu().numpy().astype(np.uint64)
+        assert np.array_equal(h, oracle.histogram(v, ref["min"], ref["max"], r["nbins"]))
+        return 0.0
+    rc = r["rc"]
+    sampling = "nearest" if rc.sampling == 0 else "trilinear"
+    ref = oracle.render(v, r["cam"], rc.width, rc.height, rc.step, sampling, r["kind"], tf=r["tf"],
+                        vmin=info["vmin"], vmax=info["vmax"])
+    got = out.cpu().numpy().astype(np.float64)
+    if r["kind"] == "mip":
+        if sampling == "nearest":
+            assert np.array_equal(got, ref["out"])
+        else:
+            assert np.all(np.abs(got - ref["out"]) <= 1e-5 * np.maximum(np.abs(ref["out"]), 1.0))
+        return 0.0
+    got = got.reshape(-1, 4)
+    d = np.abs(got - ref["out"]).max(axis=1)
+    inside = np.all((got >= ref["lo"] - 1e-4) & (got <= ref["hi"] + 1e-4), axis=1)
+    assert np.all((d <= 1e-4) | (ref["fragile"] & inside))
+    return float(ref["fragile"].mean())
+
+
 def test_alone_equals_mixed(setup):
     vrc, ctx, cubes = setup
     reqs = make_requests(vrc, cubes)
@@ -61,6 +97,7 @@ def test_alone_equals_mixed(setup):
     outs = [out_for(r) for r in reqs]
     tickets = [submit(ctx, r, o) for r, o in zip(reqs, outs)]
     results = [ctx.poll(t, -1) for t in tickets]
+    fragile = []
     for r, o, res, (ao, ares) in zip(reqs, outs, results, alone):
         assert res["status"] == 0
         assert torch.equal(o.cpu(), ao), r["kind"]
@@ -69,6 +106,36 @@ def test_alone_equals_mixed(setup):
         else:
             assert res["samples"] == ares["samples"] and res["samples"] > 0
         assert res["latency_ms"] >= res["queue_ms"] >= 0
+        fragile.append(check_against_oracle(ctx, cubes, r, o, res))
+    assert max(fragile) < 0.05, fragile
+
+
+def test_short_request_overtakes_long_render(setup):
+    """Continuous batching, not a queue: a short request that arrives while a
+    long render is on the GPU is admitted at once and completes first (large
+    render batches run in slices; statistics and small renders take a stream of
+    higher priority, so they get SMs at the next slice boundary)."""
+    import time
+    vrc, ctx, cubes = setup
+    cid, dims, v = cubes[2]
+    cam = cubegen.orbit_cameras(dims, 1)[0]
+    long_out = torch.zeros(2048 * 2048 * 4, device="cuda")
+    rc = vrc.raycfg(2048, 2048, 0.005)                 # hundreds of ms of work, no early termination
+    t_long = ctx.submit("dvr", cid, cam=cam, rc=rc, tf=cubegen.tf_sparse(), term_alpha=2.0, out=long_out)
+    time.sleep(0.05)                                    # the long render is on the GPU
+    assert ctx.poll(t_long, 0) is None
+    hist = torch.zeros(64, dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    t_short = ctx.submit("stats", cid, nbins=64, out=hist)
+    short = ctx.poll(t_short, -1)
+    short_ms = 1e3 * (time.perf_counter() - t0)
+    still_running = ctx.poll(t_long, 0) is None         # the long render has not finished yet
+    long = ctx.poll(t_long, -1)
+    assert short["status"] == 0 and long["status"] == 0
+    assert still_running, (short, long)
+    assert short["queue_ms"] < 5.0, short               # admitted at once, not queued behind the render
+    assert short_ms < long["latency_ms"]
+    check_against_oracle(ctx, cubes, dict(kind="stats", cid=cid, nbins=64), hist, short)
 
 
 def test_serving_matches_direct_api(setup):
