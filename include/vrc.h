@@ -184,6 +184,38 @@ vrc_status vrc_memory(vrc_ctx *ctx, int64_t *used_bytes, int64_t *budget_bytes);
 vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device, int64_t nx, int64_t ny,
                            int64_t nz, int32_t storage, int32_t brick, void *stream, int64_t *cube_id);
 
+/* Render-copy flags, OR-ed into the storage argument of vrc_cube_upload and
+ * vrc_cube_register.  AUTO: make the copy when it fits the budget with 2 GiB
+ * to spare, else render through global loads (vrc_last_render_path tells);
+ * REQUIRED: fail with VRC_E_NOMEM instead; NONE: no copy (the global-load
+ * path, half the resident memory of the default). */
+#define VRC_COPY_AUTO     0x000
+#define VRC_COPY_REQUIRED 0x100
+#define VRC_COPY_NONE     0x200
+#define VRC_COPY_MASK     0x300
+
+/*
+ * Register a cube without making it resident (Abstract, Sec. 3: a shared,
+ * multi-user service holds many users' cubes; on one GPU it keeps as many
+ * resident as its HBM budget allows).  src: caller-owned HOST array of
+ * nx*ny*nz floats, x fastest, that must stay valid and unchanged until
+ * vrc_cube_free.  storage and brick as for vrc_cube_upload (the render copy is
+ * made unless VRC_COPY_NONE is given).  No device memory is used until the cube
+ * is needed.  The serving loop admits a request for a registered cube once the
+ * cube is resident: it uploads it (the vrc_cube_upload passes, on a loader
+ * thread) as soon as the memory the upload needs fits the budget, evicting
+ * registered cubes that no queued or running request references, least
+ * recently used first; until then the request waits in the queue
+ * (vrc_result.memory_wait_ms).  A direct call (render, statistics, median,
+ * brick read) on a registered cube makes it resident first, on the calling
+ * thread.  Errors: VRC_E_INVAL.
+ */
+vrc_status vrc_cube_register(vrc_ctx *ctx, const float *src, int64_t nx, int64_t ny, int64_t nz, int32_t storage,
+                             int32_t brick, int64_t *cube_id);
+
+/* Registered cubes currently resident, uploads and evictions so far. */
+vrc_status vrc_residency(vrc_ctx *ctx, int64_t *resident, uint64_t *loads, uint64_t *evictions);
+
 /*
  * Out-of-core cube (Sec. 2: larger-than-memory cubes; streams overlap I/O):
  * bricks live in pinned host memory and are streamed to the device on side
@@ -324,8 +356,9 @@ vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vr
  * latency-bound interactive or serving loop, where cudaMalloc/cudaFree may
  * stall the whole device, or a plug-in inside an application that keeps the
  * device memory in its own pool).  Same inputs, outputs and errors as
- * vrc_cube_stats_async, for resident cubes (out-of-core cubes stream through
- * their device ring: VRC_E_UNSUPPORTED here); the pass's block partials go to one static device
+ * vrc_cube_stats_async, for resident cubes (VRC_E_UNSUPPORTED for out-of-core
+ * cubes, which stream through their device ring, and for registered cubes that
+ * are not resident at the time); the pass's block partials go to one static device
  * array of 64 KiB that the library holds on every device that loads it, so
  * the call performs no cudaMalloc, cudaFree or other allocation.  Devices whose
  * statistics pass needs more scratch than that are refused with VRC_E_NOMEM.
@@ -405,6 +438,16 @@ vrc_status vrc_render_dvr(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams,
 vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *evaluated);
 
 /*
+ * Path the most recent vrc_render_mip / vrc_render_dvr call on this context
+ * took: VRC_PATH_FUSED (texture gathers from the render copy), VRC_PATH_FUSED_LDG
+ * (global loads: requested, nearest sampling, or the cube has no render copy),
+ * VRC_PATH_SORTLAST, VRC_PATH_STREAMED (out-of-core: bricks copied through the
+ * device ring), VRC_PATH_ZEROCOPY or VRC_PATH_SLAB.  *path is HOST memory.
+ */
+#define VRC_PATH_STREAMED  5   /* reported only: sort-last with brick streaming */
+vrc_status vrc_last_render_path(vrc_ctx *ctx, int32_t *path);
+
+/*
  * Bricks of the most recent sort-last render on this context (Sec. 2: each
  * brick is rendered on its own into a partial image): *traversed = distinct
  * bricks that some view's rays cross and that were rendered (for a streamed
@@ -481,11 +524,14 @@ typedef struct {
 
 typedef struct {
     vrc_status status;     /* VRC_OK or the request's error */
-    int32_t reserved;
+    int32_t path;          /* render: VRC_PATH_FUSED (texture gathers) or VRC_PATH_FUSED_LDG (global loads) */
     vrc_stats stats;       /* stats requests */
     double queue_ms;       /* submit -> launch */
     double latency_ms;     /* submit -> completion observed */
     uint64_t samples;      /* render: ray samples taken */
+    double memory_wait_ms; /* part of queue_ms spent waiting for the cube to become resident */
+    int32_t cube_loaded;   /* 1 if the cube was uploaded for this request (registered cubes) */
+    int32_t reserved;
 } vrc_result;
 
 /*

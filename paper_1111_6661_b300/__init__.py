@@ -14,7 +14,7 @@ import ctypes
 import numpy as np
 
 from . import _vrc
-from ._vrc import DTYPES, INJECT, PATHS, SAMPLING
+from ._vrc import COPY, DTYPES, INJECT, PATH_NAMES, PATHS, SAMPLING
 
 __all__ = ["VrcError", "Context", "raycfg", "camera_struct", "lib"]
 
@@ -106,8 +106,10 @@ class Context:
         self._check(self._lib.vrc_debug_inject(self.h, INJECT[what], nth))
 
     # ------------------------------------------------------------ cubes
-    def cube_upload(self, src, storage: str = "f32", brick: int = 0, stream=None) -> int:
-        """src: float32 array (sz, sy, sx) -- numpy (host) or torch tensor (host or cuda)."""
+    def cube_upload(self, src, storage: str = "f32", brick: int = 0, stream=None, render_copy: str = "auto") -> int:
+        """src: float32 array (sz, sy, sx) -- numpy (host) or torch tensor (host or cuda).
+        render_copy: "auto" (made when it fits), "required" (VRC_E_NOMEM when it
+        does not fit) or "none"."""
         import torch
         if isinstance(src, np.ndarray):
             assert src.dtype == np.float32 and src.flags.c_contiguous and src.ndim == 3
@@ -117,8 +119,29 @@ class Context:
             ptr, on_dev, shape = src.data_ptr(), int(src.is_cuda), tuple(src.shape)
         cid = ctypes.c_int64()
         self._check(self._lib.vrc_cube_upload(self.h, ctypes.c_void_p(ptr), on_dev, shape[2], shape[1], shape[0],
-                                              DTYPES[storage], brick, _stream_ptr(stream), ctypes.byref(cid)))
+                                              DTYPES[storage] | COPY[render_copy], brick, _stream_ptr(stream),
+                                              ctypes.byref(cid)))
         return cid.value
+
+    def cube_register(self, src: np.ndarray, storage: str = "f32", brick: int = 0, render_copy: str = "auto") -> int:
+        """Register a host cube (float32 numpy array (sz, sy, sx)) that the
+        library makes resident only while it is needed; the array is kept
+        referenced until cube_free."""
+        assert isinstance(src, np.ndarray) and src.dtype == np.float32 and src.flags.c_contiguous and src.ndim == 3
+        cid = ctypes.c_int64()
+        self._check(self._lib.vrc_cube_register(self.h, ctypes.c_void_p(src.ctypes.data), src.shape[2], src.shape[1],
+                                                src.shape[0], DTYPES[storage] | COPY[render_copy], brick,
+                                                ctypes.byref(cid)))
+        if not hasattr(self, "_sources"):
+            self._sources = {}
+        self._sources[cid.value] = src
+        return cid.value
+
+    def residency(self) -> dict:
+        """Registered cubes resident now, uploads and evictions so far."""
+        r, l, e = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._lib.vrc_residency(self.h, ctypes.byref(r), ctypes.byref(l), ctypes.byref(e)))
+        return dict(resident=r.value, loads=l.value, evictions=e.value)
 
     def cube_create_streamed(self, dims, brick: int, n_host_bricks: int, ring_bricks: int = 0) -> int:
         cid = ctypes.c_int64()
@@ -162,6 +185,7 @@ class Context:
 
     def cube_free(self, cube_id: int):
         self._check(self._lib.vrc_cube_free(self.h, cube_id))
+        getattr(self, "_sources", {}).pop(cube_id, None)
 
     def cube_free_async(self, cube_id: int, stream=None):
         """Release once the work issued on `stream` so far has completed."""
@@ -243,6 +267,13 @@ class Context:
         self._check(self._lib.vrc_last_render_samples(self.h, ctypes.byref(n), ctypes.byref(e)))
         return (n.value, e.value) if evaluated else n.value
 
+    def last_render_path(self) -> str:
+        """Path the last render took: fused (texture gathers), fused_ldg (global
+        loads), sortlast, streamed, zerocopy or slab."""
+        p = ctypes.c_int32()
+        self._check(self._lib.vrc_last_render_path(self.h, ctypes.byref(p)))
+        return PATH_NAMES[p.value]
+
     def last_render_bricks(self):
         """(traversed, culled) distinct bricks of the last sort-last render."""
         t, c = ctypes.c_int64(), ctypes.c_int64()
@@ -318,4 +349,6 @@ class Context:
         self._check(st)
         s = res.stats
         return dict(status=res.status, queue_ms=res.queue_ms, latency_ms=res.latency_ms, samples=res.samples,
+                    path=PATH_NAMES.get(res.path, res.path), memory_wait_ms=res.memory_wait_ms,
+                    cube_loaded=bool(res.cube_loaded),
                     stats=dict(min=s.min, max=s.max, mean=s.mean, std=s.std, n=s.n, n_nonfinite=s.n_nonfinite))

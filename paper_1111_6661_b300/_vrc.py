@@ -17,6 +17,8 @@ STATUS = {0: "VRC_OK", 1: "VRC_PENDING", -1: "VRC_E_INVAL", -2: "VRC_E_NOMEM", -
 DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
 SAMPLING = {"nearest": 0, "trilinear": 1}
 PATHS = {"fused": 0, "sortlast": 1, "fused_ldg": 2, "zerocopy": 3, "slab": 4}
+PATH_NAMES = {0: "fused", 1: "sortlast", 2: "fused_ldg", 3: "zerocopy", 4: "slab", 5: "streamed"}
+COPY = {"auto": 0x000, "required": 0x100, "none": 0x200}
 INJECT = {"none": 0, "alloc": 1, "h2d": 2, "drop": 3, "slab_wait": 4}
 
 
@@ -52,8 +54,9 @@ class vrc_request(ctypes.Structure):
 
 
 class vrc_result(ctypes.Structure):
-    _fields_ = [("status", c_i32), ("reserved", c_i32), ("stats", vrc_stats), ("queue_ms", c_f64),
-                ("latency_ms", c_f64), ("samples", c_u64)]
+    _fields_ = [("status", c_i32), ("path", c_i32), ("stats", vrc_stats), ("queue_ms", c_f64),
+                ("latency_ms", c_f64), ("samples", c_u64), ("memory_wait_ms", c_f64), ("cube_loaded", c_i32),
+                ("reserved", c_i32)]
 
 
 # vrc_brick_source_fn: int32 (*)(void *user, int64 brick, int32 bx, int32 by, int32 bz, float *dst)
@@ -67,6 +70,9 @@ PROTOTYPES = {
     "vrc_last_error": (ctypes.c_char_p, [c_p]),
     "vrc_memory": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "vrc_cube_upload": (c_i32, [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i32, c_i32, c_p, ctypes.POINTER(c_i64)]),
+    "vrc_cube_register": (c_i32, [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, ctypes.POINTER(c_i64)]),
+    "vrc_residency": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)]),
+    "vrc_last_render_path": (c_i32, [c_p, ctypes.POINTER(c_i32)]),
     "vrc_cube_create_streamed": (c_i32, [c_p, c_i64, c_i64, c_i64, c_i32, c_i64, c_i32, ctypes.POINTER(c_i64)]),
     "vrc_cube_put_brick": (c_i32, [c_p, c_i64, c_i64, c_p]),
     "vrc_cube_upload_streamed": (c_i32, [c_p, c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i64, c_i32,

@@ -373,6 +373,7 @@ const char *vrc_status_str(vrc_status s)
     case VRC_E_NONFINITE: return "no finite values";
     case VRC_E_INJECTED: return "injected failure";
     case VRC_E_UNSUPPORTED: return "unsupported";
+    case VRC_E_SOURCE: return "brick provider failed";
     default: return "unknown status";
     }
 }

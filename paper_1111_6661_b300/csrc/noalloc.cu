@@ -57,9 +57,20 @@ extern "C" vrc_status vrc_cube_stats_noalloc(vrc_ctx *ctx, int64_t cube_id, int3
     if (!ctx) return VRC_E_INVAL;
     if (nbins < 0 || nbins > 65536) return set_err(ctx, VRC_E_INVAL, "nbins must be in [0, 65536]");
     if (!dev_out || (nbins > 0 && !dev_hist)) return set_err(ctx, VRC_E_INVAL, "null output");
-    Cube *c = find_cube(ctx, cube_id);
-    if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    Cube *c = nullptr;
+    CubeUse use;   // held for the call: a registered cube is not evicted meanwhile
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->cubes.find(cube_id);
+        if (it == ctx->cubes.end()) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+        c = it->second;
+        c->refs.fetch_add(1);
+    }
+    use.c = c;
     if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "statistics need a resident cube");
+    // making a registered cube resident would allocate
+    if (c->managed && c->state.load() != CUBE_RESIDENT)
+        return set_err(ctx, VRC_E_UNSUPPORTED, "registered cube %lld is not resident", (long long)cube_id);
     const size_t need = stats_scratch_bytes(ctx);
     if (need > kNoAllocScratchBytes)
         return set_err(ctx, VRC_E_NOMEM, "the statistics pass needs %zu bytes of scratch on this device; the static "

@@ -5,6 +5,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -604,8 +605,9 @@ vrc_status alloc_textures(vrc_ctx *ctx, Cube *c)
     const int64_t tex_layers = g.dtype == VRC_F32 ? g.R : g.R - 1;
     const int64_t arr_bytes = tex_esize * (int64_t)g.R * g.R * tex_layers;
     const int64_t per_copy = arr_bytes * g.nbricks + (1 << 20);
-    // leave room in the budget for the render scratch of a large multi-view call
-    const int64_t reserve = (int64_t)2 << 30;
+    // optional copies leave room in the budget for the render scratch of a
+    // large multi-view call; a required copy is charged as it is
+    const int64_t reserve = c->copy_mode == VRC_COPY_REQUIRED ? 0 : (int64_t)2 << 30;
     if (ctx->used.load() + per_copy + reserve > ctx->budget &&
         !(reap_pending(ctx, true) && ctx->used.load() + per_copy + reserve <= ctx->budget))
         return set_err(ctx, VRC_E_NOMEM, "budget: no room for texture copies");
@@ -672,7 +674,9 @@ vrc_status launch_textures(vrc_ctx *ctx, Cube *c, cudaStream_t st)
 
 }  // namespace
 
-void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
+// Give back every device allocation of a cube (bricks, metadata, render copy,
+// halo copy, ring) and clear the pointers; the record itself stays.
+void release_device(vrc_ctx *ctx, Cube *c, bool sync)
 {
     const BrickGeom &g = c->g;
     // the memory goes back to the context's cache and may be handed out at
@@ -689,6 +693,15 @@ void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
     if (c->bmax) dev_free(ctx, c->bmax, g.nbricks * 4);
     if (c->bnonfinite) dev_free(ctx, c->bnonfinite, g.nbricks * 4);
     if (c->bhalo) dev_free(ctx, c->bhalo, g.nbricks * 4);
+    c->pool = c->ring_pool = nullptr;
+    c->scales = c->cellmax = c->bmin = c->bmax = c->bhalo = nullptr;
+    c->bnonfinite = nullptr;
+    c->h_tex.clear();
+}
+
+void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
+{
+    release_device(ctx, c, sync);
     if (c->host_pool) cudaFreeHost(c->host_pool);
     for (cudaEvent_t e : c->slot_ev)
         if (e) cudaEventDestroy(e);
@@ -807,22 +820,15 @@ vrc_status call_source(vrc_ctx *ctx, Cube *c, int64_t b)
 
 }  // namespace
 
-extern "C" {
-
-vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device, int64_t nx, int64_t ny,
-                           int64_t nz, int32_t storage, int32_t brick, void *stream, int64_t *cube_id)
+// Make cube c (geometry and render-copy mode set) resident from `src`: the
+// upload passes of vrc_cube_upload on `st`.  On failure every device
+// allocation of c is given back.
+vrc_status upload_cube(vrc_ctx *ctx, Cube *c, const float *src, int32_t src_on_device, cudaStream_t st)
 {
-    if (!ctx || !src || !cube_id) return VRC_E_INVAL;
-    if (src_on_device != 0 && src_on_device != 1) return set_err(ctx, VRC_E_INVAL, "src_on_device must be 0 or 1");
-    BrickGeom g;
-    if (!make_geom(nx, ny, nz, brick, storage, &g, 32))
-        return set_err(ctx, VRC_E_INVAL, "bad dims/storage/brick (%lld %lld %lld, %d, %d)", (long long)nx,
-                       (long long)ny, (long long)nz, storage, brick);
+    const BrickGeom &g = c->g;
+    const int32_t storage = g.dtype;
+    const int64_t nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
     VRC_CK(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t st = (cudaStream_t)stream;
-    Cube *c = new (std::nothrow) Cube();
-    if (!c) return VRC_E_NOMEM;
-    c->g = g;
     // 1. every allocation first (host work that overlaps earlier device work)
     vrc_status s = dev_alloc(ctx, &c->pool, g.nbricks * g.brick_bytes);
     if (s == VRC_OK) s = alloc_meta(ctx, c);
@@ -838,8 +844,11 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
     if (s == VRC_OK) s = dev_alloc(ctx, (void **)&part, part_bytes);
     double *dbsum = part ? reinterpret_cast<double *>(part + g.nbricks * split) : nullptr;
     bool tex = false;
-    if (s == VRC_OK && getenv("VRC_NO_TEXTURES") == nullptr) {
-        // texture copies are an accelerator: without room for them the cube still renders
+    if (s == VRC_OK && c->copy_mode == VRC_COPY_REQUIRED) {
+        tex = (s = alloc_textures(ctx, c)) == VRC_OK;
+    } else if (s == VRC_OK && c->copy_mode == VRC_COPY_AUTO && getenv("VRC_NO_TEXTURES") == nullptr) {
+        // texture copies are an accelerator: without room for them the cube still
+        // renders (vrc_last_render_path then reports the global-load path)
         tex = alloc_textures(ctx, c) == VRC_OK;
         if (!tex) {
             release_textures(ctx, c);
@@ -882,10 +891,61 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
     if (part) dev_free(ctx, part, part_bytes);
     if (staging) dev_free(ctx, staging, src_bytes);
     if (s != VRC_OK) {
-        release_cube(ctx, c, true);
+        release_device(ctx, c, true);
         return s;
     }
     c->charged = g.nbricks * g.brick_bytes + 16 * g.nbricks;
+    return VRC_OK;
+}
+
+extern "C" {
+
+vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device, int64_t nx, int64_t ny,
+                           int64_t nz, int32_t storage, int32_t brick, void *stream, int64_t *cube_id)
+{
+    if (!ctx || !src || !cube_id) return VRC_E_INVAL;
+    if (src_on_device != 0 && src_on_device != 1) return set_err(ctx, VRC_E_INVAL, "src_on_device must be 0 or 1");
+    const int32_t copy_mode = storage & VRC_COPY_MASK;
+    if (copy_mode != VRC_COPY_AUTO && copy_mode != VRC_COPY_REQUIRED && copy_mode != VRC_COPY_NONE)
+        return set_err(ctx, VRC_E_INVAL, "bad render-copy flags %d", copy_mode);
+    BrickGeom g;
+    if (!make_geom(nx, ny, nz, brick, storage & ~VRC_COPY_MASK, &g, 32))
+        return set_err(ctx, VRC_E_INVAL, "bad dims/storage/brick (%lld %lld %lld, %d, %d)", (long long)nx,
+                       (long long)ny, (long long)nz, storage, brick);
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    Cube *c = new (std::nothrow) Cube();
+    if (!c) return VRC_E_NOMEM;
+    c->g = g;
+    c->copy_mode = copy_mode;
+    const vrc_status s = upload_cube(ctx, c, src, src_on_device, (cudaStream_t)stream);
+    if (s != VRC_OK) {
+        delete c;
+        return s;
+    }
+    *cube_id = register_cube(ctx, c);
+    return VRC_OK;
+}
+
+vrc_status vrc_cube_register(vrc_ctx *ctx, const float *src, int64_t nx, int64_t ny, int64_t nz, int32_t storage,
+                             int32_t brick, int64_t *cube_id)
+{
+    if (!ctx || !src || !cube_id) return VRC_E_INVAL;
+    const int32_t copy_mode = storage & VRC_COPY_MASK;
+    if (copy_mode != VRC_COPY_AUTO && copy_mode != VRC_COPY_REQUIRED && copy_mode != VRC_COPY_NONE)
+        return set_err(ctx, VRC_E_INVAL, "bad render-copy flags %d", copy_mode);
+    BrickGeom g;
+    if (!make_geom(nx, ny, nz, brick, storage & ~VRC_COPY_MASK, &g, 32))
+        return set_err(ctx, VRC_E_INVAL, "bad dims/storage/brick (%lld %lld %lld, %d, %d)", (long long)nx,
+                       (long long)ny, (long long)nz, storage, brick);
+    Cube *c = new (std::nothrow) Cube();
+    if (!c) return VRC_E_NOMEM;
+    c->g = g;
+    // a registered cube keeps its render copy whenever it is resident: the
+    // memory it needs is counted when the cube is admitted
+    c->copy_mode = copy_mode == VRC_COPY_NONE ? VRC_COPY_NONE : VRC_COPY_REQUIRED;
+    c->managed = true;
+    c->host_src = src;
+    c->state.store(CUBE_ABSENT);
     *cube_id = register_cube(ctx, c);
     return VRC_OK;
 }
@@ -1010,8 +1070,10 @@ vrc_status vrc_cube_read_brick(vrc_ctx *ctx, int64_t cube_id, int64_t brick, voi
 {
     if (!ctx) return VRC_E_INVAL;
     if (!dst) return set_err(ctx, VRC_E_INVAL, "dst is NULL");
-    Cube *c = find_cube(ctx, cube_id);
-    if (!c) return VRC_E_BADID;
+    Cube *c = nullptr;
+    CubeUse use;
+    vrc_status s = acquire_cube(ctx, cube_id, nullptr, &c, use);
+    if (s != VRC_OK) return s;
     if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "streamed cube: bricks live in host slots");
     const BrickGeom &g = c->g;
     if (brick < 0 || brick >= g.nbricks) return set_err(ctx, VRC_E_INVAL, "brick %lld out of range", (long long)brick);
@@ -1033,7 +1095,8 @@ vrc_status vrc_cube_free(vrc_ctx *ctx, int64_t cube_id)
         std::lock_guard<std::mutex> lk(ctx->mu);
         auto it = ctx->cubes.find(cube_id);
         if (it == ctx->cubes.end()) return VRC_E_BADID;
-        if (it->second->refs.load() > 0) return set_err(ctx, VRC_E_BUSY, "cube referenced by serving requests");
+        if (it->second->refs.load() > 0 || it->second->state.load() == CUBE_LOADING)
+            return set_err(ctx, VRC_E_BUSY, "cube referenced by serving requests or being uploaded");
         c = it->second;
         ctx->cubes.erase(it);
     }
@@ -1052,7 +1115,7 @@ vrc_status vrc_cube_free_async(vrc_ctx *ctx, int64_t cube_id, void *stream)
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         auto it = ctx->cubes.find(cube_id);
-        if (it == ctx->cubes.end() || it->second->refs.load() > 0) {
+        if (it == ctx->cubes.end() || it->second->refs.load() > 0 || it->second->state.load() == CUBE_LOADING) {
             const bool busy = it != ctx->cubes.end();
             cudaEventDestroy(ev);
             return busy ? set_err(ctx, VRC_E_BUSY, "cube referenced by serving requests") : VRC_E_BADID;
@@ -1149,5 +1212,117 @@ vrc_status ring_load(vrc_ctx *ctx, Cube *c, int64_t b0, int64_t n, int first, cu
     }
     const cudaError_t e = cudaEventRecord(done, cs);
     if (e != cudaSuccess) return cuda_err(ctx, e, "ring event");
+    return VRC_OK;
+}
+
+// ------------------------------------------------------------ residency
+
+double host_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int64_t upload_peak_bytes(const Cube *c)
+{
+    const BrickGeom &g = c->g;
+    const int64_t slack = (int64_t)2 << 20;   // block rounding, per allocation
+    const int64_t cells = (int64_t)g.nb[0] * g.nb[1] * g.nb[2] * (g.B / 8) * (g.B / 8) * (g.B / 8);
+    int64_t n = g.nbricks * g.brick_bytes + slack;                 // bricks
+    n += 5 * (g.nbricks * 4 + slack);                              // per-brick metadata
+    n += cells * 4 + slack;                                        // macro-cell maxima
+    n += g.dims[0] * g.dims[1] * g.dims[2] * 4 + slack;            // staging of the source
+    n += g.nbricks * 4096 + slack;                                 // scan partials
+    if (c->copy_mode != VRC_COPY_NONE) {
+        const int64_t tex_esize = g.dtype == VRC_F32 ? 4 : 2 * g.esize;
+        const int64_t layers = g.dtype == VRC_F32 ? g.R : g.R - 1;
+        n += tex_esize * (int64_t)g.R * g.R * layers * g.nbricks + (1 << 20);   // render copy
+        n += 4 * g.nbricks * 8 + slack;                                          // handle table
+    }
+    return n;
+}
+
+bool evict_for(vrc_ctx *ctx, int64_t need, const Cube *keep)
+{
+    auto fits = [&] { return ctx->used.load() + ctx->reserved + need <= ctx->budget; };
+    if (fits()) return true;
+    std::vector<Cube *> idle;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto &kv : ctx->cubes) {
+            Cube *c = kv.second;
+            if (c != keep && c->managed && c->state.load() == CUBE_RESIDENT && c->refs.load() == 0) idle.push_back(c);
+        }
+    }
+    std::sort(idle.begin(), idle.end(), [](const Cube *a, const Cube *b) { return a->last_use < b->last_use; });
+    for (Cube *c : idle) {
+        if (fits()) break;
+        if (c->refs.load() != 0) continue;
+        c->state.store(CUBE_ABSENT);
+        // requests that used it have completed; work of direct calls may still run
+        release_device(ctx, c, c->direct_used);
+        c->direct_used = false;
+        ctx->evictions.fetch_add(1);
+    }
+    if (!fits()) reap_pending(ctx, true);
+    return fits();
+}
+
+vrc_status acquire_cube(vrc_ctx *ctx, int64_t id, cudaStream_t st, Cube **out, CubeUse &use)
+{
+    Cube *c = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->cubes.find(id);
+        if (it == ctx->cubes.end()) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)id);
+        c = it->second;
+        c->refs.fetch_add(1);   // held until the call returns: never evicted or freed meanwhile
+    }
+    use.c = c;
+    if (c->managed) {
+        for (;;) {
+            std::unique_lock<std::mutex> lk(ctx->res_mu);
+            const int state = c->state.load();
+            if (state == CUBE_RESIDENT) break;
+            if (state == CUBE_LOADING) {   // the serving loader is uploading it
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(200));
+                continue;
+            }
+            if (!evict_for(ctx, upload_peak_bytes(c), c))
+                return set_err(ctx, VRC_E_NOMEM, "budget: no room to make registered cube %lld resident",
+                               (long long)id);
+            c->state.store(CUBE_LOADING);
+            lk.unlock();
+            const vrc_status s = upload_cube(ctx, c, c->host_src, 0, st);
+            lk.lock();
+            c->state.store(s == VRC_OK ? CUBE_RESIDENT : CUBE_ABSENT);
+            if (s != VRC_OK) return s;
+            ++c->loads;
+            break;
+        }
+        c->last_use = host_ms();
+        c->direct_used = true;
+    }
+    *out = c;
+    return VRC_OK;
+}
+
+extern "C" vrc_status vrc_residency(vrc_ctx *ctx, int64_t *resident, uint64_t *loads, uint64_t *evictions)
+{
+    if (!ctx) return VRC_E_INVAL;
+    int64_t r = 0;
+    uint64_t l = 0;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto &kv : ctx->cubes)
+            if (kv.second->managed) {
+                r += kv.second->state.load() == CUBE_RESIDENT;
+                l += kv.second->loads;
+            }
+    }
+    if (resident) *resident = r;
+    if (loads) *loads = l;
+    if (evictions) *evictions = ctx->evictions.load();
     return VRC_OK;
 }

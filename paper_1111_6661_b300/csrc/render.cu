@@ -1083,7 +1083,8 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
 namespace {
 
 vrc_status validate_render(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg *rc,
-                           const float *tf, float term, float *out, int mode, Cube **cube)
+                           const float *tf, float term, float *out, int mode, Cube **cube, CubeUse &use,
+                           cudaStream_t st)
 {
     if (!ctx) return VRC_E_INVAL;
     if (!cams || !out || n_views < 1 || n_views > 4096) return set_err(ctx, VRC_E_INVAL, "bad cams/out/n_views");
@@ -1095,8 +1096,8 @@ vrc_status validate_render(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams
             if (!std::isfinite(tf[i])) return set_err(ctx, VRC_E_INVAL, "tf has non-finite entries");
     for (int v = 0; v < n_views; ++v)
         if (!valid_cam(cams[v])) return set_err(ctx, VRC_E_INVAL, "bad camera %d", v);
-    Cube *c = find_cube(ctx, cube_id);
-    if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    Cube *c = nullptr;
+    if ((s = acquire_cube(ctx, cube_id, st, &c, use)) != VRC_OK) return s;
     if ((s = validate_step(ctx, c, rc->step)) != VRC_OK) return s;
     *cube = c;
     return VRC_OK;
@@ -1111,7 +1112,8 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
                          unsigned long long *samples_out, bool host_sync_samples)
 {
     Cube *c = nullptr;
-    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term, out, mode, &c);
+    CubeUse use;
+    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term, out, mode, &c, use, st);
     if (s != VRC_OK) return s;
     VRC_CK(ctx, cudaSetDevice(ctx->device));
     int tw, th;
@@ -1136,6 +1138,14 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     }
     const bool zerocopy = rc->path == VRC_PATH_ZEROCOPY;
     const bool sortlast = c->streamed || rc->path == VRC_PATH_SORTLAST;
+    ctx->last_path = slab ? VRC_PATH_SLAB
+                          : (zerocopy ? VRC_PATH_ZEROCOPY
+                                      : (c->streamed ? VRC_PATH_STREAMED
+                                                     : (sortlast ? VRC_PATH_SORTLAST
+                                                                 : (rc->path == VRC_PATH_FUSED && c->dtex &&
+                                                                            rc->sampling == VRC_TRILINEAR
+                                                                        ? VRC_PATH_FUSED
+                                                                        : VRC_PATH_FUSED_LDG))));
     if (!sortlast && !c->pool) return set_err(ctx, VRC_E_UNSUPPORTED, "cube has no resident bricks");
     if (c->streamed && c->n_filled < c->n_host)
         return set_err(ctx, VRC_E_INVAL, "streamed cube: %lld of %lld host slots never written",
@@ -1370,6 +1380,13 @@ vrc_status vrc_render_dvr(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams,
                          false);
 }
 
+vrc_status vrc_last_render_path(vrc_ctx *ctx, int32_t *path)
+{
+    if (!ctx || !path) return VRC_E_INVAL;
+    *path = ctx->last_path.load();
+    return VRC_OK;
+}
+
 vrc_status vrc_composite(vrc_ctx *ctx, const float *front, const float *back, float *out, int64_t n_pixels, int32_t mode,
                          void *stream)
 {
@@ -1407,8 +1424,10 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     *graph = nullptr;
     const int mode = tf_rgba ? 1 : 0;
     Cube *c = nullptr;
-    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c);
+    CubeUse use;
+    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c, use, nullptr);
     if (s != VRC_OK) return s;
+    if (c->managed) return set_err(ctx, VRC_E_UNSUPPORTED, "graphs need a cube uploaded with vrc_cube_upload");
     if (c->streamed || rc->path == VRC_PATH_SORTLAST || rc->path == VRC_PATH_SLAB)
         return set_err(ctx, VRC_E_UNSUPPORTED, "graphs capture the fused path of resident cubes");
     const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
@@ -1496,7 +1515,9 @@ vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, i
 {
     const int mode = tf_rgba ? 1 : 0;
     Cube *c = nullptr;
-    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c);
+    CubeUse use;
+    vrc_status s = validate_render(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, mode, &c, use,
+                                   (cudaStream_t)stream);
     if (s != VRC_OK) return s;
     if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "autotuning needs a resident cube");
     VRC_CK(ctx, cudaSetDevice(ctx->device));

@@ -29,6 +29,9 @@ struct SReq {
     vrc_request r{};
     Cube *cube = nullptr;
     double t_submit = 0, t_launch = 0, t_done = 0;
+    double t_wait0 = 0, t_wait1 = 0;   // waiting for the cube to become resident (registered cubes)
+    bool loaded_for = false;           // this request triggered the cube's upload
+    int32_t path = 0;
     vrc_status status = VRC_OK;
     vrc_stats stats{};
     uint64_t samples = 0;
@@ -67,6 +70,14 @@ struct Server {
     // (the default pool returns it at every synchronisation, and mapping it
     // again stalls later allocations)
     cudaMemPool_t pool = nullptr;
+    // loader of registered cubes: uploads run on a thread of their own so that
+    // admission and completion go on meanwhile
+    std::thread loader;
+    std::deque<std::pair<Cube *, int64_t>> load_q;   // cube, bytes reserved for it
+    std::condition_variable cv_load;
+    bool loader_stop = false;                         // set once the serving loop has drained
+    cudaStream_t load_stream = nullptr;
+    std::map<Cube *, vrc_status> load_err;            // failed uploads, reported to the waiting requests
 };
 
 namespace {
@@ -142,6 +153,7 @@ bool launch_batch(Server *S, SBatch *B, bool render)
     if (render) {
         std::vector<HetJob> jobs;
         for (SReq *q : B->reqs) {
+            q->path = q->cube->dtex && q->r.rc.sampling == VRC_TRILINEAR ? VRC_PATH_FUSED : VRC_PATH_FUSED_LDG;
             HetJob j;
             j.cube = q->cube;
             j.cam = q->r.cam;
@@ -242,7 +254,7 @@ void serve_loop(Server *S)
         // admit: FIFO, up to max_inflight requests on the GPU
         const int room = ctx->cfg.max_inflight - S->inflight;
         if (room > 0 && !S->queue.empty()) {
-            std::vector<SReq *> take;
+            std::vector<SReq *> take, waiting;
             while (!S->queue.empty() && (int)take.size() < room) {
                 SReq *q = S->queue.front();
                 S->queue.pop_front();
@@ -251,8 +263,46 @@ void serve_loop(Server *S)
                     any_done = true;
                     continue;
                 }
+                if (q->cube->managed) {
+                    // registered cube: admitted once resident; its upload starts as
+                    // soon as the memory it needs fits the budget (idle cubes evicted)
+                    std::lock_guard<std::mutex> rl(ctx->res_mu);
+                    const int state = q->cube->state.load();
+                    if (state != CUBE_RESIDENT) {
+                        auto fe = S->load_err.find(q->cube);
+                        if (state == CUBE_ABSENT && fe != S->load_err.end()) {
+                            finish_req(S, q, fe->second);   // its upload failed
+                            any_done = true;
+                            continue;
+                        }
+                        if (q->t_wait0 == 0) q->t_wait0 = now_ms();
+                        if (state == CUBE_ABSENT) {
+                            const int64_t need = upload_peak_bytes(q->cube);
+                            if (need > ctx->budget) {
+                                finish_req(S, q, VRC_E_NOMEM);
+                                set_err(ctx, VRC_E_NOMEM, "registered cube needs %lld bytes, budget %lld",
+                                        (long long)need, (long long)ctx->budget);
+                                any_done = true;
+                                continue;
+                            }
+                            if (evict_for(ctx, need, q->cube)) {
+                                ctx->reserved += need;
+                                q->cube->state.store(CUBE_LOADING);
+                                q->loaded_for = true;
+                                S->load_q.push_back({q->cube, need});
+                                S->cv_load.notify_one();
+                            }
+                        }
+                        waiting.push_back(q);
+                        continue;
+                    }
+                    q->cube->last_use = now_ms();
+                    if (q->t_wait0 > 0 && q->t_wait1 == 0) q->t_wait1 = now_ms();
+                }
                 take.push_back(q);
             }
+            // requests whose cube is not resident yet keep their place in the queue
+            for (auto it = waiting.rbegin(); it != waiting.rend(); ++it) S->queue.push_front(*it);
             // group: one batch per (mode, sampling, dtype) of renders, one for statistics
             std::map<int, std::vector<SReq *>> groups;
             for (SReq *q : take) {
@@ -298,6 +348,39 @@ void serve_loop(Server *S)
         lk.unlock();
         std::this_thread::sleep_for(std::chrono::microseconds(50));
         lk.lock();
+    }
+}
+
+// Uploads registered cubes handed over by the admission step.
+void load_loop(Server *S)
+{
+    vrc_ctx *ctx = S->ctx;
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        S->cv_load.wait(lk, [&] { return S->loader_stop || !S->load_q.empty(); });
+        if (S->load_q.empty()) {
+            if (S->loader_stop) break;
+            continue;
+        }
+        auto job = S->load_q.front();
+        S->load_q.pop_front();
+        lk.unlock();
+        Cube *c = job.first;
+        const vrc_status st = upload_cube(ctx, c, c->host_src, 0, S->load_stream);
+        {
+            std::lock_guard<std::mutex> rl(ctx->res_mu);
+            ctx->reserved -= job.second;
+            if (st == VRC_OK) {
+                ++c->loads;
+                c->last_use = now_ms();
+            }
+            c->state.store(st == VRC_OK ? CUBE_RESIDENT : CUBE_ABSENT);
+        }
+        lk.lock();
+        if (st == VRC_OK) S->load_err.erase(c);
+        else S->load_err[c] = st;
+        S->cv_work.notify_all();
     }
 }
 
@@ -356,7 +439,12 @@ Server *server_get(vrc_ctx *ctx)
                 S->pinned_free.push_back({p, full});
             }
         }
+        if (cudaStreamCreateWithFlags(&S->load_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            S->load_stream = nullptr;
+        }
         S->th = std::thread(serve_loop, S);
+        S->loader = std::thread(load_loop, S);
         ctx->server = S;
     }
     return ctx->server;
@@ -378,7 +466,14 @@ void server_stop(vrc_ctx *ctx)
         S->stop = true;
     }
     S->cv_work.notify_all();
-    S->th.join();
+    S->th.join();   // every queued request finishes first (uploads included)
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->loader_stop = true;
+    }
+    S->cv_load.notify_all();
+    S->loader.join();
+    if (S->load_stream) cudaStreamDestroy(S->load_stream);
     for (auto &kv : S->tickets) delete kv.second;
     if (S->urgent) S->streams.push_back(S->urgent);
     for (cudaStream_t st : S->streams) cudaStreamSynchronize(st);
@@ -458,6 +553,9 @@ vrc_status vrc_poll(vrc_ctx *ctx, uint64_t ticket, vrc_result *res, int32_t time
     res->queue_ms = q->t_launch > 0 ? q->t_launch - q->t_submit : 0;
     res->latency_ms = q->t_done - q->t_submit;
     res->samples = q->samples;
+    res->path = q->path;
+    res->memory_wait_ms = q->t_wait0 > 0 ? (q->t_wait1 > 0 ? q->t_wait1 : q->t_done) - q->t_wait0 : 0.0;
+    res->cube_loaded = q->loaded_for ? 1 : 0;
     S->tickets.erase(it);
     delete q;
     return VRC_OK;

@@ -781,12 +781,14 @@ vrc_status stats_launch_with(vrc_ctx *ctx, Cube *c, int32_t nbins, vrc_stats *de
     return VRC_OK;
 }
 
-static vrc_status check_stats_args(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, Cube **out)
+static vrc_status check_stats_args(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, Cube **out, CubeUse &use,
+                                   void *stream)
 {
     if (!ctx) return VRC_E_INVAL;
     if (nbins < 0 || nbins > 65536) return set_err(ctx, VRC_E_INVAL, "nbins must be in [0, 65536]");
-    Cube *c = find_cube(ctx, cube_id);
-    if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    Cube *c = nullptr;
+    vrc_status s = acquire_cube(ctx, cube_id, (cudaStream_t)stream, &c, use);
+    if (s != VRC_OK) return s;
     if (c->streamed && c->n_filled < c->n_host)
         return set_err(ctx, VRC_E_INVAL, "streamed cube: %lld of %lld host slots never written",
                        (long long)(c->n_host - c->n_filled), (long long)c->n_host);
@@ -800,7 +802,8 @@ vrc_status vrc_cube_stats_async(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vr
                                 uint64_t *dev_hist, void *stream)
 {
     Cube *c = nullptr;
-    vrc_status s = check_stats_args(ctx, cube_id, nbins, &c);
+    CubeUse use;
+    vrc_status s = check_stats_args(ctx, cube_id, nbins, &c, use, stream);
     if (s != VRC_OK) return s;
     if (!dev_out || (nbins > 0 && !dev_hist)) return set_err(ctx, VRC_E_INVAL, "null output");
     VRC_CK(ctx, cudaSetDevice(ctx->device));
@@ -813,7 +816,8 @@ vrc_status vrc_cube_stats(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stat
                           void *stream)
 {
     Cube *c = nullptr;
-    vrc_status s = check_stats_args(ctx, cube_id, nbins, &c);
+    CubeUse use;
+    vrc_status s = check_stats_args(ctx, cube_id, nbins, &c, use, stream);
     if (s != VRC_OK) return s;
     if (!out || (nbins > 0 && !hist)) return set_err(ctx, VRC_E_INVAL, "null output");
     VRC_CK(ctx, cudaSetDevice(ctx->device));
@@ -835,7 +839,8 @@ vrc_status vrc_cube_stats(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, vrc_stat
 vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *stream)
 {
     Cube *c = nullptr;
-    vrc_status s = check_stats_args(ctx, cube_id, 0, &c);
+    CubeUse use;
+    vrc_status s = check_stats_args(ctx, cube_id, 0, &c, use, stream);
     if (s != VRC_OK) return s;
     if (!out) return VRC_E_INVAL;
     VRC_CK(ctx, cudaSetDevice(ctx->device));

@@ -109,8 +109,20 @@ struct Cube {
     alignas(64) unsigned char slab_maps[3 * 128];
     // tuning (0 = default)
     int32_t tile_w = 0, tile_h = 0, ctas_per_sm = 0;
-    std::atomic<int> refs{0};
+    std::atomic<int> refs{0};     // queued or running requests and direct calls using the cube
+    // render copy: VRC_COPY_AUTO, VRC_COPY_REQUIRED or VRC_COPY_NONE
+    int32_t copy_mode = 0;
+    // registered cubes (vrc_cube_register): voxels stay in the caller's host
+    // memory; the library makes the cube resident when it is needed and evicts
+    // it (least recently used, when no request or call holds it) to make room
+    bool managed = false;
+    const float *host_src = nullptr;
+    std::atomic<int> state{2};    // CUBE_ABSENT, CUBE_LOADING, CUBE_RESIDENT
+    double last_use = 0;          // host ms of the last admission or direct use
+    bool direct_used = false;     // work of direct calls may be in flight: evictions wait for the device
+    uint64_t loads = 0;           // uploads of this cube so far
 };
+constexpr int CUBE_ABSENT = 0, CUBE_LOADING = 1, CUBE_RESIDENT = 2;
 
 struct Server;  // serving loop (serve.cu)
 
@@ -152,6 +164,12 @@ struct vrc_ctx {
     // the event recorded on the caller's stream has completed
     std::mutex pend_mu;
     std::vector<std::pair<cudaEvent_t, Cube *>> pending;
+    // residency of registered cubes: state changes and evictions
+    std::mutex res_mu;
+    int64_t reserved = 0;         // bytes promised to uploads in progress (serving loader)
+    std::atomic<uint64_t> evictions{0};
+    // path of the most recent render (VRC_PATH_*)
+    std::atomic<int32_t> last_path{0};
     // pinned staging slots for small host-to-device inputs (stage_h2d)
     std::mutex stage_mu;
     struct PinnedSlot {
@@ -233,6 +251,34 @@ size_t render_hetero_scratch_bytes(const std::vector<HetJob> &jobs);
 size_t render_hetero_stage_bytes(size_t n_jobs);
 
 void server_stop(vrc_ctx *ctx);
+
+// Resident cubes (pack.cu).  upload_cube runs the upload passes into a cube
+// record whose geometry and render-copy mode are set; release_device gives
+// back its device memory (the record stays).
+vrc_status upload_cube(vrc_ctx *ctx, Cube *c, const float *src, int32_t src_on_device, cudaStream_t st);
+void release_device(vrc_ctx *ctx, Cube *c, bool sync);
+// Device bytes a registered cube needs while its upload runs (bricks,
+// metadata, render copy, staging of the source, scratch reserve).
+int64_t upload_peak_bytes(const Cube *c);
+// Evict idle registered cubes (no references, least recently used first)
+// until `need` more bytes fit the budget beside the reservations; true if
+// they fit.  Caller holds ctx->res_mu.
+bool evict_for(vrc_ctx *ctx, int64_t need, const Cube *keep);
+double host_ms();
+
+// A cube held by a direct call: it is not evicted while the call runs.
+struct CubeUse {
+    Cube *c = nullptr;
+    CubeUse() = default;
+    CubeUse(const CubeUse &) = delete;
+    ~CubeUse()
+    {
+        if (c) c->refs.fetch_sub(1);
+    }
+};
+// Look up a cube for a direct call, hold it, and make a registered cube
+// resident (uploading it on `st`, evicting idle registered cubes first).
+vrc_status acquire_cube(vrc_ctx *ctx, int64_t id, cudaStream_t st, Cube **out, CubeUse &use);
 
 // Out-of-core cubes (pack.cu).  host_brick makes host slot brick % n_host hold
 // brick `brick` (calling the provider when another brick is there, after the

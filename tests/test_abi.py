@@ -44,7 +44,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(_vrc.vrc_raycfg) == 40
     assert ctypes.sizeof(_vrc.vrc_tuning) == 32
     assert ctypes.sizeof(_vrc.vrc_request) == 4216
-    assert ctypes.sizeof(_vrc.vrc_result) == 80
+    assert ctypes.sizeof(_vrc.vrc_result) == 96
 
 
 def test_status_strings_and_no_device_error(lib):
