@@ -293,6 +293,7 @@ def run_gpu(args, w):
         step()
     torch.cuda.synchronize()
     samples_per_step = ctx.last_render_samples()
+    render_path = ctx.last_render_path()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -486,6 +487,18 @@ def run_gpu(args, w):
         cpu = {"value": rate, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{npix} random pixels of {nv} views ({nsamp} samples, {el:.1f} s), FP64 oracle, OpenMP"}
 
+    # precision forms: the same step with the cube stored as bf16 and fp8
+    precision = None
+    if not args.no_precision and w["storage"] == "f32":
+        fp32_row = {"step_samples_per_s": samples_per_step / ((render_ms + stats_ms) / 1e3),
+                    "samples_per_s": samples_per_step / (render_ms / 1e3), "render_ms": render_ms,
+                    "stats_ms": stats_ms, "view_latency": view_latency, "render_path": render_path}
+        precision = precision_forms(ctx, v, cams, tf, w, rc, out, args, fp32_row)
+    if cid is not None:
+        ctx.cube_free(cid)
+    ctx.close()   # the serving contexts below need the device memory this one caches
+    serving = serving_forms(args) if (not args.no_serving and rank == 0) else None
+
     # the committed captures are of the default step (fp32 cube, fused path, 32 views)
     profiled = w["name"] == "dvr1024" and w["storage"] == "f32" and args.path == "fused" and len(cams) == 32
     if rank == 0:
@@ -503,16 +516,143 @@ def run_gpu(args, w):
                              "flops_per_sample": DVR_FLOPS_PER_SAMPLE,
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
                              "binding": render_binding() if profiled else None},
-                "frames_per_s": len(cams) / (render_ms / 1e3), "skip_empty_variant": skip,
+                "frames_per_s": len(cams) / (render_ms / 1e3), "render_path": render_path,
+                "precision_forms": precision, "serving_forms": serving, "skip_empty_variant": skip,
                 "view_latency": view_latency, "mip_native": mip_native,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms, "median_ms": median_ms,
                             "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
                             "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_kind": pk_kind},
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    if cid is not None:
+
+
+# ------------------------------------------------- precision and serving forms
+# Stated error bounds of the precision forms: largest difference, per RGBA
+# channel, between a DVR pixel of the stored cube and the FP64 oracle on the
+# original fp32 cube (the error a user sees: storage rounding plus kernel
+# error).  The bound is one spacing of the storage format at 1.0 (the images'
+# channels lie in [0, 1]): 2^-7 for bf16 (7 stored mantissa bits), 2^-3 for
+# fp8 e4m3 (3 stored mantissa bits, per-brick scale).
+ERROR_BOUNDS = {"bf16": 2.0 ** -7, "fp8": 2.0 ** -3}
+
+
+def view_latency_ms(ctx, cid, cams, rc, tf, term, out, rounds=2):
+    import torch
+    st = torch.cuda.current_stream()
+    ms = []
+    ctx.render_dvr(cid, cams[:1], rc, tf, term, out=out[:1])
+    for _ in range(rounds):
+        for i, cam in enumerate(cams):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.render_dvr(cid, [cam], rc, tf, term, out=out[i:i + 1])
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    return {"p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)), "renders": len(ms)}
+
+
+def precision_forms(ctx, v, cams, tf, w, rc, out, args, fp32_row):
+    """The step of the default workload on the cube stored as bf16 and as fp8
+    e4m3 (per-brick scale): samples/s, one-view latency, and the error of
+    sampled DVR pixels against the FP64 oracle on the original fp32 cube and
+    on the stored cube."""
+    import torch
+
+    import oracle
+    rows = {"f32": fp32_row}
+    rng = np.random.default_rng(7)
+    npix = w["W"] * w["H"]
+    pix = rng.choice(npix, size=args.error_pixels, replace=False)
+    err_views = [0, len(cams) // 2]
+    dstats = torch.empty(8, dtype=torch.float64, device="cuda")
+    dhist = torch.empty(w["nbins"], dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream()
+    for dt in ("bf16", "fp8"):
+        cid = ctx.cube_upload(v, dt, brick=w["brick"])
+        info = ctx.cube_info(cid)
+        for _ in range(max(args.warmup, 1)):
+            ctx.cube_stats_async(cid, w["nbins"], dstats, dhist)
+            ctx.render_dvr(cid, cams, rc, tf, w["term"], out=out)
+        torch.cuda.synchronize()
+        samples = ctx.last_render_samples()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(st)
+        for _ in range(args.steps):
+            ctx.cube_stats_async(cid, w["nbins"], dstats, dhist)
+        e[1].record(st)
+        for _ in range(args.steps):
+            ctx.render_dvr(cid, cams, rc, tf, w["term"], out=out)
+        e[2].record(st)
+        torch.cuda.synchronize()
+        stats_ms = e[0].elapsed_time(e[1]) / args.steps
+        render_ms = e[1].elapsed_time(e[2]) / args.steps
+        path = ctx.last_render_path()
+        lat = view_latency_ms(ctx, cid, cams, rc, tf, w["term"], out)
+        ctx.render_dvr(cid, cams, rc, tf, w["term"], out=out)
+        torch.cuda.synchronize()
+        err32, errs, fragile = 0.0, 0.0, 0
+        for vi in err_views:
+            got = out[vi].reshape(-1, 4).cpu().numpy().astype(np.float64)[pix]
+            kw = dict(tf=tf, vmin=info["vmin"], vmax=info["vmax"], term=w["term"], pixels=pix)
+            r32 = oracle.render(v, cams[vi], w["W"], w["H"], w["step"], "trilinear", "dvr", **kw)
+            rst = oracle.render(v, cams[vi], w["W"], w["H"], w["step"], "trilinear", "dvr", dtype=dt,
+                                brick=w["brick"], **kw)
+            err32 = max(err32, float(np.abs(got - r32["out"]).max()))
+            d = np.abs(got - rst["out"]).max(axis=1)
+            ok = (d <= 1e-4) | (rst["fragile"] & np.all((got >= rst["lo"] - 1e-4) & (got <= rst["hi"] + 1e-4), axis=1))
+            errs = max(errs, float(d[~rst["fragile"]].max()) if (~rst["fragile"]).any() else 0.0)
+            fragile += int(rst["fragile"].sum())
+            assert ok.all(), (dt, vi)
+        rows[dt] = {"samples_per_s": samples / (render_ms / 1e3),
+                    "step_samples_per_s": samples / ((render_ms + stats_ms) / 1e3), "render_ms": render_ms,
+                    "stats_ms": stats_ms, "stored_bytes": info["bytes"], "render_copy_bytes": info["render_copy_bytes"],
+                    "render_path": path, "view_latency": lat,
+                    "dvr_max_abs_err_vs_fp32_oracle": err32, "dvr_max_abs_err_vs_stored_oracle": errs,
+                    "error_bound_vs_fp32_oracle": ERROR_BOUNDS[dt], "fragile_pixels": fragile,
+                    "error_sample": f"{len(pix)} random pixels of views {err_views}"}
+        rows[dt]["meets_error_bound"] = err32 <= ERROR_BOUNDS[dt]
+        rows[dt]["beats_fp32_samples_per_s"] = rows[dt]["step_samples_per_s"] > fp32_row["step_samples_per_s"]
+        rows[dt]["beats_fp32_view_p99"] = lat["p99_ms"] < fp32_row["view_latency"]["p99_ms"]
         ctx.cube_free(cid)
-    ctx.close()
+    return rows
+
+
+def serving_forms(args):
+    """cfg4 serving, bounded: the Poisson stream (200 requests/s) over 64 cubes
+    of 256^3-1024^3 (one generated volume per side) as a resident set, served
+    for a few seconds with every cube stored as fp32, bf16 and fp8 in turn."""
+    import torch
+
+    import cubegen
+    import paper_1111_6661_b300 as vrc
+    wl = cubegen.serving_stream(seed=5, rate_hz=200.0, duration_s=args.serving_seconds, n_cubes=64)
+    out = {}
+    vols = {}
+    for dt in ("f32", "bf16", "fp8"):
+        for c in wl["cubes"]:
+            c["dtype"] = dt
+        ctx = vrc.Context(0, hbm_budget_bytes=220 * 2 ** 30, n_streams=4, max_inflight=32)
+        ids = []
+        t0 = time.perf_counter()
+        for c in wl["cubes"]:
+            if c["dims"] not in vols:
+                vols[c["dims"]] = cubegen.generate(c["dims"], c["n_sources"], c["seed"])
+            ids.append(ctx.cube_upload(vols[c["dims"]], dt, brick=128 if c["dims"][0] <= 512 else 256))
+        setup = time.perf_counter() - t0
+        r = serving_run(ctx, wl, ids)
+        r["setup_s"] = setup
+        r["resident_bytes"] = ctx.memory()[0]
+        out[dt] = r
+        ctx.close()
+        torch.cuda.empty_cache()
+    for dt in ("bf16", "fp8"):
+        out[dt]["beats_fp32_p99"] = out[dt]["p99_ms"] < out["f32"]["p99_ms"]
+        out[dt]["beats_fp32_p50"] = out[dt]["p50_ms"] < out["f32"]["p50_ms"]
+    out["workload"] = ("Poisson 200 requests/s for %.0f s (%d requests), 64 cubes 256^3-1024^3 (one generated volume "
+                       "per side), resident set, 50%% DVR / 30%% MIP / 20%% statistics, 512^2-1920x1080"
+                       % (args.serving_seconds, len(wl["requests"])))
+    return out
 
 
 # ------------------------------------------------- axis-aligned native MIP
@@ -827,60 +967,100 @@ def run_ooc(args):
 
 
 # ---------------------------------------------------------------- serving form
-def run_serving(args):
+def serving_run(ctx, wl, cube_ids, duration_s=None, seed_outs=8):
+    """Submit the request stream in real time (Poisson arrivals) and poll every
+    ticket; latency per request, samples/s and memory waits."""
     import torch
 
     import cubegen
     import paper_1111_6661_b300 as vrc
-    wl = cubegen.serving_stream(seed=5, rate_hz=args.rate, duration_s=args.duration, n_cubes=args.n_cubes)
-    if args.serving_dtype != "mix":
-        for c in wl["cubes"]:
-            c["dtype"] = args.serving_dtype
-    ctx = vrc.Context(0, hbm_budget_bytes=int(args.budget_gib * 2 ** 30), n_streams=4, max_inflight=32)
-    ids = []
-    t0 = time.perf_counter()
-    for c in wl["cubes"]:
-        v = cubegen.generate(c["dims"], c["n_sources"], c["seed"])
-        ids.append(ctx.cube_upload(v, c["dtype"], brick=128 if c["dims"][0] <= 512 else 256))
-    load_s = time.perf_counter() - t0
-    used, budget = ctx.memory()
     outs = {}
     for (w, h) in [(512, 512), (1024, 1024), (1920, 1080)]:
-        outs[(w, h)] = [torch.empty(w * h * 4, device="cuda") for _ in range(8)]
-    hists = [torch.empty(4096, dtype=torch.int64, device="cuda") for _ in range(8)]
-    reqs = wl["requests"]
+        outs[(w, h)] = [torch.empty(w * h * 4, device="cuda") for _ in range(seed_outs)]
+    hists = [torch.empty(4096, dtype=torch.int64, device="cuda") for _ in range(seed_outs)]
+    reqs = [r for r in wl["requests"] if duration_s is None or r["t"] < duration_s]
     tickets = []
     start = time.perf_counter()
     for i, r in enumerate(reqs):
         now = time.perf_counter() - start
         if r["t"] > now:
             time.sleep(r["t"] - now)
-        cid = ids[r["cube"]]
+        cid = cube_ids[r["cube"]]
         dims = wl["cubes"][r["cube"]]["dims"]
         if r["kind"] == "stats":
-            t = ctx.submit("stats", cid, nbins=4096, out=hists[i % 8])
+            t = ctx.submit("stats", cid, nbins=4096, out=hists[i % seed_outs])
         else:
             cam = cubegen.random_cameras(dims, 1, r["view_seed"])[0]
             rc = vrc.raycfg(r["width"], r["height"], 0.5, "trilinear")
             tf = cubegen.tf_random(r["tf_seed"] % 1000)
-            t = ctx.submit(r["kind"], cid, cam=cam, rc=rc, tf=tf, out=outs[(r["width"], r["height"])][i % 8])
+            t = ctx.submit(r["kind"], cid, cam=cam, rc=rc, tf=tf, out=outs[(r["width"], r["height"])][i % seed_outs])
         tickets.append((t, r["kind"]))
     res = [(ctx.poll(t, -1), k) for t, k in tickets]
     wall = time.perf_counter() - start
     lat = np.array([r["latency_ms"] for r, _ in res])
+    waits = np.array([r["memory_wait_ms"] for r, _ in res])
     samples = sum(r["samples"] for r, _ in res)
     bykind = {}
     for kind in ("dvr", "mip", "stats"):
         l = np.array([r["latency_ms"] for r, k in res if k == kind])
         if l.size:
             bykind[kind] = {"n": int(l.size), "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99))}
-    line = {"metric": "serving p50/p99 latency and samples/s", "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "samples_per_s": samples / wall, "requests": len(res),
-            "errors": int(sum(1 for r, _ in res if r["status"] != 0)), "rate_hz": args.rate,
-            "duration_s": args.duration, "wall_s": wall, "by_kind": bykind, "cubes": len(ids),
-            "resident_bytes": used, "budget_bytes": budget, "load_s": load_s,
+    paths = {}
+    for r, k in res:
+        if k != "stats":
+            paths[r["path"]] = paths.get(r["path"], 0) + 1
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "samples_per_s": samples / wall, "requests": len(res),
+            "errors": int(sum(1 for r, _ in res if r["status"] != 0)), "wall_s": wall, "by_kind": bykind,
             "queue_ms_p99": float(np.percentile([r["queue_ms"] for r, _ in res], 99)),
-            "cube_dtype": args.serving_dtype}
+            "memory_waits": {"requests_waited": int((waits > 0).sum()),
+                             "p50_ms_of_waited": float(np.percentile(waits[waits > 0], 50)) if (waits > 0).any() else 0.0,
+                             "p99_ms": float(np.percentile(waits, 99)),
+                             "uploads_triggered": int(sum(1 for r, _ in res if r["cube_loaded"]))},
+            "render_paths": paths}
+
+
+def make_serving_cubes(ctx, wl, registered: bool, shared_volumes: bool):
+    """Cubes of the serving workload: uploaded (resident set) or registered
+    (made resident on demand under the budget).  shared_volumes: one generated
+    volume per cube side, shared by every cube of that side (bounds the host
+    generation time; every cube is still uploaded, cached and evicted on its own)."""
+    import cubegen
+    vols, ids = {}, []
+    t0 = time.perf_counter()
+    for c in wl["cubes"]:
+        key = c["dims"] if shared_volumes else (c["dims"], c["seed"])
+        if key not in vols:
+            vols[key] = cubegen.generate(c["dims"], c["n_sources"], c["seed"])
+        brick = 128 if c["dims"][0] <= 512 else 256
+        if registered:
+            ids.append(ctx.cube_register(vols[key], c["dtype"], brick=brick))
+        else:
+            ids.append(ctx.cube_upload(vols[key], c["dtype"], brick=brick))
+    return ids, vols, time.perf_counter() - t0
+
+
+def run_serving(args):
+    import paper_1111_6661_b300 as vrc
+    import cubegen
+    wl = cubegen.serving_stream(seed=5, rate_hz=args.rate, duration_s=args.duration, n_cubes=args.n_cubes)
+    if args.serving_dtype != "mix":
+        for c in wl["cubes"]:
+            c["dtype"] = args.serving_dtype
+    registered = args.residency == "registered"
+    budget = args.budget_gib if args.budget_gib > 0 else (32.0 if registered else 200.0)
+    ctx = vrc.Context(0, hbm_budget_bytes=int(budget * 2 ** 30), n_streams=4, max_inflight=32)
+    ids, vols, load_s = make_serving_cubes(ctx, wl, registered, args.shared_volumes)
+    used, bud = ctx.memory()
+    line = {"metric": "serving p50/p99 latency and samples/s", "rate_hz": args.rate, "duration_s": args.duration,
+            "cubes": len(ids), "cube_dtype": args.serving_dtype,
+            "residency": "registered (uploaded on demand, LRU eviction under the budget)" if registered else
+                         "resident set (all cubes uploaded before the stream)",
+            "distinct_volumes": len(vols), "host_cube_bytes": int(sum(v.nbytes for v in vols.values())),
+            "resident_bytes_at_start": used, "budget_bytes": bud, "setup_s": load_s}
+    line.update(serving_run(ctx, wl, ids))
+    line["residency_counts"] = ctx.residency()
+    line["resident_bytes_at_end"] = ctx.memory()[0]
     ctx.close()
     print(json.dumps(line), flush=True)
 
@@ -902,6 +1082,9 @@ def main():
     ap.add_argument("--path", default="fused", choices=["fused", "slab", "sortlast"],
                     help="render path of the timed step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-precision", action="store_true", help="skip the bf16/fp8 forms of the default step")
+    ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving run per storage type")
+    ap.add_argument("--serving-seconds", type=float, default=8.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
     ap.add_argument("--dims", type=int, nargs=3, default=None, help="precision/ooc: cube dims")
     ap.add_argument("--error-pixels", type=int, default=4096)
@@ -915,8 +1098,13 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=20.0)
     ap.add_argument("--n-cubes", type=int, default=64)
-    ap.add_argument("--budget-gib", type=float, default=200.0)
+    ap.add_argument("--budget-gib", type=float, default=0.0,
+                    help="serving: HBM budget (0 = 32 GiB for registered cubes, 200 GiB for a resident set)")
     ap.add_argument("--serving-dtype", default="mix", choices=["mix", "f32", "bf16", "fp8"])
+    ap.add_argument("--residency", default="registered", choices=["registered", "resident"],
+                    help="serving: cubes registered (uploaded on demand under the budget) or all uploaded first")
+    ap.add_argument("--shared-volumes", action="store_true",
+                    help="serving: one generated volume per cube side, shared by the cubes of that side")
     args = ap.parse_args()
     if args.workload == "precision":
         return run_precision(args)

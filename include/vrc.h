@@ -200,8 +200,10 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
  * resident as its HBM budget allows).  src: caller-owned HOST array of
  * nx*ny*nz floats, x fastest, that must stay valid and unchanged until
  * vrc_cube_free.  storage and brick as for vrc_cube_upload (the render copy is
- * made unless VRC_COPY_NONE is given).  No device memory is used until the cube
- * is needed.  The serving loop admits a request for a registered cube once the
+ * made unless VRC_COPY_NONE is given).  The array is page-locked
+ * (cudaHostRegister) until vrc_cube_free when it is not page-locked already, so
+ * that uploads run at the host link's speed.  No device memory is used until
+ * the cube is needed.  The serving loop admits a request for a registered cube once the
  * cube is resident: it uploads it (the vrc_cube_upload passes, on a loader
  * thread) as soon as the memory the upload needs fits the budget, evicting
  * registered cubes that no queued or running request references, least

@@ -703,6 +703,7 @@ void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
 {
     release_device(ctx, c, sync);
     if (c->host_pool) cudaFreeHost(c->host_pool);
+    if (c->host_pinned) cudaHostUnregister((void *)c->host_src);
     for (cudaEvent_t e : c->slot_ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -946,6 +947,14 @@ vrc_status vrc_cube_register(vrc_ctx *ctx, const float *src, int64_t nx, int64_t
     c->managed = true;
     c->host_src = src;
     c->state.store(CUBE_ABSENT);
+    // page-lock the caller's array so that uploads copy at the link's speed;
+    // an array already page-locked (by the caller or another registration) is
+    // used as it is, and a failure only makes uploads slower
+    if (cudaSetDevice(ctx->device) == cudaSuccess &&
+        cudaHostRegister((void *)src, (size_t)(nx * ny * nz) * sizeof(float), cudaHostRegisterPortable) == cudaSuccess)
+        c->host_pinned = true;
+    else
+        cudaGetLastError();
     *cube_id = register_cube(ctx, c);
     return VRC_OK;
 }

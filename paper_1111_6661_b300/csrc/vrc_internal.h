@@ -117,6 +117,7 @@ struct Cube {
     // it (least recently used, when no request or call holds it) to make room
     bool managed = false;
     const float *host_src = nullptr;
+    bool host_pinned = false;     // host_src was page-locked by the registration (unlocked at release)
     std::atomic<int> state{2};    // CUBE_ABSENT, CUBE_LOADING, CUBE_RESIDENT
     double last_use = 0;          // host ms of the last admission or direct use
     bool direct_used = false;     // work of direct calls may be in flight: evictions wait for the device
