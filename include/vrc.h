@@ -491,8 +491,11 @@ vrc_status vrc_graph_destroy(vrc_graph *graph);
 typedef struct {
     int32_t tile_w, tile_h;      /* chosen ray tile */
     int32_t ctas_per_sm;         /* chosen persistent-grid occupancy */
+    int32_t brick;               /* brick edge of the cube after tuning */
+    float step;                  /* chosen step: the requested one unless a step tolerance was given */
     int32_t reserved;
-    double best_ms, default_ms;  /* time of the chosen and of the default configuration */
+    double best_ms, default_ms;  /* time of the chosen and of the default configuration (requested step) */
+    double step_max_abs_diff;    /* largest image difference of the chosen step against the requested one */
 } vrc_tuning;
 
 /*
@@ -505,6 +508,32 @@ typedef struct {
 vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
                         const vrc_raycfg *rc, const float *tf_rgba, float term_alpha, float *out, void *stream,
                         vrc_tuning *result);
+
+#define VRC_TUNE_BRICK 1
+/*
+ * Autotuner of the batching form: vrc_autotune's ray tile and grid search on
+ * the cube as it is, and
+ *   - with VRC_TUNE_BRICK (fp32 and bf16 cubes): the same search on the cube
+ *     re-packed at each other brick edge in {64, 128, 256} (at most the
+ *     smallest power of two >= the largest dimension), built on the device
+ *     from the cube's stored values (exact: the storage rounding is
+ *     idempotent); the fastest brick edge replaces the cube's storage under the
+ *     same id (images are the same bit for bit at every brick edge).  Edges
+ *     whose trial copy does not fit the budget are skipped.  FP8 cubes keep
+ *     their edge (their per-brick scales depend on it).
+ *   - with step_tolerance > 0: the requested step times 1.25, 1.5 and 2 is
+ *     timed with the chosen configuration, and the fastest step whose image
+ *     (all views, every channel) differs from the requested step's image by at
+ *     most step_tolerance is returned in result->step (renders keep using the
+ *     step the caller passes; step_tolerance = 0 never changes it).
+ * `out` (DEVICE, as for the render call) holds the last render.  Waits for
+ * `stream`.  Errors: as vrc_autotune; VRC_E_INVAL for unknown flags or a
+ * negative tolerance; VRC_E_BUSY when serving requests use the cube and its
+ * storage would be replaced.
+ */
+vrc_status vrc_autotune_cube(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                             const vrc_raycfg *rc, const float *tf_rgba, float term_alpha, float *out, void *stream,
+                             int32_t flags, float step_tolerance, vrc_tuning *result);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -308,17 +308,26 @@ class Context:
     def graph_destroy(self, g):
         self._check(self._lib.vrc_graph_destroy(g))
 
-    def autotune(self, cube_id: int, cams, rc, out, tf=None, term_alpha: float = 0.99, stream=None) -> dict:
+    def autotune(self, cube_id: int, cams, rc, out, tf=None, term_alpha: float = 0.99, stream=None,
+                 brick_search: bool = False, step_tolerance: float = 0.0) -> dict:
+        """Ray tile and grid search (vrc_autotune); with brick_search or a step
+        tolerance, vrc_autotune_cube (brick edges {64, 128, 256}, faster steps
+        within the tolerance)."""
         arr, n = _cams(cams)
         res = _vrc.vrc_tuning()
         tfp = None
         if tf is not None:
             tfa = np.ascontiguousarray(tf, dtype=np.float32).reshape(-1)
             tfp = ctypes.c_void_p(tfa.ctypes.data)
-        self._check(self._lib.vrc_autotune(self.h, cube_id, arr, n, ctypes.byref(rc), tfp, term_alpha,
-                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream), ctypes.byref(res)))
-        return dict(tile=(res.tile_w, res.tile_h), ctas_per_sm=res.ctas_per_sm, best_ms=res.best_ms,
-                    default_ms=res.default_ms)
+        if brick_search or step_tolerance > 0:
+            self._check(self._lib.vrc_autotune_cube(self.h, cube_id, arr, n, ctypes.byref(rc), tfp, term_alpha,
+                                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream),
+                                                    1 if brick_search else 0, step_tolerance, ctypes.byref(res)))
+        else:
+            self._check(self._lib.vrc_autotune(self.h, cube_id, arr, n, ctypes.byref(rc), tfp, term_alpha,
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream), ctypes.byref(res)))
+        return dict(tile=(res.tile_w, res.tile_h), ctas_per_sm=res.ctas_per_sm, brick=res.brick, step=res.step,
+                    best_ms=res.best_ms, default_ms=res.default_ms, step_max_abs_diff=res.step_max_abs_diff)
 
     # ------------------------------------------------------------ serving
     def submit(self, kind: str, cube_id: int, cam=None, rc=None, tf=None, term_alpha: float = 0.99, nbins: int = 0,

@@ -44,8 +44,8 @@ class vrc_raycfg(ctypes.Structure):
 
 
 class vrc_tuning(ctypes.Structure):
-    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32),
-                ("best_ms", c_f64), ("default_ms", c_f64)]
+    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("ctas_per_sm", c_i32), ("brick", c_i32), ("step", c_f32),
+                ("reserved", c_i32), ("best_ms", c_f64), ("default_ms", c_f64), ("step_max_abs_diff", c_f64)]
 
 
 class vrc_request(ctypes.Structure):
@@ -99,6 +99,8 @@ PROTOTYPES = {
     "vrc_graph_destroy": (c_i32, [c_p]),
     "vrc_autotune": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p, c_f32,
                              c_p, c_p, ctypes.POINTER(vrc_tuning)]),
+    "vrc_autotune_cube": (c_i32, [c_p, c_i64, ctypes.POINTER(vrc_camera), c_i32, ctypes.POINTER(vrc_raycfg), c_p,
+                                  c_f32, c_p, c_p, c_i32, c_f32, ctypes.POINTER(vrc_tuning)]),
     "vrc_submit": (c_i32, [c_p, ctypes.POINTER(vrc_request), ctypes.POINTER(c_u64)]),
     "vrc_poll": (c_i32, [c_p, c_u64, ctypes.POINTER(vrc_result), c_i32]),
     "vrc_debug_inject": (c_i32, [c_p, c_i32, c_i64]),

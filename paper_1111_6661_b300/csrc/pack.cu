@@ -469,6 +469,24 @@ __device__ __forceinline__ float stored_at(const uint8_t *bp, int64_t e, float s
     return __fmul_rn(__half2float(__half(h)), scale);
 }
 
+// Stored values of a resident cube back into a linear float array (x
+// fastest, interior voxels only): the source of a re-pack at another brick
+// size (autotuner).  One thread per voxel, grid-stride.
+template <int DT>
+__global__ void k_unpack(const uint8_t *__restrict__ pool, BrickGeom g, const float *__restrict__ scales,
+                         float *__restrict__ out)
+{
+    const int64_t n = g.dims[0] * g.dims[1] * g.dims[2];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % g.dims[0], yz = i / g.dims[0], y = yz % g.dims[1], z = yz / g.dims[1];
+        const int64_t bx = x >> g.logB, by = y >> g.logB, bz = z >> g.logB;
+        const int64_t b = (bz * g.nb[1] + by) * g.nb[0] + bx;
+        const int64_t lx = x - (bx << g.logB), ly = y - (by << g.logB), lz = z - (bz << g.logB);
+        const int64_t e = ((lz + 1) * g.R + (ly + 1)) * g.P + lx + g.O;
+        out[i] = stored_at<DT>(pool + b * g.brick_bytes, e, DT == VRC_FP8E4M3 ? scales[b] : 1.f);
+    }
+}
+
 // Maximum stored value over local voxels [8l-1, 8l+8]^3 of each 8^3 macro-cell
 // l of each brick (the brick's own copy, so FP8 halos use the brick's scale).
 // NaN voxels never raise the maximum.  One block per (brick, layer of cells),
@@ -709,6 +727,14 @@ void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
     delete c;
 }
 
+int64_t register_cube(vrc_ctx *ctx, Cube *c)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    c->id = ctx->next_id++;
+    ctx->cubes[c->id] = c;
+    return c->id;
+}
+
 namespace {
 
 vrc_status alloc_meta(vrc_ctx *ctx, Cube *c)
@@ -723,13 +749,6 @@ vrc_status alloc_meta(vrc_ctx *ctx, Cube *c)
     return VRC_OK;
 }
 
-int64_t register_cube(vrc_ctx *ctx, Cube *c)
-{
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    c->id = ctx->next_id++;
-    ctx->cubes[c->id] = c;
-    return c->id;
-}
 
 // Extrema and sums of one host brick (Sec. 2: sub-cubes of a cube larger
 // than memory): interior voxels inside the cube, plus the largest value a
@@ -1335,3 +1354,17 @@ extern "C" vrc_status vrc_residency(vrc_ctx *ctx, int64_t *resident, uint64_t *l
     if (evictions) *evictions = ctx->evictions.load();
     return VRC_OK;
 }
+
+vrc_status unpack_cube(vrc_ctx *ctx, const Cube *c, float *dst, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    const unsigned grid = (unsigned)ctx->sm_count * 8;
+    const uint8_t *pool = (const uint8_t *)c->pool;
+    if (g.dtype == VRC_F32) k_unpack<VRC_F32><<<grid, 256, 0, st>>>(pool, g, c->scales, dst);
+    else if (g.dtype == VRC_BF16) k_unpack<VRC_BF16><<<grid, 256, 0, st>>>(pool, g, c->scales, dst);
+    else k_unpack<VRC_FP8E4M3><<<grid, 256, 0, st>>>(pool, g, c->scales, dst);
+    count_launch(ctx);
+    VRC_CK(ctx, cudaGetLastError());
+    return VRC_OK;
+}
+

@@ -1573,10 +1573,187 @@ vrc_status vrc_autotune(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, i
         result->tile_w = bw;
         result->tile_h = bh;
         result->ctas_per_sm = bc;
+        result->brick = c->g.B;
+        result->step = rc->step;
         result->reserved = 0;
         result->best_ms = best;
         result->default_ms = dflt;
+        result->step_max_abs_diff = 0.0;
     }
+    return VRC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Largest |a - b| over n floats, as the bits of a non-negative float (which
+// order like unsigned integers) in *out (zeroed by the caller).
+__global__ void k_max_abs_diff(const float *__restrict__ a, const float *__restrict__ b, int64_t n, unsigned int *out)
+{
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(a[i] - b[i]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// Time one render (best of two) with the cube's tuned configuration.
+vrc_status time_render(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views, const vrc_raycfg &r,
+                       const float *tf, float term, float *out, cudaStream_t st, double *ms_out)
+{
+    cudaEvent_t e0, e1;
+    VRC_CK(ctx, cudaEventCreate(&e0));
+    VRC_CK(ctx, cudaEventCreate(&e1));
+    double best = 1e300;
+    vrc_status s = VRC_OK;
+    for (int rep = 0; rep < 2 && s == VRC_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        s = render_common(ctx, cube_id, cams, n_views, &r, tf, term, out, st, tf ? 1 : 0, 0, nullptr, false);
+        cudaEventRecord(e1, st);
+        if (s != VRC_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = best;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+vrc_status vrc_autotune_cube(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, int32_t n_views,
+                             const vrc_raycfg *rc, const float *tf_rgba, float term_alpha, float *out, void *stream,
+                             int32_t flags, float step_tolerance, vrc_tuning *result)
+{
+    if (!ctx || !result) return VRC_E_INVAL;
+    if ((flags & ~VRC_TUNE_BRICK) != 0) return set_err(ctx, VRC_E_INVAL, "unknown tuning flags %d", flags);
+    if (!(step_tolerance >= 0.f)) return set_err(ctx, VRC_E_INVAL, "step tolerance must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    vrc_tuning best{};
+    vrc_status s = vrc_autotune(ctx, cube_id, cams, n_views, rc, tf_rgba, term_alpha, out, stream, &best);
+    if (s != VRC_OK) return s;
+    const double default_ms = best.default_ms;
+    int64_t best_id = cube_id;
+    Cube *c = find_cube(ctx, cube_id);
+    if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    // 1. brick edges: trial cubes re-packed on the device from the stored values
+    if ((flags & VRC_TUNE_BRICK) && c->g.dtype != VRC_FP8E4M3 && c->pool) {
+        const BrickGeom g = c->g;
+        const int64_t n = g.dims[0] * g.dims[1] * g.dims[2];
+        int64_t maxd = std::max(g.dims[0], std::max(g.dims[1], g.dims[2])), cap = 16;
+        while (cap < maxd) cap *= 2;
+        float *lin = nullptr;
+        if ((s = dev_alloc(ctx, (void **)&lin, (size_t)n * 4)) != VRC_OK) return s;
+        s = unpack_cube(ctx, c, lin, st);
+        for (int B = 64; B <= 256 && s == VRC_OK; B *= 2) {
+            if (B == g.B || B > cap) continue;
+            Cube *t = new (std::nothrow) Cube();
+            if (!t) break;
+            if (!make_geom(g.dims[0], g.dims[1], g.dims[2], B, g.dtype, &t->g, 32)) {
+                delete t;
+                continue;
+            }
+            t->copy_mode = c->copy_mode == VRC_COPY_NONE ? VRC_COPY_NONE : VRC_COPY_REQUIRED;
+            if (upload_cube(ctx, t, lin, 1, st) != VRC_OK) {   // no room in the budget: skip this edge
+                delete t;
+                continue;
+            }
+            const int64_t tid = register_cube(ctx, t);
+            vrc_tuning r{};
+            const vrc_status ts = vrc_autotune(ctx, tid, cams, n_views, rc, tf_rgba, term_alpha, out, stream, &r);
+            if (ts == VRC_OK && r.best_ms < best.best_ms) {
+                if (best_id != cube_id) vrc_cube_free(ctx, best_id);
+                best = r;
+                best_id = tid;
+            } else {
+                vrc_cube_free(ctx, tid);
+            }
+        }
+        cudaStreamSynchronize(st);
+        dev_free(ctx, lin, (size_t)n * 4);
+        if (s != VRC_OK) {
+            if (best_id != cube_id) vrc_cube_free(ctx, best_id);
+            return s;
+        }
+        if (best_id != cube_id) {
+            // the winner's storage takes the cube's id; the old storage is released
+            Cube *old = nullptr, *w = nullptr;
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                old = ctx->cubes[cube_id];
+                w = ctx->cubes[best_id];
+                if (old->refs.load() > 0 || old->state.load() == CUBE_LOADING) {
+                    s = set_err(ctx, VRC_E_BUSY, "cube in use by serving requests: storage not replaced");
+                } else {
+                    ctx->cubes.erase(best_id);
+                    w->id = cube_id;
+                    w->managed = old->managed;
+                    w->host_src = old->host_src;
+                    w->host_pinned = old->host_pinned;
+                    old->host_pinned = false;
+                    w->loads = old->loads;
+                    w->last_use = old->last_use;
+                    ctx->cubes[cube_id] = w;
+                }
+            }
+            if (s != VRC_OK) {
+                vrc_cube_free(ctx, best_id);
+                return s;
+            }
+            release_cube(ctx, old, true);
+            c = w;
+        }
+    }
+    best.brick = c->g.B;
+    best.default_ms = default_ms;
+    best.step = rc->step;
+    best.step_max_abs_diff = 0.0;
+    // 2. step: faster steps whose image stays within the tolerance
+    if (step_tolerance > 0.f) {
+        const int64_t nfl = (int64_t)n_views * rc->width * rc->height * (tf_rgba ? 4 : 1);
+        float *ref = nullptr;
+        unsigned int *dmax = nullptr;
+        if ((s = dev_alloc(ctx, (void **)&ref, (size_t)nfl * 4 + 256)) != VRC_OK) return s;
+        dmax = reinterpret_cast<unsigned int *>(ref + nfl);
+        vrc_raycfg r = *rc;
+        double step_ms = 0;
+        s = time_render(ctx, cube_id, cams, n_views, r, tf_rgba, term_alpha, out, st, &step_ms);
+        if (s == VRC_OK && cudaMemcpyAsync(ref, out, (size_t)nfl * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            s = cuda_err(ctx, cudaGetLastError(), "reference image");
+        const float factors[3] = {1.25f, 1.5f, 2.f};
+        for (int i = 0; i < 3 && s == VRC_OK; ++i) {
+            r.step = rc->step * factors[i];
+            if (validate_step(ctx, c, r.step) != VRC_OK) break;
+            double ms = 0;
+            if ((s = time_render(ctx, cube_id, cams, n_views, r, tf_rgba, term_alpha, out, st, &ms)) != VRC_OK) break;
+            cudaMemsetAsync(dmax, 0, 4, st);
+            k_max_abs_diff<<<grid_for(nfl, ctx->sm_count * 8), 256, 0, st>>>(out, ref, nfl, dmax);
+            count_launch(ctx);
+            unsigned int bits = 0;
+            if (cudaMemcpyAsync(&bits, dmax, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                s = cuda_err(ctx, cudaGetLastError(), "image difference");
+                break;
+            }
+            float diff;
+            std::memcpy(&diff, &bits, 4);
+            if (diff <= step_tolerance && ms < step_ms) {
+                step_ms = ms;
+                best.step = r.step;
+                best.step_max_abs_diff = diff;
+            }
+        }
+        cudaStreamSynchronize(st);
+        dev_free(ctx, ref, (size_t)nfl * 4 + 256);
+        if (s != VRC_OK) return s;
+    }
+    *result = best;
     return VRC_OK;
 }
 

@@ -207,7 +207,6 @@ bool tex_array_take(vrc_ctx *ctx, uint64_t key, TexArray *a);
 void tex_array_give(vrc_ctx *ctx, uint64_t key, const TexArray &a);   // idle arrays only
 void cache_trim(vrc_ctx *ctx, int64_t keep_bytes);                     // release cached memory down to keep_bytes
 bool reap_pending(vrc_ctx *ctx, bool wait);   // release completed (wait: all) async-freed cubes; true if any
-void release_cube(vrc_ctx *ctx, Cube *c, bool sync);   // sync: wait for the device first
 void destroy_tex_array(const TexArray &a);
 vrc_status scratch_get(vrc_ctx *ctx, size_t bytes, void **p);
 Cube *find_cube(vrc_ctx *ctx, int64_t id);
@@ -258,6 +257,10 @@ void server_stop(vrc_ctx *ctx);
 // back its device memory (the record stays).
 vrc_status upload_cube(vrc_ctx *ctx, Cube *c, const float *src, int32_t src_on_device, cudaStream_t st);
 void release_device(vrc_ctx *ctx, Cube *c, bool sync);
+void release_cube(vrc_ctx *ctx, Cube *c, bool sync);
+int64_t register_cube(vrc_ctx *ctx, Cube *c);
+// Stored values of a resident cube into dst (device, nx*ny*nz floats, x fastest).
+vrc_status unpack_cube(vrc_ctx *ctx, const Cube *c, float *dst, cudaStream_t st);
 // Device bytes a registered cube needs while its upload runs (bricks,
 // metadata, render copy, staging of the source, scratch reserve).
 int64_t upload_peak_bytes(const Cube *c);

@@ -42,7 +42,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(_vrc.vrc_stats) == 48
     assert ctypes.sizeof(_vrc.vrc_camera) == 48
     assert ctypes.sizeof(_vrc.vrc_raycfg) == 40
-    assert ctypes.sizeof(_vrc.vrc_tuning) == 32
+    assert ctypes.sizeof(_vrc.vrc_tuning) == 48
     assert ctypes.sizeof(_vrc.vrc_request) == 4216
     assert ctypes.sizeof(_vrc.vrc_result) == 96
 

@@ -21,6 +21,9 @@ import oracle
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 PIXELS_PER_VIEW = 512
+# largest share of termination-fragile pixels allowed per view (see
+# test_gpu_parity.FRAGILE_MAX); measured at most 3.21% over the 32 orbit views
+FRAGILE_MAX = 0.035
 
 
 @pytest.fixture(scope="module")
@@ -84,8 +87,10 @@ def test_fullsize_dvr_orbit(full):
         ok = d <= 1e-4
         inside = np.all((got >= r["lo"] - 1e-4) & (got <= r["hi"] + 1e-4), axis=1)
         ok |= r["fragile"] & inside
-        assert ok.all(), (i, int((~ok).sum()), float(d.max()))
-        assert r["fragile"].mean() < 0.05
+        frac = float(r["fragile"].mean())
+        print(f"view {i}: fragile fraction {frac:.4f} ({int(r['fragile'].sum())} of {r['fragile'].size})")
+        assert ok.all(), (i, int((~ok).sum()), float(d.max()), f"fragile fraction {frac:.4f}")
+        assert frac <= FRAGILE_MAX, (i, f"fragile fraction {frac:.4f}")
         nonzero += int((r["out"][:, 3] > 0).sum())
     assert nonzero > 0   # the sampled pixels see sources, not only background
 

@@ -152,13 +152,22 @@ def render_check_mip(ctx, v, cid, cams, W, H, step, sampling, dtype="f32", B=0, 
     return got
 
 
+# Largest share of termination-fragile pixels allowed in one image: pixels
+# whose stopping sample a binary32 evaluation could move (the oracle's alpha
+# window, see oracle.render); they are checked against the oracle's bracket
+# instead of its exact-index result.  Measured at most 1.87% in these tests.
+FRAGILE_MAX = 0.02
+
+
 def check_dvr(got, r, tol=1e-4):
     d = np.abs(got - r["out"]).max(axis=1)
     ok = d <= tol
     inside = np.all((got >= r["lo"] - tol) & (got <= r["hi"] + tol), axis=1)
     ok |= r["fragile"] & inside
-    assert ok.all(), (int((~ok).sum()), float(d.max()))
-    assert r["fragile"].mean() < 0.05   # conservative alpha-error window; see oracle.render
+    frac = float(r["fragile"].mean())
+    print(f"fragile fraction {frac:.4f} ({int(r['fragile'].sum())} of {r['fragile'].size})")
+    assert ok.all(), (int((~ok).sum()), float(d.max()), f"fragile fraction {frac:.4f}")
+    assert frac <= FRAGILE_MAX, f"fragile fraction {frac:.4f}"
 
 
 def render_check_dvr(ctx, v, cid, cams, W, H, step, tf, term=0.99, dtype="f32", B=0, path="fused", opc=False,
@@ -305,6 +314,45 @@ def test_graph_and_autotune(ctx, cube128):
     assert res["best_ms"] <= res["default_ms"] + 1e-9
     again = ctx.render_dvr(cid, cams, rc, tf)
     assert torch.equal(again, ref)
+    ctx.cube_free(cid)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_autotune_brick_edge_and_step(ctx, cube128, dtype):
+    """The batching form's autotuner: the cube re-packed on the device at brick
+    edges 64 and 128 (the stored values are kept exactly), the fastest edge
+    replacing its storage under the same id; images and statistics are the
+    same at every edge, and they still match the oracle.  A faster step is
+    taken only within the caller's image tolerance."""
+    vrc = vrcmod()
+    v = cube128[:, :, :120].copy()          # 120 x 128 x 128: ragged along x at edge 64 and 128
+    cid = ctx.cube_upload(v, dtype, brick=32)
+    cams = cubegen.orbit_cameras((120, 128, 128), 2)
+    rc = vrc.raycfg(64, 48, 0.5)
+    tf = cubegen.tf_dense()
+    ref = ctx.render_dvr(cid, cams, rc, tf).clone()
+    s0, h0 = ctx.cube_stats(cid, 100)
+    out = torch.zeros_like(ref)
+    res = ctx.autotune(cid, cams, rc, out, tf=tf, brick_search=True)
+    assert res["brick"] in (32, 64, 128) and ctx.cube_info(cid)["brick"] == res["brick"]
+    assert res["step"] == rc.step and res["step_max_abs_diff"] == 0.0
+    assert res["best_ms"] <= res["default_ms"] + 1e-9
+    assert torch.equal(ctx.render_dvr(cid, cams, rc, tf), ref)
+    s1, h1 = ctx.cube_stats(cid, 100)
+    assert s1["min"] == s0["min"] and s1["max"] == s0["max"] and np.array_equal(h0, h1)
+    assert abs(s1["mean"] - s0["mean"]) <= 1e-12 * s0["std"] and abs(s1["std"] - s0["std"]) <= 1e-12 * s0["std"]
+    vv = v if dtype == "f32" else oracle.dequantize(v, dtype)
+    render_check_dvr(ctx, vv, cid, cams[:1], 64, 48, 0.5, tf)
+    # every edge gives the same image: re-pack at each one through the tuner's trial path
+    for B in (64, 128):
+        other = ctx.cube_upload(v, dtype, brick=B)
+        assert torch.equal(ctx.render_dvr(other, cams, rc, tf), ref)
+        ctx.cube_free(other)
+    # step: a tolerance of 0 never changes it; a loose one may take a faster step within it
+    res = ctx.autotune(cid, cams, rc, out, tf=tf, step_tolerance=1.0)
+    assert res["step"] >= rc.step and res["step_max_abs_diff"] <= 1.0
+    res2 = ctx.autotune(cid, cams, rc, out, tf=tf, step_tolerance=1e-9)
+    assert res2["step"] == rc.step or res2["step_max_abs_diff"] <= 1e-9
     ctx.cube_free(cid)
 
 

@@ -107,7 +107,8 @@ def test_alone_equals_mixed(setup):
             assert res["samples"] == ares["samples"] and res["samples"] > 0
         assert res["latency_ms"] >= res["queue_ms"] >= 0
         fragile.append(check_against_oracle(ctx, cubes, r, o, res))
-    assert max(fragile) < 0.05, fragile
+    print(f"served images: largest fragile fraction {max(fragile):.4f}")
+    assert max(fragile) <= 0.03, fragile   # termination-fragile share (see test_gpu_parity); measured 2.88%
 
 
 def test_short_request_overtakes_long_render(setup):
@@ -158,9 +159,10 @@ def test_busy_drop_timeout_and_bad_ticket(setup):
     vrc, ctx, cubes = setup
     cid, dims, _ = cubes[0]
     cam = cubegen.orbit_cameras(dims, 1)[0]
-    out = torch.zeros(256 * 256 * 4, device="cuda")
-    rc = vrc.raycfg(256, 256, 0.25)
-    tickets = [ctx.submit("dvr", cid, cam=cam, rc=rc, tf=cubegen.tf_sparse(), out=out) for _ in range(4)]
+    out = torch.zeros(1024 * 1024 * 4, device="cuda")
+    rc = vrc.raycfg(1024, 1024, 0.005)      # long enough to be pending when the cube is freed
+    tickets = [ctx.submit("dvr", cid, cam=cam, rc=rc, tf=cubegen.tf_sparse(), term_alpha=2.0, out=out)
+               for _ in range(4)]
     with pytest.raises(vrc.VrcError, match="BUSY"):
         ctx.cube_free(cid)                  # referenced by pending requests
     for t in tickets:
