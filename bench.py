@@ -58,7 +58,7 @@ def workload_config(w: dict, views: int) -> dict:
 
 
 RENDER_SOURCES = ("paper_1111_6661_b300/csrc/render.cu", "paper_1111_6661_b300/csrc/ray.cuh")
-TRAFFIC_PROFILE = "profiles/k_render_fused_dvr1024_traffic.md"
+TRAFFIC_PROFILE = "profiles/k_render_fused_dvr768_traffic.md"
 
 
 def render_source_hash() -> str:
