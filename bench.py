@@ -721,12 +721,14 @@ def run_precision(args):
     rng = np.random.default_rng(0)
     pix = rng.choice(W * H, size=args.error_pixels, replace=False)
     ref_views = list(range(0, views, max(1, views // 2)))[:2]
-    ctx = vrc.Context(0)
     st_ref = oracle.stats(v)
     out = {}
     pk, pk_kind = peaks()
     nvox = dims[0] * dims[1] * dims[2]
     for dt in ("f32", "bf16", "fp8"):
+        # a context per storage type: the previous one's cached device memory
+        # (bricks, render copies, the upload's staging) goes back to the device
+        ctx = vrc.Context(0)
         torch.cuda.synchronize()
         t_up = time.perf_counter()
         cid = ctx.cube_upload(v, dt, brick=256)
@@ -783,10 +785,11 @@ def run_precision(args):
                          "max_abs_err_vs_stored_oracle": max(errs["vs_stored_oracle"])}
             del img
         row["stored_bytes"] = info["bytes"]
+        row["render_copy_bytes"] = info["render_copy_bytes"]
         out[dt] = row
         ctx.cube_free(cid)
+        ctx.close()
         torch.cuda.empty_cache()
-    ctx.close()
     line = {"metric": "precision form: samples/s and error vs FP64 oracle per storage type", "workload":
             f"precision{dims[0]}x{dims[1]}x{dims[2]}", "views": views, "image": [W, H], "step": 0.5,
             "error_sample": f"{args.error_pixels} random pixels of views {ref_views}; stats over all voxels",

@@ -392,12 +392,14 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
 
 // Fused path, persistent: CTAs pull (job, tile) items from an atomic counter.
 // TEX: trilinear samples come from the cubes' texture copies.  Register caps
-// (CTAs per SM) are the measured best: 6 for the texture ray walk (32-view
-// 1080p DVR of a 1024^3 cube: bf16 302 -> 338, fp8 318 -> 355, fp32 227 ->
-// 230 G samples/s against 5; 7 for bf16/fp8 DVR: 307 / 302; 4: 256 / 276 / 200),
-// 5 otherwise.
+// (CTAs per SM) are the measured best.  6 for the texture ray walk of MIP and
+// of bf16/fp8 DVR (32-view 1080p DVR of a 1024^3 cube: bf16 302 -> 338, fp8
+// 318 -> 355 G samples/s against 5; a 2048^3 cube +9..13%; 7: 307 / 302).
+// fp32 DVR keeps 5 (48 registers, no spills): at 6 (40 registers, spills) it
+// gained 1% on the 1024^3 cube and lost 7..11% on a 2048^3 cube, where the
+// autotuner also found no better grid for the 6-CTA build.  5 otherwise.
 template <int MODE, int SAMPLING, int DT, bool TEX, bool SKIP>
-__global__ void __launch_bounds__(kThreads, (TEX && !SKIP) ? 6 : 5)
+__global__ void __launch_bounds__(kThreads, (TEX && !SKIP && !(MODE == 1 && DT == VRC_F32)) ? 6 : 5)
     k_render_fused(const JobDesc *__restrict__ jobs, int n_jobs, int64_t total_items, int *counter)
 {
     __shared__ float4 s_tf[256];
