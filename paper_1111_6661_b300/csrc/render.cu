@@ -1645,8 +1645,10 @@ vrc_status vrc_autotune_cube(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *ca
     if (s != VRC_OK) return s;
     const double default_ms = best.default_ms;
     int64_t best_id = cube_id;
-    Cube *c = find_cube(ctx, cube_id);
-    if (!c) return set_err(ctx, VRC_E_BADID, "unknown cube %lld", (long long)cube_id);
+    // held for the whole call: a registered cube is not evicted while it is re-packed
+    Cube *c = nullptr;
+    CubeUse use;
+    if ((s = acquire_cube(ctx, cube_id, st, &c, use)) != VRC_OK) return s;
     // 1. brick edges: trial cubes re-packed on the device from the stored values
     if ((flags & VRC_TUNE_BRICK) && c->g.dtype != VRC_FP8E4M3 && c->pool) {
         const BrickGeom g = c->g;
@@ -1693,7 +1695,8 @@ vrc_status vrc_autotune_cube(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *ca
                 std::lock_guard<std::mutex> lk(ctx->mu);
                 old = ctx->cubes[cube_id];
                 w = ctx->cubes[best_id];
-                if (old->refs.load() > 0 || old->state.load() == CUBE_LOADING) {
+                // this call's own reference is the only one allowed
+                if (old->refs.load() > 1 || old->state.load() == CUBE_LOADING) {
                     s = set_err(ctx, VRC_E_BUSY, "cube in use by serving requests: storage not replaced");
                 } else {
                     ctx->cubes.erase(best_id);
@@ -1711,6 +1714,10 @@ vrc_status vrc_autotune_cube(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *ca
                 vrc_cube_free(ctx, best_id);
                 return s;
             }
+            // hand the reference over to the new storage before the old one goes
+            w->refs.fetch_add(1);
+            use.c = w;
+            old->refs.fetch_sub(1);
             release_cube(ctx, old, true);
             c = w;
         }
