@@ -300,14 +300,18 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
         float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
         float pu = -1.f, pv = -1.f;
         int pl = -1;
+        // one compare per sample: kh_stop <= kh_end, so the ray's end is tested
+        // only where a brick ends; the samples taken are counted once at the end
+        float kh = 0.5f;
 #pragma unroll 1
-        for (float kh = 0.5f; kh < kh_end; kh = __fadd_rn(kh, 1.f)) {
+        for (;; kh = __fadd_rn(kh, 1.f)) {
             // positions as stated: each product and sum rounded on its own (the
             // scalar intrinsics are never contracted into a fused multiply-add)
             const float t = t_at(kh);
             const float2 pxy = make_float2(__fadd_rn(o[0], __fmul_rn(t, d[0])), __fadd_rn(o[1], __fmul_rn(t, d[1])));
             const float p2 = __fadd_rn(o[2], __fmul_rn(t, d[2]));
             if (kh >= kh_stop) {
+                if (!(kh < kh_end)) break;
                 // entering the brick of this sample
                 const int bx = min(max((int)floorf(pxy.x), 0), cv.dims[0] - 1) >> cv.logB;
                 const int by = min(max((int)floorf(pxy.y), 0), cv.dims[1] - 1) >> cv.logB;
@@ -381,15 +385,17 @@ __device__ __forceinline__ void trace_tex(const JobDesc &J, const float4 *s_tf, 
                 sv = fmaf(wz, e.y - e.x, e.x);
                 if (DT == VRC_FP8E4M3) sv = sv * scale;
             }
-            ++nsamp;
             if (MODE == 0) {
                 m = fmaxf(m, sv);
-            } else {
-                if (sv > J.skip_below)   // false for NaN
-                    over(acc, classify(s_tf, sv, J.vmin, J.inv_range), step, J.opacity_correction);
-                if (acc.A >= J.term) break;
+            } else if (sv > J.skip_below) {   // false for NaN; transparent samples leave A as it is
+                over(acc, classify(s_tf, sv, J.vmin, J.inv_range), step, J.opacity_correction);
+                if (acc.A >= J.term) {
+                    kh = __fadd_rn(kh, 1.f);   // this sample counts
+                    break;
+                }
             }
         }
+        nsamp += (uint32_t)(kh - 0.5f);   // samples k = 0 .. kh - 1.5 were taken
     }
     if (MODE == 0) J.out[pix] = m;
     else reinterpret_cast<float4 *>(J.out)[pix] = make_float4(acc.rg.x, acc.rg.y, acc.b, acc.A);
