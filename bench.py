@@ -378,10 +378,11 @@ def run_gpu(args, w):
         torch.cuda.synchronize()
         n_ms = e0.elapsed_time(e1) / reps
         n_samp = ctx.last_render_samples()
+        n_path = ctx.last_render_path()
         n_bytes = n_samp * {"f32": 4, "bf16": 2, "fp8": 1}[w["storage"]]
         n_gbs = n_bytes / (n_ms / 1e3) / 1e9
         mip_native = {"ms": n_ms, "samples": n_samp, "samples_per_s": n_samp / (n_ms / 1e3), "hbm_gbs": n_gbs,
-                      "hbm_frac": n_gbs / pk["hbm_gbs"], "hbm_peak_kind": pk_kind,
+                      "hbm_frac": n_gbs / pk["hbm_gbs"], "hbm_peak_kind": pk_kind, "render_path": n_path,
                       "note": "orthographic MIP along z at native resolution (%dx%d pixels, step 1, nearest): one "
                               "sample per voxel, each voxel read once; algorithmic bytes = stored bytes of the "
                               "samples; cube larger than L2" % (NX, NY)}
@@ -694,7 +695,8 @@ def run_mip_native(args):
                       "warmup": args.warmup, "dtype": storage, "data": "synthetic",
                       "config": {"workload": "mip_native", "dims": list(w["dims"]), "image": [NX, NY], "step": 1.0,
                                  "sampling": "nearest", "storage": storage},
-                      "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "hbm_peak_kind": pk_kind}), flush=True)
+                      "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "hbm_peak_kind": pk_kind,
+                      "render_path": ctx.last_render_path()}), flush=True)
     ctx.cube_free(cid)
     ctx.close()
 
@@ -934,6 +936,32 @@ def run_ooc(args):
     if not args.aliased and not args.no_parity:
         parity = ooc_window_parity(ctx, cid, dims, nsrc, seed, info, tf,
                                    x0=min(1536, dims[0] - 68), y0=min(1024, dims[1] - 68))
+    overlap = None
+    if not args.aliased and K == total and dims[0] * dims[1] * dims[2] * 4 <= 0.25 * avail:
+        # copy/compute overlap of the streamed frame: the same view rendered by
+        # the same brick kernels (sort-last, global loads) from resident bricks
+        # gives the compute time; the pinned-copy probe gives the copy time
+        rid = ctx.cube_upload(cubegen.generate(dims, nsrc, seed), "f32", brick=B, render_copy="none")
+        rs = vrc.raycfg(1920, 1080, 0.5, "trilinear", path="sortlast")
+        ref = out.clone()
+        ct = []
+        for _ in range(3):
+            e0.record()
+            ctx.render_dvr(rid, cams, rs, tf, 0.99, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ct.append(e0.elapsed_time(e1))
+        comp_ms = float(np.median(ct))
+        copy_ms = streamed / (link_gbs * 1e9) * 1e3
+        hidden = copy_ms + comp_ms - frame_ms
+        overlap = {"compute_ms_resident": comp_ms, "copy_ms_at_probe": copy_ms, "frame_ms": frame_ms,
+                   "overlap_pct": max(0.0, min(100.0, 100.0 * hidden / min(copy_ms, comp_ms))),
+                   "max_abs_diff_vs_streamed": float((ref - out).abs().max()),
+                   "note": "share of the shorter of copy and compute hidden under the other: "
+                           "(copy + compute - frame) / min(copy, compute); compute = the same sort-last "
+                           "render from resident bricks, copy = streamed bytes at the pinned-copy probe"}
+        ctx.cube_free(rid)
+        out.copy_(ref)
     zc = None
     if args.zerocopy_frames > 0 and (args.aliased or K == total):
         # zero-copy variant: the brick kernels read the mapped pinned slots in place
@@ -959,7 +987,7 @@ def run_ooc(args):
             "bricks_culled": culled, "bytes_streamed_per_frame": streamed,
             "achieved_link_gbs": streamed / (frame_ms / 1e3) / 1e9, "pinned_h2d_probe_gbs": link_gbs,
             "link_bound_frame_ms": streamed / (link_gbs * 1e9) * 1e3, "samples": nsamp,
-            "samples_per_s": nsamp / (frame_ms / 1e3), "parity_window": parity,
+            "samples_per_s": nsamp / (frame_ms / 1e3), "parity_window": parity, "copy_compute_overlap": overlap,
             "note": ("bricks missing from the host cache are generated on the rendering thread before their "
                      "copies (provider-bound frames)") if not args.aliased else
                     "logical brick b reads pinned host slot b % host_slots",

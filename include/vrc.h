@@ -444,9 +444,16 @@ vrc_status vrc_last_render_samples(vrc_ctx *ctx, uint64_t *samples, uint64_t *ev
  * took: VRC_PATH_FUSED (texture gathers from the render copy), VRC_PATH_FUSED_LDG
  * (global loads: requested, nearest sampling, or the cube has no render copy),
  * VRC_PATH_SORTLAST, VRC_PATH_STREAMED (out-of-core: bricks copied through the
- * device ring), VRC_PATH_ZEROCOPY or VRC_PATH_SLAB.  *path is HOST memory.
+ * device ring), VRC_PATH_ZEROCOPY, VRC_PATH_SLAB or VRC_PATH_ROWS (nearest MIP
+ * of orthographic views along y or z; groups of rays whose voxel columns are
+ * not consecutive x of one brick row take the per-ray loop inside the same
+ * launch).  *path is HOST memory.
  */
 #define VRC_PATH_STREAMED  5   /* reported only: sort-last with brick streaming */
+#define VRC_PATH_ROWS      6   /* reported only: fused nearest MIP of an orthographic view along
+                                  y or z, 8 pixels of an image row per thread (one 8-, 16- or
+                                  32-byte load per sample of the group's rays); same image as
+                                  the per-ray loop, bit for bit */
 vrc_status vrc_last_render_path(vrc_ctx *ctx, int32_t *path);
 
 /*

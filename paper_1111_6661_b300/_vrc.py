@@ -17,7 +17,7 @@ STATUS = {0: "VRC_OK", 1: "VRC_PENDING", -1: "VRC_E_INVAL", -2: "VRC_E_NOMEM", -
 DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
 SAMPLING = {"nearest": 0, "trilinear": 1}
 PATHS = {"fused": 0, "sortlast": 1, "fused_ldg": 2, "zerocopy": 3, "slab": 4}
-PATH_NAMES = {0: "fused", 1: "sortlast", 2: "fused_ldg", 3: "zerocopy", 4: "slab", 5: "streamed"}
+PATH_NAMES = {0: "fused", 1: "sortlast", 2: "fused_ldg", 3: "zerocopy", 4: "slab", 5: "streamed", 6: "rows"}
 COPY = {"auto": 0x000, "required": 0x100, "none": 0x200}
 INJECT = {"none": 0, "alloc": 1, "h2d": 2, "drop": 3, "slab_wait": 4}
 

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, (TEX && !SKIP && !(MODE == 1 && DT =
         if (item >= total_items) break;
         const JobDesc &J = jobs[jid];
         if (MODE == 1 && jid != loaded) {
-            s_tf[threadIdx.x] = J.tf[threadIdx.x];
+            s_tf[threadIdx.x] = J.tf[threadIdx.x];   // tiles are 256 pixels: one entry per thread
             __syncthreads();
             loaded = jid;
         }
@@ -452,6 +452,189 @@ __global__ void __launch_bounds__(kThreads, (TEX && !SKIP && !(MODE == 1 && DT =
         nsamp = neval = 0;
         __syncthreads();
     }
+}
+
+// Orthographic nearest MIP along the cube's y or z axis, G = 8 pixels of an
+// image row per thread.  When the G rays share their direction, their t range
+// and their coordinate on the moving axis, and their voxel columns are G
+// consecutive x (in either order, the lowest a multiple of G) at one index of
+// the other fixed axis, each sample of the G rays reads G consecutive stored
+// voxels of one brick row: one vector load per sample (fp32 two 16-byte loads,
+// bf16 one 16-byte load, fp8 one 8-byte load) instead of G scalar loads with
+// their index arithmetic.  The samples, their positions and values and the
+// order in which each ray takes them are those of the per-ray loop, so every
+// pixel gets the same maximum bit for bit; a group that fails the test takes
+// the per-ray loop.  At native resolution each voxel is read once, and the
+// vector loads leave HBM as the bound for fp32.
+// pixels per thread and samples whose loads are in flight together.
+// Measured on the 1024^3 cube (native z view): fp32 0.678 / bf16 0.409 / fp8
+// 0.435 ms; 16 pixels per thread (fewer threads, 16-byte fp8 loads) 0.472 /
+// 0.656 ms for bf16 / fp8, 8 samples in flight 0.862 / 0.405 / 0.453 ms,
+// 2 samples 0.681 ms for fp32, 4 pixels (16-byte fp32 loads) 0.950 ms.
+constexpr int kRowG = 8;
+constexpr int kRowU = 4;
+
+// G stored voxels of a brick row as 32-bit words (G x esize bytes, 8-byte
+// aligned at least): loaded by 16-byte (or, below 16 bytes, 8-byte) loads
+template <int DT, int G>
+struct RowVec {
+    static constexpr int kBytes = G * (DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 2 : 1));
+    static constexpr int kWords = kBytes / 4;
+    uint32_t w[kWords];
+};
+
+// The loads are volatile asm: each is issued where it stands, ahead of the
+// samples that consume them, so the group's loads are all in flight at once
+// (a compiler free to sink a load next to its use would serialise them).
+template <int DT, int G>
+__device__ __forceinline__ void row_load(const uint8_t *p, RowVec<DT, G> &r)
+{
+    if constexpr (RowVec<DT, G>::kBytes >= 16) {
+#pragma unroll
+        for (int i = 0; i < RowVec<DT, G>::kWords / 4; ++i)
+            asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r.w[4 * i]), "=r"(r.w[4 * i + 1]), "=r"(r.w[4 * i + 2]), "=r"(r.w[4 * i + 3])
+                         : "l"(p + 16 * i));
+    } else {
+        asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(r.w[0]), "=r"(r.w[1]) : "l"(p));
+    }
+}
+
+// Voxel values x = lowest .. lowest + G - 1 (fp8: code values, the brick scale
+// not yet applied), each as raw_voxel reads it.
+template <int DT, int G>
+__device__ __forceinline__ void row_values(const RowVec<DT, G> &r, float v[G])
+{
+#pragma unroll
+    for (int i = 0; i < RowVec<DT, G>::kWords; ++i) {
+        const uint32_t w = r.w[i];
+        if constexpr (DT == VRC_F32) {
+            v[i] = __uint_as_float(w);
+        } else if constexpr (DT == VRC_BF16) {
+            v[2 * i] = __uint_as_float(w << 16);
+            v[2 * i + 1] = __uint_as_float(w & 0xffff0000u);
+        } else {
+            const float2 lo = e4m3x2_to_float2(w & 0xffffu), hi = e4m3x2_to_float2(w >> 16);
+            v[4 * i] = lo.x, v[4 * i + 1] = lo.y, v[4 * i + 2] = hi.x, v[4 * i + 3] = hi.y;
+        }
+    }
+}
+
+// The G rays of pixels (px0 .. px0 + G - 1, py).  Returns false (nothing
+// written) when they do not form a row group as described above.
+template <int DT>
+__device__ __forceinline__ bool mip_row_group(const JobDesc &J, int px0, int py, uint32_t &nsamp)
+{
+    const CubeView &cv = J.cv;
+    if (px0 + kRowG > J.vp.W) return false;
+    float o[3], d[3], tin = 0.f, tout = 0.f;
+    const bool hit = ray_setup(J.vp, cv.fdims, px0, py, o, d, tin, tout);
+    if (d[0] != 0.f || (d[1] != 0.f) == (d[2] != 0.f)) return false;   // rays along y or z only
+    const int m = d[1] != 0.f ? 1 : 2, f = 3 - m;   // moving axis; the fixed axis besides x
+    // (components picked by selects: a runtime index would put the arrays in local memory)
+    const float om = m == 1 ? o[1] : o[2], dm = m == 1 ? d[1] : d[2];
+    const int nm = m == 1 ? cv.dims[1] : cv.dims[2], nf = f == 1 ? cv.dims[1] : cv.dims[2];
+    const int X0 = nearest_index(o[0], cv.dims[0]), F = nearest_index(f == 1 ? o[1] : o[2], nf);
+    int sx = 0;
+#pragma unroll 1
+    for (int i = 1; i < kRowG; ++i) {
+        float oi[3], di[3], ti = 0.f, to = 0.f;
+        const bool hi = ray_setup(J.vp, cv.fdims, px0 + i, py, oi, di, ti, to);
+        const int Xi = nearest_index(oi[0], cv.dims[0]);
+        if (i == 1) sx = Xi - X0;
+        if (hi != hit || (sx != 1 && sx != -1) || Xi != X0 + sx * i || di[0] != d[0] || di[1] != d[1] ||
+            di[2] != d[2])
+            return false;
+        if (hit && (ti != tin || to != tout || (m == 1 ? oi[1] : oi[2]) != om ||
+                    nearest_index(f == 1 ? oi[1] : oi[2], nf) != F))
+            return false;
+    }
+    const int Xlo = sx > 0 ? X0 : X0 - (kRowG - 1);
+    if (hit && (Xlo & (kRowG - 1))) return false;
+    float mx[kRowG];
+#pragma unroll
+    for (int j = 0; j < kRowG; ++j) mx[j] = -FLT_MAX;
+    if (hit) {
+        // brick and in-brick element terms of x and of the other fixed axis;
+        // element of local (lx, ly, lz) = (lz+1) R P + (ly+1) P + lx + O
+        const uint32_t estr_f = f == 1 ? (uint32_t)cv.P : (uint32_t)(cv.R * cv.P);
+        const uint32_t estr_m = m == 1 ? (uint32_t)cv.P : (uint32_t)(cv.R * cv.P);
+        const int bstr_f = f == 1 ? cv.nb[0] : cv.nb[0] * cv.nb[1];
+        const int bstr_m = m == 1 ? cv.nb[0] : cv.nb[0] * cv.nb[1];
+        const uint32_t e_c = (uint32_t)(cv.O + cv.P + cv.R * cv.P) + (uint32_t)(Xlo & (cv.B - 1)) +
+                             (uint32_t)(F & (cv.B - 1)) * estr_f;
+        const int b_c = (Xlo >> cv.logB) + (F >> cv.logB) * bstr_f;
+        const uint8_t *const base = cv.pool + (int64_t)b_c * cv.brick_bytes;
+        const int64_t bstride = (int64_t)bstr_m * cv.brick_bytes;
+        constexpr int es = DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 2 : 1);
+        const float step = J.step;
+        // sample k + u of every ray of the group, as the per-ray loop forms it
+        auto index_of = [&](float kf, int u) {
+            const float tk = __fadd_rn(tin, __fmul_rn(__fadd_rn(kf, (float)u + 0.5f), step));
+            return make_int2(nearest_index(__fadd_rn(om, __fmul_rn(tk, dm)), nm), tk < tout);
+        };
+        for (int k = 0;; k += kRowU) {
+            const float kf = (float)k;
+            RowVec<DT, kRowG> rv[kRowU];
+            int nv = 0;   // t grows with k, so the samples inside the ray form a prefix
+#pragma unroll
+            for (int u = 0; u < kRowU; ++u) {
+                const int2 iv = index_of(kf, u);
+                row_load<DT, kRowG>(base + (iv.x >> cv.logB) * bstride +
+                                 (size_t)(e_c + (uint32_t)(iv.x & (cv.B - 1)) * estr_m) * es,
+                             rv[u]);
+                nv += iv.y;
+            }
+#pragma unroll
+            for (int u = 0; u < kRowU; ++u) {
+                // a sample past the rays' end read an in-bounds voxel (its index is
+                // clamped) and counts as -FLT_MAX, which leaves every maximum as it is
+                const bool in = u < nv;
+                float v[kRowG];
+                row_values<DT, kRowG>(rv[u], v);
+                if (DT == VRC_FP8E4M3) {
+                    // the brick's scale (its index formed again: fewer registers held across the loads)
+                    const float sc = __ldg(cv.scales + b_c + (index_of(kf, u).x >> cv.logB) * bstr_m);
+#pragma unroll
+                    for (int j = 0; j < kRowG; ++j) mx[j] = fmaxf(mx[j], in ? __fmul_rn(v[j], sc) : -FLT_MAX);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kRowG; ++j) mx[j] = fmaxf(mx[j], in ? v[j] : -FLT_MAX);
+                }
+            }
+            nsamp += (uint32_t)(kRowG * nv);
+            if (nv < kRowU) break;
+        }
+    }
+    float *out = J.out + (int64_t)py * J.vp.W + px0;
+#pragma unroll
+    for (int i = 0; i < kRowG; ++i) out[i] = mx[sx > 0 ? i : kRowG - 1 - i];
+    return true;
+}
+
+// One thread per group of kRowG pixels of a row (64 registers, 4 CTAs per SM:
+// a 1024^2 view's 131,072 groups are all resident at once), every view of the launch the
+// same size (groups_x groups per row, groups_per_job per view).
+template <int DT>
+__global__ void __launch_bounds__(kThreads, 4) k_mip_rows(const JobDesc *__restrict__ jobs, int n_jobs,
+                                                      int64_t groups_per_job, int groups_x)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t nsamp = 0, neval = 0;
+    if (g < groups_per_job * n_jobs) {
+        const int jid = (int)(g / groups_per_job);
+        const int64_t r = g - (int64_t)jid * groups_per_job;
+        const JobDesc &J = jobs[jid];
+        const int py = (int)(r / groups_x), px0 = (int)(r - (int64_t)py * groups_x) * kRowG;
+        if (mip_row_group<DT>(J, px0, py, nsamp)) {
+            neval = nsamp;
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < kRowG && px0 + i < J.vp.W; ++i)
+                trace_fused<0, VRC_NEAREST, DT, -1, false>(J, nullptr, px0 + i, py, nsamp, neval);
+        }
+    }
+    if (jobs[0].samples) warp_count2(jobs[0].samples, nsamp, neval);   // every job of the launch shares them
 }
 
 // Sort-last work item: one screen tile of one brick of one view.
@@ -836,21 +1019,49 @@ JobDesc make_job(const Cube *c, const vrc_camera &cam, const vrc_raycfg &rc, int
 }
 
 template <int MODE, int SAMPLING, int DT, bool TEX, bool SKIP>
-int fused_occupancy()
+int fused_occupancy(int nthreads)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fused<MODE, SAMPLING, DT, TEX, SKIP>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_render_fused<MODE, SAMPLING, DT, TEX, SKIP>, nthreads, 0);
     return n > 0 ? n : 1;
 }
 
+// nthreads = the jobs' tile_w x tile_h (one thread per pixel of a tile; 256)
 template <int MODE, int SAMPLING, int DT, bool TEX, bool SKIP>
-void launch_fused_t(int grid, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total, int *counter)
+void launch_fused_t(int grid, int nthreads, cudaStream_t st, const JobDesc *jobs, int n_jobs, int64_t total,
+                    int *counter)
 {
-    k_render_fused<MODE, SAMPLING, DT, TEX, SKIP><<<grid, kThreads, 0, st>>>(jobs, n_jobs, total, counter);
+    k_render_fused<MODE, SAMPLING, DT, TEX, SKIP><<<grid, nthreads, 0, st>>>(jobs, n_jobs, total, counter);
 }
 
-typedef void (*fused_fn)(int, cudaStream_t, const JobDesc *, int, int64_t, int *);
-typedef int (*occ_fn)();
+// Views that the row-group MIP kernel can take: nearest MIP, orthographic,
+// rays along y or z whose coordinate on that axis does not vary over the
+// image, and image x moving along the cube's x axis.  (The kernel checks each
+// group of eight rays itself and takes the per-ray loop where they do not fit.)
+bool rows_views(const std::vector<JobDesc> &jobs, int mode, const vrc_raycfg &rc)
+{
+    if (mode != 0 || rc.sampling != VRC_NEAREST || rc.width < kRowG) return false;
+    for (const JobDesc &j : jobs) {
+        const ViewParams &vp = j.vp;
+        if (vp.kind != VRC_CAM_ORTHO || vp.D0[0] != 0.f || (vp.D0[1] != 0.f) == (vp.D0[2] != 0.f)) return false;
+        const int m = vp.D0[1] != 0.f ? 1 : 2;
+        if (vp.DX[m] != 0.f || vp.DY[m] != 0.f || vp.DX[0] == 0.f) return false;
+    }
+    return true;
+}
+
+void launch_rows(int dt, cudaStream_t st, const JobDesc *jobs, int n_jobs, int W, int H)
+{
+    const int gx = (W + kRowG - 1) / kRowG;
+    const int64_t gpj = (int64_t)gx * H;
+    const unsigned grid = (unsigned)((gpj * n_jobs + kThreads - 1) / kThreads);
+    if (dt == VRC_F32) k_mip_rows<VRC_F32><<<grid, kThreads, 0, st>>>(jobs, n_jobs, gpj, gx);
+    else if (dt == VRC_BF16) k_mip_rows<VRC_BF16><<<grid, kThreads, 0, st>>>(jobs, n_jobs, gpj, gx);
+    else k_mip_rows<VRC_FP8E4M3><<<grid, kThreads, 0, st>>>(jobs, n_jobs, gpj, gx);
+}
+
+typedef void (*fused_fn)(int, int, cudaStream_t, const JobDesc *, int, int64_t, int *);
+typedef int (*occ_fn)(int);
 
 // Variant: nearest reads one voxel; trilinear reads texture gathers when the
 // cubes have texture copies (TEX), optionally with empty-space skipping (SKIP).
@@ -886,9 +1097,10 @@ occ_fn pick_occ2(int sampling, int dt, bool tex, bool skip)
     if (dt == VRC_BF16) return pick_occ3<MODE, VRC_BF16>(sampling, tex, skip);
     return pick_occ3<MODE, VRC_FP8E4M3>(sampling, tex, skip);
 }
-int occupancy(int mode, int sampling, int dt, bool tex, bool skip = false)
+int occupancy(int mode, int sampling, int dt, bool tex, bool skip = false, int nthreads = kThreads)
 {
-    return mode == 0 ? pick_occ2<0>(sampling, dt, tex, skip)() : pick_occ2<1>(sampling, dt, tex, skip)();
+    return mode == 0 ? pick_occ2<0>(sampling, dt, tex, skip)(nthreads)
+                     : pick_occ2<1>(sampling, dt, tex, skip)(nthreads);
 }
 
 template <int MODE, int SAMPLING, int DT, bool TEX>
@@ -1154,7 +1366,8 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
     }
     const bool zerocopy = rc->path == VRC_PATH_ZEROCOPY;
     const bool sortlast = c->streamed || rc->path == VRC_PATH_SORTLAST;
-    ctx->last_path = slab ? VRC_PATH_SLAB
+    const bool rows = !slab && !sortlast && !zerocopy && rows_views(jobs, mode, *rc);
+    ctx->last_path = rows ? VRC_PATH_ROWS : slab ? VRC_PATH_SLAB
                           : (zerocopy ? VRC_PATH_ZEROCOPY
                                       : (c->streamed ? VRC_PATH_STREAMED
                                                      : (sortlast ? VRC_PATH_SORTLAST
@@ -1202,14 +1415,19 @@ vrc_status render_common(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cams, 
                     inject_fire(ctx, VRC_INJECT_SLAB_WAIT));
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
+    } else if (rows) {
+        launch_rows(c->g.dtype, st, djobs, n_views, rc->width, rc->height);
+        count_launch(ctx);
+        VRC_CK(ctx, cudaGetLastError());
     } else if (!sortlast) {
         const bool tex = rc->path == VRC_PATH_FUSED && c->dtex != nullptr;
         const bool skip = tex && jobs[0].cellmax != nullptr;
         int per_sm = ctas_override > 0 ? ctas_override
                                        : (c->ctas_per_sm > 0 ? c->ctas_per_sm
-                                                             : occupancy(mode, rc->sampling, c->g.dtype, tex, skip));
+                                                             : occupancy(mode, rc->sampling, c->g.dtype, tex, skip,
+                                                                         tw * th));
         const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
-        pick_fused(mode, rc->sampling, c->g.dtype, tex, skip)(grid, st, djobs, n_views, total, counter);
+        pick_fused(mode, rc->sampling, c->g.dtype, tex, skip)(grid, tw * th, st, djobs, n_views, total, counter);
         count_launch(ctx);
         VRC_CK(ctx, cudaGetLastError());
     } else if (!c->streamed || zerocopy) {
@@ -1477,7 +1695,8 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
         return cuda_err(ctx, e, "graph upload");
     }
     const bool skip = tex && jobs[0].cellmax != nullptr;
-    const int per_sm = c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype, tex, skip);
+    const int per_sm =
+        c->ctas_per_sm > 0 ? c->ctas_per_sm : occupancy(mode, rc->sampling, c->g.dtype, tex, skip, tw * th);
     const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, total);
     cudaStream_t cs;
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -1489,7 +1708,7 @@ vrc_status vrc_graph_create(vrc_ctx *ctx, int64_t cube_id, const vrc_camera *cam
     if (e == cudaSuccess) {
         cudaMemsetAsync(counter, 0, sizeof(int), cs);
         cudaMemsetAsync(dsamples, 0, 2 * sizeof(unsigned long long), cs);
-        pick_fused(mode, rc->sampling, c->g.dtype, tex, skip)(grid, cs, djobs, n_views, total, counter);
+        pick_fused(mode, rc->sampling, c->g.dtype, tex, skip)(grid, tw * th, cs, djobs, n_views, total, counter);
         e = cudaStreamEndCapture(cs, &gph->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gph->exec, gph->graph, 0);
@@ -1849,7 +2068,7 @@ vrc_status render_hetero(vrc_ctx *ctx, const std::vector<HetJob> &hj, cudaStream
     for (int k = 0; k < nslices; ++k) {
         const int64_t end = std::min<int64_t>(total, (int64_t)(k + 1) * per);
         const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, end - (int64_t)k * per);
-        fn(grid, st, djobs, (int)hj.size(), end, counters + k);
+        fn(grid, kThreads, st, djobs, (int)hj.size(), end, counters + k);
         count_launch(ctx);
     }
     VRC_CK(ctx, cudaGetLastError());

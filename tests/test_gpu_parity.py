@@ -675,3 +675,42 @@ def test_axis_aligned_nearest_mip_every_direction(ctx, dtype):
     for step in (1.0, 0.7):
         render_check_mip(ctx, v, cid, cams, 44, 44, step, "nearest", dtype=dtype, B=B)
     ctx.cube_free(cid)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_row_group_nearest_mip(ctx, dtype):
+    """Orthographic nearest MIP along +-z and +-y at native resolution takes the
+    row-group kernel (8 rays of an image row per thread, one vector load per
+    sample): image x along +x and along -x, a view shifted by 3 voxels
+    (no group aligned: every group takes the per-ray loop), a width that
+    leaves a ragged last group, fp8 scales changing along the ray.  Every pixel
+    equals the oracle's bit for bit, and a view that does not qualify
+    (perspective) in the same call keeps the per-ray kernel."""
+    vrc = vrcmod()
+    dims = (60, 48, 40)
+    B = 16
+    v = cubegen.generate(dims, 6, 67)
+    cid = ctx.cube_upload(v, dtype, brick=B)
+    nx, ny, nz = dims
+    c = (nx / 2, ny / 2, nz / 2)
+    zview = [cubegen.ortho_z_camera(dims),
+             cubegen.camera("ortho", (c[0], c[1], nz + 5.0), c, (0, -1, 0), ortho_height=float(ny)),   # x reversed
+             cubegen.camera("ortho", (c[0] + 3.0, c[1], -5.0), (c[0] + 3.0, c[1], 0.0), (0, -1, 0),
+                            ortho_height=float(ny))]                                                  # shifted
+    yview = [cubegen.camera("ortho", (c[0], -5.0, c[2]), c, (0, 0, 1), ortho_height=float(nz)),
+             cubegen.camera("ortho", (c[0], ny + 5.0, c[2]), c, (0, 0, 1), ortho_height=float(nz))]
+    for cams, W, H in ((zview, nx, ny), (yview, nx, nz)):
+        for step in (1.0, 0.7):
+            render_check_mip(ctx, v, cid, cams, W, H, step, "nearest", dtype=dtype, B=B)
+            assert ctx.last_render_path() == "rows"
+            assert ctx.last_render_samples() > 0
+    # 48-pixel-wide z views over x = 0 .. 47 (every group full and aligned), image x along +x and -x
+    cam48 = [cubegen.camera("ortho", (24.0, c[1], -5.0), (24.0, c[1], 0.0), (0, -1, 0), ortho_height=float(ny)),
+             cubegen.camera("ortho", (24.0, c[1], nz + 5.0), (24.0, c[1], 0.0), (0, -1, 0), ortho_height=float(ny))]
+    got = render_check_mip(ctx, v, cid, cam48, 48, ny, 1.0, "nearest", dtype=dtype, B=B)
+    assert ctx.last_render_path() == "rows"
+    assert np.array_equal(got[0].reshape(ny, 48), got[1].reshape(ny, 48)[:, ::-1])
+    mixed = [zview[0], cubegen.orbit_cameras(dims, 4)[1]]
+    render_check_mip(ctx, v, cid, mixed, nx, ny, 1.0, "nearest", dtype=dtype, B=B)
+    assert ctx.last_render_path() == "fused_ldg"
+    ctx.cube_free(cid)
