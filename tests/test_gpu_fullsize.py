@@ -139,7 +139,8 @@ def test_fullsize_trilinear_mip(full):
 def test_fullsize_precision_storage(full, dtype):
     """The bench cube stored as bf16 / fp8 e4m3 (per-brick scale) in 256^3
     bricks: statistics over all 2^30 stored values against the oracle on the
-    dequantised cube (min/max, histogram and median exact, mean/std 1e-9), sampled
+    dequantised cube (min/max, histogram and median exact, mean/std 1e-9), the
+    native-resolution nearest MIP equal to the stored column maxima, sampled
     pixels of DVR and trilinear MIP renders at the fp32 tolerances."""
     import paper_1111_6661_b300 as vrc
     w, v, cams, tf, ctx, _ = full
@@ -155,7 +156,13 @@ def test_fullsize_precision_storage(full, dtype):
         assert np.array_equal(h, oracle.histogram(dq, ref["min"], ref["max"], 1024))
         k = (dq.size - 1) // 2
         assert ctx.cube_median(cid) == float(np.partition(dq.reshape(-1), k)[k])
-        del dq
+        # native-resolution orthographic nearest MIP (row-group kernel): the stored column maxima
+        NX, NY, NZ = w["dims"]
+        nat = ctx.render_mip(cid, [cubegen.ortho_z_camera(w["dims"])], vrc.raycfg(NX, NY, 1.0, "nearest"))
+        torch.cuda.synchronize()
+        assert ctx.last_render_path() == "rows" and ctx.last_render_samples() == v.size
+        assert np.array_equal(nat[0].cpu().numpy(), dq.max(axis=0))
+        del dq, nat
         info = ctx.cube_info(cid)
         W, H = w["W"], w["H"]
         views = [cams[3], cams[20]]
