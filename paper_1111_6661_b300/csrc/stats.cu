@@ -474,14 +474,15 @@ __global__ void k_stats_final(const StatPartial *__restrict__ p, int nparts, flo
 
 // ----------------------------------------------------------------- median
 
-// Order-preserving map from float bits to uint32 (negative values reversed).
+// Order-preserving map from float bits to uint32 (negative values reversed);
+// the FP8 passes apply it to 0 for both zeros.
 __device__ __forceinline__ uint32_t ord_key(float x)
 {
     const uint32_t u = __float_as_uint(x);
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// One radix-selection pass over the finite stored values: keys k = ord_key(x)
+// One radix-selection pass over the finite stored values: keys k = sel_key(x)
 // whose bits above `shift + nbits` equal `prefix` are counted by their digit
 // (k >> shift) & (2^nbits - 1).  Counters live in shared memory per block and
 // are added to the global histogram once per block (a global atomic per voxel
@@ -497,11 +498,29 @@ struct SelArgs {
     uint32_t prefix;               // required value of k >> (shift + nbits)
     unsigned long long *hist;      // device [2^nbits], zeroed by the caller
     int64_t brick0, nrun;          // the pool holds bricks brick0 .. brick0 + nrun - 1 of the cube
+    uint32_t *keys;                // not null: the keys counted by this pass are also appended here
+    unsigned int *nkeys;           // keys appended so far (zeroed by the caller)
+    uint32_t key_cap;              // room in `keys`
 };
 
 constexpr int kSelMaxBins = 4096;
+// Candidates of the float32 median kept for its last pass (4 bytes each), and
+// the key slots a warp reserves at a time
+constexpr uint32_t kMaxMedianCandidates = 1u << 26;
+constexpr unsigned kKeyChunk = 256;
 
-template <int DT>
+// Order-preserving key of a stored value for the radix passes: u ^ (sign ?
+// 0xffffffff : 0x80000000).  -0 gets the key just below +0's and no value lies
+// between them, so an order statistic that falls among the zeros is 0 either
+// way (-0 and +0 are one value).
+__device__ __forceinline__ uint32_t sel_key(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    return u ^ (uint32_t)(((int32_t)u >> 31) | (int32_t)0x80000000);
+}
+
+// FIRST: the first pass (no prefix condition; digit = the key's top a.nbits bits).
+template <int DT, bool FIRST>
 __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(SelArgs a)
 {
     __shared__ uint32_t sh[kSelMaxBins];
@@ -521,6 +540,16 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(
     const uint32_t Pb = (uint32_t)(g.P * g.esize), RPb = (uint32_t)g.R * Pb, Ob = (uint32_t)(g.O * g.esize);
     const uint32_t dmask = (uint32_t)nb - 1u;
     const int hshift = a.shift + a.nbits;
+    // byte offsets of this lane's vectors after its chunk's first row, when the
+    // chunk's rows lie in one slice (as in the statistics pass)
+    const bool one_slice = logRPC <= g.logB;
+    uint32_t loff[kVecPerLane];
+#pragma unroll
+    for (int i = 0; i < kVecPerLane; ++i) {
+        const uint32_t j = lane + 32 * i;
+        loff[i] = (j >> logVPR) * Pb + Ob + ((j & ((1u << logVPR) - 1)) << 4);
+    }
+    unsigned wpos = 0, wend = 0;   // this warp's reserved key slots [wpos, wend)
     for (int64_t ch = warp0; ch < total_chunks; ch += nwarps) {
         const uint32_t pb = (uint32_t)(ch >> logCPB);          // brick slot in the pool
         const uint32_t b = pb + (uint32_t)a.brick0;            // brick of the cube
@@ -540,13 +569,19 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(
         const uint8_t *bp = a.pool + (uint64_t)pb * (uint64_t)g.brick_bytes;
         const float scale = DT == VRC_FP8E4M3 ? __ldg(a.scales + b) : 1.f;
         uint4 raw[kVecPerLane];
+        if (one_slice) {
+            const uint32_t rb = ((lr0 >> g.logB) + 1) * RPb + ((lr0 & (g.B - 1)) + 1) * Pb;
 #pragma unroll
-        for (int i = 0; i < kVecPerLane; ++i) {
-            const uint32_t j = lane + 32 * i;
-            const uint32_t lr = lr0 + (j >> logVPR);
-            const uint32_t off = ((lr >> g.logB) + 1) * RPb + ((lr & (g.B - 1)) + 1) * Pb + Ob +
-                                 ((j & ((1u << logVPR) - 1)) << 4);
-            raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + off));
+            for (int i = 0; i < kVecPerLane; ++i) raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + rb + loff[i]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < kVecPerLane; ++i) {
+                const uint32_t j = lane + 32 * i;
+                const uint32_t lr = lr0 + (j >> logVPR);
+                const uint32_t off = ((lr >> g.logB) + 1) * RPb + ((lr & (g.B - 1)) + 1) * Pb + Ob +
+                                     ((j & ((1u << logVPR) - 1)) << 4);
+                raw[i] = __ldcs(reinterpret_cast<const uint4 *>(bp + off));
+            }
         }
 #pragma unroll
         for (int i = 0; i < kVecPerLane; ++i) {
@@ -567,13 +602,60 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsCtasPerSm) k_select_hist(
                 nvalid = (int)min((int64_t)VE, g.dims[0] - gx0);
                 if (gy >= g.dims[1] || gz >= g.dims[2] || nvalid < 0) nvalid = 0;
             }
+            uint32_t kk[VE];
+            bool mm[VE], any = false;
 #pragma unroll
             for (int e = 0; e < VE; ++e) {
-                if (!clean && (e >= nvalid || !(fabsf(x[e]) <= FLT_MAX))) continue;
-                const uint32_t k = ord_key(x[e] == 0.f ? 0.f : x[e]);   // -0 and +0 are one value
-                if (a.prefix_all || (k >> hshift) == a.prefix) atomicAdd(&sh[(k >> a.shift) & dmask], 1u);
+                const bool ok = clean || (e < nvalid && fabsf(x[e]) <= FLT_MAX);
+                kk[e] = sel_key(x[e]);
+                mm[e] = ok && (FIRST || (kk[e] >> hshift) == a.prefix);
+                if (mm[e]) atomicAdd(&sh[FIRST ? (kk[e] >> a.shift) : ((kk[e] >> a.shift) & dmask)], 1u);
+                any = any || mm[e];
+            }
+            // the warp's matching keys appended into slots it reserved kKeyChunk at
+            // a time (one global atomic per chunk: a single counter bumped per
+            // match serialises in L2); matches are rare, so one vote per vector
+            // skips the vectors where no lane matched (the warp is converged
+            // here).  Slots a warp leaves unused keep the caller's key 0, which
+            // no finite value's key has.
+            if (a.keys && __any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int e = 0; e < VE; ++e) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, mm[e]);
+                    const unsigned n = (unsigned)__popc(bal);
+                    if (n == 0) continue;
+                    if (wpos + n > wend) {
+                        unsigned base = 0;
+                        if (lane == 0) base = atomicAdd(a.nkeys, kKeyChunk);
+                        wpos = __shfl_sync(0xffffffffu, base, 0);
+                        wend = wpos + kKeyChunk;
+                    }
+                    const unsigned i = wpos + (unsigned)__popc(bal & ((1u << lane) - 1u));
+                    if (mm[e] && i < a.key_cap) a.keys[i] = kk[e];
+                    wpos += n;
+                }
             }
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (sh[i]) atomicAdd(&a.hist[i], (unsigned long long)sh[i]);
+}
+
+// Radix-selection pass over keys appended by an earlier pass (the candidates
+// that share the selected leading digit): the digit histogram of those whose
+// bits above `shift + nbits` equal `prefix`.
+__global__ void __launch_bounds__(kStatsThreads) k_select_keys(const uint32_t *__restrict__ keys, uint32_t n, SelArgs a)
+{
+    __shared__ uint32_t sh[kSelMaxBins];
+    const int nb = 1 << a.nbits;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint32_t dmask = (uint32_t)nb - 1u;
+    const int hshift = a.shift + a.nbits;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        if ((k >> hshift) == a.prefix) atomicAdd(&sh[(k >> a.shift) & dmask], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
@@ -870,13 +952,16 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     a.hist = dh;
     a.brick0 = 0;
     a.nrun = c->g.nbricks;
+    a.keys = nullptr;
+    a.nkeys = nullptr;
+    a.key_cap = 0;
     if (c->streamed &&
         (s = stage_h2d(ctx, st, {{c->bnonfinite, c->h_bnonfinite.data(), sizeof(int32_t) * (size_t)c->g.nbricks}})) !=
             VRC_OK)
         return s;
     int occ = 1;
-    if (c->g.dtype == VRC_F32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_F32>, kStatsThreads, 0);
-    else if (c->g.dtype == VRC_BF16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_BF16>, kStatsThreads, 0);
+    if (c->g.dtype == VRC_F32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_F32, true>, kStatsThreads, 0);
+    else if (c->g.dtype == VRC_BF16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_select_hist<VRC_BF16, true>, kStatsThreads, 0);
     const int grid = ctx->sm_count * std::max(occ, 1);
     // three digits of the 32-bit ordered key: 12, 10 and 10 bits
     const int shifts[3] = {20, 10, 0}, widths[3] = {12, 10, 10};
@@ -886,14 +971,56 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     // key's are 0 for positive values and 1 for negative ones): two passes fix
     // bits 31..10 and with them the value
     const int npass = c->g.dtype == VRC_BF16 ? 2 : 3;
+    // float32: the second pass also appends the keys of its candidates (those
+    // in the first digit's selected bin, whose number the first pass gave), so
+    // the third pass reads them instead of the cube (when at most
+    // kMaxMedianCandidates and their buffer fits the budget; else it reads the
+    // cube again)
+    uint32_t ncand = 0;
+    unsigned int hk = 0;
+    uint64_t prev_count = 0;   // keys in the digit bin the previous pass selected
+    struct CandBuf {   // device buffer of the candidates' keys; released once `st` has finished with it
+        vrc_ctx *ctx;
+        cudaStream_t st;
+        void *p = nullptr;
+        size_t n = 0;
+        ~CandBuf()
+        {
+            if (!p) return;
+            cudaStreamSynchronize(st);
+            dev_free(ctx, p, n);
+        }
+    } cand{ctx, st};
     for (int pass = 0; pass < npass; ++pass) {
         a.shift = shifts[pass];
         a.nbits = widths[pass];
         a.prefix_all = pass == 0;
         a.prefix = pass == 0 ? 0u : key >> (a.shift + a.nbits);
         const int nb = 1 << a.nbits;
+        const bool from_keys = pass == 2 && a.keys != nullptr;
+        if (pass == 1 && npass == 3 && !codes && ncand > 0 && ncand <= kMaxMedianCandidates) {
+            // room for the candidates, the chunk tails the warps leave (under 1/8)
+            // and one open chunk per warp and launch
+            const uint64_t warps = (uint64_t)grid * (kStatsThreads / 32);
+            const uint64_t cap = (uint64_t)ncand + ncand / 8 + (uint64_t)kKeyChunk * (warps + 1);
+            cand.n = 16 + (size_t)cap * sizeof(uint32_t);
+            if (dev_alloc(ctx, &cand.p, cand.n) == VRC_OK) {
+                a.nkeys = reinterpret_cast<unsigned int *>(cand.p);
+                a.keys = reinterpret_cast<uint32_t *>((char *)cand.p + 16);
+                a.key_cap = (uint32_t)cap;
+                VRC_CK(ctx, cudaMemsetAsync(cand.p, 0, cand.n, st));   // count 0, every slot key 0
+            } else {
+                cand.p = nullptr;   // no room: the third pass reads the cube again
+            }
+        }
         VRC_CK(ctx, cudaMemsetAsync(dh, 0, nb * sizeof(unsigned long long), st));
-        if (codes) {
+        if (from_keys) {
+            SelArgs r = a;
+            r.keys = nullptr;
+            k_select_keys<<<(unsigned)std::min<int64_t>((hk + 255) / 256, grid), kStatsThreads, 0, st>>>(a.keys, hk,
+                                                                                                       r);
+            count_launch(ctx);
+        } else if (codes) {
             k_select_codes<<<(unsigned)std::min<int64_t>((nentries + 255) / 256, grid), 256, 0, st>>>(
                 table, c->scales, nentries, a);
             count_launch(ctx);
@@ -904,20 +1031,45 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
                 r.pool = pool;
                 r.brick0 = b0;
                 r.nrun = n;
-                k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(r);
+                if (pass == 0) k_select_hist<VRC_F32, true><<<grid, kStatsThreads, 0, st>>>(r);
+                else k_select_hist<VRC_F32, false><<<grid, kStatsThreads, 0, st>>>(r);
                 count_launch(ctx);
                 const cudaError_t e = cudaGetLastError();
                 return e == cudaSuccess ? VRC_OK : cuda_err(ctx, e, "median run");
             });
             if (s != VRC_OK) return s;
         } else {
-            if (c->g.dtype == VRC_F32) k_select_hist<VRC_F32><<<grid, kStatsThreads, 0, st>>>(a);
-            else k_select_hist<VRC_BF16><<<grid, kStatsThreads, 0, st>>>(a);
+            if (c->g.dtype == VRC_F32) {
+                if (pass == 0) k_select_hist<VRC_F32, true><<<grid, kStatsThreads, 0, st>>>(a);
+                else k_select_hist<VRC_F32, false><<<grid, kStatsThreads, 0, st>>>(a);
+            } else {
+                if (pass == 0) k_select_hist<VRC_BF16, true><<<grid, kStatsThreads, 0, st>>>(a);
+                else k_select_hist<VRC_BF16, false><<<grid, kStatsThreads, 0, st>>>(a);
+            }
             count_launch(ctx);
         }
         VRC_CK(ctx, cudaGetLastError());
         VRC_CK(ctx, cudaMemcpyAsync(h.data(), dh, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        if (pass == 1 && a.keys)
+            VRC_CK(ctx, cudaMemcpyAsync(&hk, a.nkeys, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
         VRC_CK(ctx, cudaStreamSynchronize(st));
+        if (pass == 1 && a.keys && hk > a.key_cap) {
+            // more slots reserved than the buffer holds: the third pass reads the cube
+            a.keys = nullptr;
+            a.nkeys = nullptr;
+            a.key_cap = 0;
+        }
+        if (from_keys) {
+            uint64_t got = 0;
+            for (int i = 0; i < nb; ++i) got += h[i];
+            if (got != prev_count) {
+                // the kept keys do not hold every key of the selected bin: this pass
+                // again, over the cube
+                a.keys = nullptr;
+                --pass;
+                continue;
+            }
+        }
         if (pass == 0) {
             uint64_t total = 0;
             for (int i = 0; i < nb; ++i) total += h[i];
@@ -934,6 +1086,8 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
             acc += h[i];
         }
         if (sel < 0) return set_err(ctx, VRC_E_CUDA, "median selection inconsistent");
+        if (pass == 0) ncand = h[sel] <= 0xffffffffull ? (uint32_t)h[sel] : 0u;
+        prev_count = h[sel];
         rank -= acc;
         key |= (uint32_t)sel << a.shift;
     }

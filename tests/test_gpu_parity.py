@@ -135,6 +135,22 @@ def test_median_special_values(ctx):
     ctx.cube_free(cid)
 
 
+def test_median_candidates_kept_or_not(ctx):
+    """Float32 medians keep the keys that share the median's leading 12-bit
+    digit for their last pass; more than 2^26 such keys (here 84 M voxels in
+    [1, 1.125), one digit) make the last pass read the cube again.  Both give
+    the oracle's lower median."""
+    rng = np.random.default_rng(9)
+    v = (1.0 + 0.124 * rng.random((320, 512, 512))).astype(np.float32)
+    cid = ctx.cube_upload(v, "f32", brick=256)
+    assert ctx.cube_median(cid) == oracle.median(v)
+    ctx.cube_free(cid)
+    w = v[:64, :256, :256].copy()             # 4 M candidates: kept
+    cid = ctx.cube_upload(w, "f32", brick=64)
+    assert ctx.cube_median(cid) == oracle.median(w)
+    ctx.cube_free(cid)
+
+
 # ------------------------------------------------------------------ rendering
 def render_check_mip(ctx, v, cid, cams, W, H, step, sampling, dtype="f32", B=0, path="fused"):
     vrc = vrcmod()
