@@ -380,9 +380,12 @@ vrc_status vrc_cube_stats_noalloc(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, 
  * Median of the finite stored values (Sec. 3: a global task needing all data):
  * the lower median, value of rank floor((n-1)/2) in ascending order.  Exact:
  * radix selection on the order-preserving 32-bit keys of the values (-0 and +0
- * are one value), three passes over the cube counting 12, 10 and 10 key bits
- * in shared-memory histograms; each pass keeps the keys whose leading bits
- * match the digits chosen so far.  FP8 cubes take one pass over the cube that
+ * are one value), three passes counting 12, 10 and 10 key bits in
+ * shared-memory histograms; each pass counts the keys whose leading bits match
+ * the digits chosen so far.  Float32 cubes: the second pass also keeps the keys
+ * of the first pass's selected bin in a device buffer (allocated for the call
+ * when they number at most 2^26 and the budget allows; otherwise the third
+ * pass reads the cube again), and the third pass reads those.  FP8 cubes take one pass over the cube that
  * counts each brick's 8-bit codes; the three radix passes then run over the
  * (brick, code) entries weighted by their counts (a stored fp8 value depends
  * only on its brick's scale and its code).  bf16 keys have 16 significant
