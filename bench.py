@@ -500,6 +500,8 @@ def run_gpu(args, w):
         ctx.cube_free(cid)
     ctx.close()   # the serving contexts below need the device memory this one caches
     serving = serving_forms(args) if (not args.no_serving and rank == 0) else None
+    serving_budget = (serving_budget_forms(args) if (not args.no_serving and not args.no_serving_budget and rank == 0)
+                      else None)
 
     # the committed captures are of the default step (fp32 cube, fused path, 32 views)
     profiled = w["name"] == "dvr1024" and w["storage"] == "f32" and args.path == "fused" and len(cams) == 32
@@ -519,7 +521,8 @@ def run_gpu(args, w):
                              "peak_kind": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
                              "binding": render_binding() if profiled else None},
                 "frames_per_s": len(cams) / (render_ms / 1e3), "render_path": render_path,
-                "precision_forms": precision, "serving_forms": serving, "skip_empty_variant": skip,
+                "precision_forms": precision, "serving_forms": serving, "serving_budget_forms": serving_budget,
+                "skip_empty_variant": skip,
                 "view_latency": view_latency, "mip_native": mip_native,
                 "kernels": {"render_ms": render_ms, "stats_ms": stats_ms, "median_ms": median_ms,
                             "stats_hbm_gbs": stats_gbs, "stats_hbm_frac": stats_gbs / pk["hbm_gbs"],
@@ -654,6 +657,47 @@ def serving_forms(args):
     out["workload"] = ("Poisson 200 requests/s for %.0f s (%d requests), 64 cubes 256^3-1024^3 (one generated volume "
                        "per side), resident set, 50%% DVR / 30%% MIP / 20%% statistics, 512^2-1920x1080"
                        % (args.serving_seconds, len(wl["requests"])))
+    return out
+
+
+def serving_budget_forms(args):
+    """cfg4 serving under the HBM budget: the same stream over the 64 cubes
+    registered (kept on the host, made resident on demand, least recently used
+    evicted) under 32 GiB, every cube stored as fp32, bf16 and fp8 in turn.
+    The budget holds a few of the cubes, so most requests wait for an upload:
+    bf16 / fp8 cubes load from their packed host copies (half / a quarter of
+    the bytes) and more of them fit."""
+    import torch
+
+    import cubegen
+    import paper_1111_6661_b300 as vrc
+    wl = cubegen.serving_stream(seed=5, rate_hz=200.0, duration_s=args.serving_budget_seconds, n_cubes=64)
+    out, vols = {}, {}
+    for dt in ("f32", "bf16", "fp8"):
+        for c in wl["cubes"]:
+            c["dtype"] = dt
+        ctx = vrc.Context(0, hbm_budget_bytes=32 * 2 ** 30, n_streams=4, max_inflight=32)
+        ids = []
+        t0 = time.perf_counter()
+        for c in wl["cubes"]:
+            if c["dims"] not in vols:
+                vols[c["dims"]] = cubegen.generate(c["dims"], c["n_sources"], c["seed"])
+            ids.append(ctx.cube_register(vols[c["dims"]], dt, brick=128 if c["dims"][0] <= 512 else 256))
+        setup = time.perf_counter() - t0
+        r = serving_run(ctx, wl, ids)
+        r["setup_s"] = setup
+        r["residency_counts"] = ctx.residency()
+        out[dt] = r
+        for i in ids:
+            ctx.cube_free(i)
+        ctx.close()
+        torch.cuda.empty_cache()
+    for dt in ("bf16", "fp8"):
+        out[dt]["beats_fp32_p99"] = out[dt]["p99_ms"] < out["f32"]["p99_ms"]
+        out[dt]["beats_fp32_samples_per_s"] = out[dt]["samples_per_s"] > out["f32"]["samples_per_s"]
+    out["workload"] = ("Poisson 200 requests/s for %.0f s (%d requests), 64 registered cubes 256^3-1024^3 (one "
+                       "generated volume per side) under a 32 GiB HBM budget, 50%% DVR / 30%% MIP / 20%% statistics, "
+                       "512^2-1920x1080" % (args.serving_budget_seconds, len(wl["requests"])))
     return out
 
 
@@ -1117,6 +1161,9 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the bf16/fp8 forms of the default step")
     ap.add_argument("--no-serving", action="store_true", help="skip the bounded serving run per storage type")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
+    ap.add_argument("--no-serving-budget", action="store_true",
+                    help="skip the serving run of registered cubes under the 32 GiB budget")
+    ap.add_argument("--serving-budget-seconds", type=float, default=6.0)
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling)")
     ap.add_argument("--dims", type=int, nargs=3, default=None, help="precision/ooc: cube dims")
     ap.add_argument("--error-pixels", type=int, default=4096)

@@ -195,22 +195,30 @@ vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device
 #define VRC_COPY_MASK     0x300
 
 /*
- * Register a cube without making it resident (Abstract, Sec. 3: a shared,
+ * Register a cube without keeping it resident (Abstract, Sec. 3: a shared,
  * multi-user service holds many users' cubes; on one GPU it keeps as many
  * resident as its HBM budget allows).  src: caller-owned HOST array of
- * nx*ny*nz floats, x fastest, that must stay valid and unchanged until
- * vrc_cube_free.  storage and brick as for vrc_cube_upload (the render copy is
- * made unless VRC_COPY_NONE is given).  The array is page-locked
- * (cudaHostRegister) until vrc_cube_free when it is not page-locked already, so
- * that uploads run at the host link's speed.  No device memory is used until
- * the cube is needed.  The serving loop admits a request for a registered cube once the
+ * nx*ny*nz floats, x fastest.  storage and brick as for vrc_cube_upload (the
+ * render copy is made unless VRC_COPY_NONE is given).
+ *   VRC_F32: src must stay valid and unchanged until vrc_cube_free; it is
+ *   page-locked (cudaHostRegister) until then when it is not page-locked
+ *   already, so that uploads run at the host link's speed, and no device
+ *   memory is used until the cube is needed.
+ *   VRC_BF16 / VRC_FP8E4M3: the call packs the cube once (the upload passes,
+ *   on the device, evicting idle registered cubes if the budget needs it) and
+ *   keeps its packed bricks and brick scales in page-locked host memory (half
+ *   / a quarter of the source's bytes) until vrc_cube_free; every later load
+ *   copies those, and src is not read after the call returns.  The cube is
+ *   resident when the call returns.  If no page-locked host memory can be had
+ *   the cube falls back to the VRC_F32 rules for src.
+ * The serving loop admits a request for a registered cube once the
  * cube is resident: it uploads it (the vrc_cube_upload passes, on a loader
  * thread) as soon as the memory the upload needs fits the budget, evicting
  * registered cubes that no queued or running request references, least
  * recently used first; until then the request waits in the queue
  * (vrc_result.memory_wait_ms).  A direct call (render, statistics, median,
  * brick read) on a registered cube makes it resident first, on the calling
- * thread.  Errors: VRC_E_INVAL.
+ * thread.  Errors: VRC_E_INVAL; VRC_E_NOMEM (bf16 / fp8: no room to pack).
  */
 vrc_status vrc_cube_register(vrc_ctx *ctx, const float *src, int64_t nx, int64_t ny, int64_t nz, int32_t storage,
                              int32_t brick, int64_t *cube_id);

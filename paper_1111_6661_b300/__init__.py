@@ -126,7 +126,8 @@ class Context:
     def cube_register(self, src: np.ndarray, storage: str = "f32", brick: int = 0, render_copy: str = "auto") -> int:
         """Register a host cube (float32 numpy array (sz, sy, sx)) that the
         library makes resident only while it is needed; the array is kept
-        referenced until cube_free."""
+        referenced until cube_free.  bf16 / fp8 cubes are packed once here and
+        load from their packed host copy afterwards."""
         assert isinstance(src, np.ndarray) and src.dtype == np.float32 and src.flags.c_contiguous and src.ndim == 3
         cid = ctypes.c_int64()
         self._check(self._lib.vrc_cube_register(self.h, ctypes.c_void_p(src.ctypes.data), src.shape[2], src.shape[1],

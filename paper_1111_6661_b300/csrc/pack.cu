@@ -722,6 +722,7 @@ void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
     release_device(ctx, c, sync);
     if (c->host_pool) cudaFreeHost(c->host_pool);
     if (c->host_pinned) cudaHostUnregister((void *)c->host_src);
+    if (c->host_packed) cudaFreeHost(c->host_packed);
     for (cudaEvent_t e : c->slot_ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -918,6 +919,76 @@ vrc_status upload_cube(vrc_ctx *ctx, Cube *c, const float *src, int32_t src_on_d
     return VRC_OK;
 }
 
+namespace {
+
+// Resident bricks of a registered cube from its packed host copy: the bricks,
+// brick scales and extrema are copied (the host kept them since the
+// registration), the macro-cell maxima and the render copy are rebuilt on the
+// device.  On failure every device allocation of c is given back.
+vrc_status upload_packed(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    VRC_CK(ctx, cudaSetDevice(ctx->device));
+    vrc_status s = dev_alloc(ctx, &c->pool, g.nbricks * g.brick_bytes);
+    if (s == VRC_OK) s = alloc_meta(ctx, c);
+    if (s == VRC_OK) s = alloc_cellmax(ctx, c);
+    bool tex = false;
+    if (s == VRC_OK && c->copy_mode == VRC_COPY_REQUIRED) tex = (s = alloc_textures(ctx, c)) == VRC_OK;
+    const int64_t nb4 = g.nbricks * 4;
+    auto h2d = [&](void *dst, const void *src, size_t n) {
+        if (s != VRC_OK) return;
+        const cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) s = cuda_err(ctx, e, "packed cube H2D");
+    };
+    h2d(c->pool, c->host_packed, (size_t)(g.nbricks * g.brick_bytes));
+    h2d(c->scales, c->h_scales.data(), nb4);
+    h2d(c->bmin, c->h_bmin.data(), nb4);
+    h2d(c->bmax, c->h_bmax.data(), nb4);
+    h2d(c->bnonfinite, c->h_bnonfinite.data(), nb4);
+    if (s == VRC_OK) s = launch_cellmax(ctx, c, st);
+    if (s == VRC_OK && tex) s = launch_textures(ctx, c, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (s == VRC_OK && e != cudaSuccess) s = cuda_err(ctx, e, "packed cube upload");
+    if (s != VRC_OK) {
+        release_device(ctx, c, true);
+        return s;
+    }
+    c->charged = g.nbricks * g.brick_bytes + 16 * g.nbricks;
+    return VRC_OK;
+}
+
+// Keep the packed bricks and scales of a resident bf16 / fp8 cube in
+// page-locked host memory.  False (nothing kept) when the host memory cannot
+// be had or a copy fails.
+bool save_packed(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+{
+    const BrickGeom &g = c->g;
+    const size_t n = (size_t)(g.nbricks * g.brick_bytes);
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, n, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    c->h_scales.resize(g.nbricks);
+    if (cudaMemcpyAsync(h, c->pool, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->h_scales.data(), c->scales, g.nbricks * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        return false;
+    }
+    c->host_packed = h;
+    return true;
+}
+
+}  // namespace
+
+vrc_status load_registered(vrc_ctx *ctx, Cube *c, cudaStream_t st)
+{
+    if (c->host_packed) return upload_packed(ctx, c, st);
+    return upload_cube(ctx, c, c->host_src, 0, st);
+}
+
 extern "C" {
 
 vrc_status vrc_cube_upload(vrc_ctx *ctx, const float *src, int32_t src_on_device, int64_t nx, int64_t ny,
@@ -969,11 +1040,40 @@ vrc_status vrc_cube_register(vrc_ctx *ctx, const float *src, int64_t nx, int64_t
     // page-lock the caller's array so that uploads copy at the link's speed;
     // an array already page-locked (by the caller or another registration) is
     // used as it is, and a failure only makes uploads slower
-    if (cudaSetDevice(ctx->device) == cudaSuccess &&
-        cudaHostRegister((void *)src, (size_t)(nx * ny * nz) * sizeof(float), cudaHostRegisterPortable) == cudaSuccess)
-        c->host_pinned = true;
-    else
-        cudaGetLastError();
+    auto pin = [&] {
+        if (cudaSetDevice(ctx->device) == cudaSuccess &&
+            cudaHostRegister((void *)src, (size_t)(nx * ny * nz) * sizeof(float), cudaHostRegisterPortable) ==
+                cudaSuccess)
+            c->host_pinned = true;
+        else
+            cudaGetLastError();
+    };
+    if (g.dtype == VRC_F32) {
+        pin();
+    } else {
+        // bf16 / fp8: packed once now; the packed bricks (half / a quarter of
+        // the source's bytes) stay in page-locked host memory and every later
+        // load copies them, so the caller's array is not read again
+        vrc_status s = VRC_OK;
+        {
+            std::unique_lock<std::mutex> lk(ctx->res_mu);
+            if (!evict_for(ctx, upload_peak_bytes(c), c))
+                s = set_err(ctx, VRC_E_NOMEM, "budget: no room to pack the registered cube");
+            if (s == VRC_OK) s = upload_cube(ctx, c, src, 0, nullptr);
+            if (s == VRC_OK) {
+                c->state.store(CUBE_RESIDENT);
+                c->loads = 1;
+                c->last_use = host_ms();
+            }
+        }
+        if (s != VRC_OK) {
+            release_cube(ctx, c, true);
+            return s;
+        }
+        // (the one copy of the source ran from pageable memory: page-locking a
+        // large array costs more than that copy saves)
+        if (!save_packed(ctx, c, nullptr)) pin();   // no packed copy: loads read src as for float32
+    }
     *cube_id = register_cube(ctx, c);
     return VRC_OK;
 }
@@ -1259,8 +1359,10 @@ int64_t upload_peak_bytes(const Cube *c)
     int64_t n = g.nbricks * g.brick_bytes + slack;                 // bricks
     n += 5 * (g.nbricks * 4 + slack);                              // per-brick metadata
     n += cells * 4 + slack;                                        // macro-cell maxima
-    n += g.dims[0] * g.dims[1] * g.dims[2] * 4 + slack;            // staging of the source
-    n += g.nbricks * 4096 + slack;                                 // scan partials
+    if (!c->host_packed) {
+        n += g.dims[0] * g.dims[1] * g.dims[2] * 4 + slack;        // staging of the source
+        n += g.nbricks * 4096 + slack;                             // scan partials
+    }
     if (c->copy_mode != VRC_COPY_NONE) {
         const int64_t tex_esize = g.dtype == VRC_F32 ? 4 : 2 * g.esize;
         const int64_t layers = g.dtype == VRC_F32 ? g.R : g.R - 1;
@@ -1322,7 +1424,7 @@ vrc_status acquire_cube(vrc_ctx *ctx, int64_t id, cudaStream_t st, Cube **out, C
                                (long long)id);
             c->state.store(CUBE_LOADING);
             lk.unlock();
-            const vrc_status s = upload_cube(ctx, c, c->host_src, 0, st);
+            const vrc_status s = load_registered(ctx, c, st);
             lk.lock();
             c->state.store(s == VRC_OK ? CUBE_RESIDENT : CUBE_ABSENT);
             if (s != VRC_OK) return s;

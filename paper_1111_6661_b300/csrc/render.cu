@@ -1036,8 +1036,10 @@ void launch_fused_t(int grid, int nthreads, cudaStream_t st, const JobDesc *jobs
 
 // Views that the row-group MIP kernel can take: nearest MIP, orthographic,
 // rays along y or z whose coordinate on that axis does not vary over the
-// image, and image x moving along the cube's x axis.  (The kernel checks each
-// group of eight rays itself and takes the per-ray loop where they do not fit.)
+// image, and image x moving along the cube's x axis one voxel per pixel (at
+// other pixel spacings no group of 8 rays would fit, and the kernel would
+// trace 8 rays per thread one after another).  The kernel checks each group
+// of eight rays itself and takes the per-ray loop where they do not fit.
 bool rows_views(const std::vector<JobDesc> &jobs, int mode, const vrc_raycfg &rc)
 {
     if (mode != 0 || rc.sampling != VRC_NEAREST || rc.width < kRowG) return false;
@@ -1045,7 +1047,7 @@ bool rows_views(const std::vector<JobDesc> &jobs, int mode, const vrc_raycfg &rc
         const ViewParams &vp = j.vp;
         if (vp.kind != VRC_CAM_ORTHO || vp.D0[0] != 0.f || (vp.D0[1] != 0.f) == (vp.D0[2] != 0.f)) return false;
         const int m = vp.D0[1] != 0.f ? 1 : 2;
-        if (vp.DX[m] != 0.f || vp.DY[m] != 0.f || vp.DX[0] == 0.f) return false;
+        if (vp.DX[m] != 0.f || vp.DY[m] != 0.f || std::fabs(vp.DX[0]) != 1.f) return false;
     }
     return true;
 }

@@ -367,7 +367,7 @@ void load_loop(Server *S)
         S->load_q.pop_front();
         lk.unlock();
         Cube *c = job.first;
-        const vrc_status st = upload_cube(ctx, c, c->host_src, 0, S->load_stream);
+        const vrc_status st = load_registered(ctx, c, S->load_stream);
         {
             std::lock_guard<std::mutex> rl(ctx->res_mu);
             ctx->reserved -= job.second;

@@ -118,6 +118,11 @@ struct Cube {
     bool managed = false;
     const float *host_src = nullptr;
     bool host_pinned = false;     // host_src was page-locked by the registration (unlocked at release)
+    // bf16 / fp8 registered cubes: the packed bricks (nbricks x brick_bytes)
+    // and brick scales, kept in page-locked host memory from the registration
+    // on; loads copy these instead of packing the source again
+    void *host_packed = nullptr;
+    std::vector<float> h_scales;
     std::atomic<int> state{2};    // CUBE_ABSENT, CUBE_LOADING, CUBE_RESIDENT
     double last_use = 0;          // host ms of the last admission or direct use
     bool direct_used = false;     // work of direct calls may be in flight: evictions wait for the device
@@ -256,6 +261,9 @@ void server_stop(vrc_ctx *ctx);
 // record whose geometry and render-copy mode are set; release_device gives
 // back its device memory (the record stays).
 vrc_status upload_cube(vrc_ctx *ctx, Cube *c, const float *src, int32_t src_on_device, cudaStream_t st);
+// Make a registered cube resident: from its packed host copy when it has one,
+// else by the upload passes on the caller's array.
+vrc_status load_registered(vrc_ctx *ctx, Cube *c, cudaStream_t st);
 void release_device(vrc_ctx *ctx, Cube *c, bool sync);
 void release_cube(vrc_ctx *ctx, Cube *c, bool sync);
 int64_t register_cube(vrc_ctx *ctx, Cube *c);

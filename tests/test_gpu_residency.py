@@ -115,3 +115,57 @@ def test_render_copy_flags_and_reported_path():
     assert small.last_render_path() == "fused_ldg"
     small.cube_free(c)
     small.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_registered_bf16_fp8_load_from_packed_host_copy(dtype):
+    """bf16 / fp8 registered cubes are packed once at registration; their
+    packed bricks stay in page-locked host memory and every later load copies
+    those: the caller's arrays are zeroed after registration and every result
+    (served or direct, after evictions and reloads) still equals that of the
+    same cube uploaded for good."""
+    import paper_1111_6661_b300 as vrc
+    vols = _cubes(3)
+    ref = vrc.Context(0)
+    rids = [ref.cube_upload(v, dtype, brick=128) for v in vols]
+    # budgets that hold one cube's upload beside another resident cube, not all three
+    budget = {"bf16": 340, "fp8": 160}[dtype] * MB
+    ctx = vrc.Context(0, hbm_budget_bytes=budget, n_streams=2, max_inflight=8)
+    srcs = [v.copy() for v in vols]
+    ids = [ctx.cube_register(s, dtype, brick=128) for s in srcs]
+    st0 = ctx.residency()
+    assert st0["loads"] == 3 and st0["resident"] >= 1
+    for s in srcs:
+        s[...] = 0.0                                  # not read after the registration
+    dims = (256, 256, 256)
+    cams = cubegen.random_cameras(dims, 6, 7)
+    tf = cubegen.tf_dense()
+    rc = vrc.raycfg(96, 64, 0.5)
+    order = [0, 1, 2, 0, 2, 1, 1, 0]
+    outs, tickets = [], []
+    for k, i in enumerate(order):
+        if k % 3 == 2:
+            out = torch.zeros(64, dtype=torch.int64, device="cuda")
+            tickets.append(("stats", i, ctx.submit("stats", ids[i], nbins=64, out=out)))
+        else:
+            out = torch.zeros(96 * 64 * 4, device="cuda")
+            tickets.append(("dvr", i, ctx.submit("dvr", ids[i], cam=cams[k % 6], rc=rc, tf=tf, out=out)))
+        outs.append(out)
+    res = [ctx.poll(t, -1) for _, _, t in tickets]
+    assert all(r["status"] == 0 for r in res), res
+    st = ctx.residency()
+    assert st["loads"] > 3 and st["evictions"] >= 2
+    for k, ((kind, i, _), r, out) in enumerate(zip(tickets, res, outs)):
+        if kind == "stats":
+            s, h = ref.cube_stats(rids[i], 64)
+            assert r["stats"] == s and np.array_equal(out.cpu().numpy().astype(np.uint64), h)
+        else:
+            assert r["path"] == "fused"
+            assert torch.equal(out, ref.render_dvr(rids[i], [cams[k % 6]], rc, tf).reshape(-1))
+    img = ctx.render_mip(ids[2], [cams[1]], vrc.raycfg(40, 40, 0.5))
+    assert torch.equal(img, ref.render_mip(rids[2], [cams[1]], vrc.raycfg(40, 40, 0.5)))
+    assert ctx.cube_median(ids[0]) == ref.cube_median(rids[0])
+    for i in ids:
+        ctx.cube_free(i)
+    ctx.close()
+    ref.close()
