@@ -251,8 +251,16 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
 typedef int32_t (*vrc_brick_source_fn)(void *user, int64_t brick, int32_t bx, int32_t by, int32_t bz, float *dst);
 
 /*
- * Out-of-core float32 cube whose bricks come from a provider (Sec. 2: cubes
- * larger than the memory of one node, streamed to the GPU on side streams).
+ * Out-of-core cube whose bricks come from a provider (Sec. 2: cubes larger
+ * than the memory of one node, streamed to the GPU on side streams).  The
+ * provider hands float32 bricks; storage (VRC_F32, VRC_BF16, VRC_FP8E4M3) is
+ * the type the host cache and the device ring keep them in, packed as
+ * vrc_cube_upload packs (bf16 / fp8: on the device, a provided brick at a
+ * time, then copied into its host slot; the FP8 scale of a brick comes from
+ * the absmax of its provided values, halo included), so a bf16 / fp8 cube
+ * needs half / a quarter of the host memory and of the bytes each frame moves
+ * over the host link.  Stored extrema, statistics, median and images equal
+ * those of the same cube uploaded with that storage.
  * The call asks `source` for every brick once, in index order, to record each
  * brick's minimum and maximum (the transfer-function range, brick culling),
  * the sums that centre the statistics and its non-finite voxels; it returns
@@ -272,8 +280,8 @@ typedef int32_t (*vrc_brick_source_fn)(void *user, int64_t brick, int32_t bx, in
  * VRC_E_SOURCE (the provider failed; no cube is created).
  */
 vrc_status vrc_cube_upload_streamed(vrc_ctx *ctx, vrc_brick_source_fn source, void *user, int64_t nx, int64_t ny,
-                                    int64_t nz, int32_t brick, int64_t n_host_bricks, int32_t ring_bricks,
-                                    int64_t *cube_id);
+                                    int64_t nz, int32_t storage, int32_t brick, int64_t n_host_bricks,
+                                    int32_t ring_bricks, int64_t *cube_id);
 
 /*
  * Fill host slot `slot` of a streamed cube with one brick given as
@@ -311,17 +319,21 @@ vrc_status vrc_cube_info(vrc_ctx *ctx, int64_t cube_id, int64_t dims[3], int32_t
 
 /*
  * Copy the stored form of brick `brick` (x fastest over the brick grid) of a
- * resident cube into host memory `dst` of at least `dst_bytes` bytes (Sec. 2:
+ * cube into host memory `dst` of at least `dst_bytes` bytes (Sec. 2:
  * sub-cubes; the quantised storage of the precision form).  Layout: R = B + 2
  * planes (local z = -1..B) of R rows (local y = -1..B) of P = B + 2*O elements
- * of esize bytes (4 fp32, 2 bf16 bits, 1 e4m3 code; O = 32 / esize: rows
- * start interior voxels on 32-byte boundaries), the
+ * of esize bytes (4 fp32, 2 bf16 bits, 1 e4m3 code; O = 32 / esize for
+ * resident cubes, 16 / esize for out-of-core cubes: rows start interior voxels
+ * on 32- / 16-byte boundaries), the
  * voxel at local x at element O + x of its row: x = -1 and x = B are the
  * halo, elements before and after them are padding (0).  Halo voxels outside
  * the cube repeat the nearest edge voxel; FP8 codes use this brick's scale.
  * Brick bytes = P * R * R * esize.  Synchronous (waits for the device).
+ * Out-of-core cubes: the brick's host slot (a provider cube provides and
+ * packs the brick again when its slot holds another one; a caller-filled cube
+ * reads slot brick % n_host_bricks).
  * Errors: VRC_E_BADID, VRC_E_INVAL (brick out of range, dst NULL, dst_bytes
- * too small), VRC_E_UNSUPPORTED (streamed cube: its bricks are the caller's).
+ * too small, caller-filled slots not all written), VRC_E_SOURCE.
  */
 vrc_status vrc_cube_read_brick(vrc_ctx *ctx, int64_t cube_id, int64_t brick, void *dst, int64_t dst_bytes);
 

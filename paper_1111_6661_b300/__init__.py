@@ -148,13 +148,16 @@ class Context:
         cid = ctypes.c_int64()
         self._check(self._lib.vrc_cube_create_streamed(self.h, dims[0], dims[1], dims[2], brick, n_host_bricks,
                                                        ring_bricks, ctypes.byref(cid)))
+        self._out_of_core = getattr(self, "_out_of_core", set()) | {cid.value}
         return cid.value
 
-    def cube_upload_streamed(self, dims, brick: int, source, n_host_bricks: int, ring_bricks: int = 0) -> int:
+    def cube_upload_streamed(self, dims, brick: int, source, n_host_bricks: int, ring_bricks: int = 0,
+                             storage: str = "f32") -> int:
         """Out-of-core cube whose bricks come from `source`: either a pair
         (C function address, user address) of a vrc_brick_source_fn, or a
         Python callable (brick, bx, by, bz) -> float32 array of (B+2)^3 values
-        (z, y, x) holding the brick and its clamp-to-edge halo."""
+        (z, y, x) holding the brick and its clamp-to-edge halo.  storage: the
+        type the host cache and the device ring keep the bricks in."""
         if callable(source):
             R = int(brick) + 2
 
@@ -172,12 +175,14 @@ class Context:
         cid = ctypes.c_int64()
         self._check(self._lib.vrc_cube_upload_streamed(self.h, ctypes.c_void_p(fn_ptr.value if hasattr(fn_ptr, "value")
                                                                                else fn_ptr),
-                                                       ctypes.c_void_p(user), dims[0], dims[1], dims[2], brick,
-                                                       n_host_bricks, ring_bricks, ctypes.byref(cid)))
+                                                       ctypes.c_void_p(user), dims[0], dims[1], dims[2],
+                                                       DTYPES[storage], brick, n_host_bricks, ring_bricks,
+                                                       ctypes.byref(cid)))
         # the provider (and its closure) must outlive the cube
         if not hasattr(self, "_sources"):
             self._sources = {}
         self._sources[cid.value] = fn
+        self._out_of_core = getattr(self, "_out_of_core", set()) | {cid.value}
         return cid.value
 
     def cube_put_brick(self, cube_id: int, slot: int, brick_with_halo: np.ndarray):
@@ -205,12 +210,14 @@ class Context:
     def cube_read_brick(self, cube_id: int, brick: int) -> np.ndarray:
         """Stored form of one brick: array (R, R, P) of float32 / uint16 (bf16
         bits) / uint8 (e4m3 codes), R = B + 2 planes and rows (local -1..B),
-        local x at element O + x of a row (O = 32 / element size)."""
+        local x at element O + x of a row (O = 32 / element size; out-of-core
+        cubes 16 / element size)."""
         info = self.cube_info(cube_id)
         B = info["brick"]
         dt = {"f32": np.float32, "bf16": np.uint16, "fp8": np.uint8}[info["storage"]]
         es = np.dtype(dt).itemsize
-        R, P = B + 2, B + 2 * (32 // es)
+        align = 16 if cube_id in getattr(self, "_out_of_core", ()) else 32
+        R, P = B + 2, B + 2 * (align // es)
         out = np.empty((R, R, P), dtype=dt)
         self._check(self._lib.vrc_cube_read_brick(self.h, cube_id, brick, ctypes.c_void_p(out.ctypes.data),
                                                   out.nbytes))

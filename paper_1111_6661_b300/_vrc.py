@@ -75,7 +75,7 @@ PROTOTYPES = {
     "vrc_last_render_path": (c_i32, [c_p, ctypes.POINTER(c_i32)]),
     "vrc_cube_create_streamed": (c_i32, [c_p, c_i64, c_i64, c_i64, c_i32, c_i64, c_i32, ctypes.POINTER(c_i64)]),
     "vrc_cube_put_brick": (c_i32, [c_p, c_i64, c_i64, c_p]),
-    "vrc_cube_upload_streamed": (c_i32, [c_p, c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i64, c_i32,
+    "vrc_cube_upload_streamed": (c_i32, [c_p, c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i64, c_i32,
                                          ctypes.POINTER(c_i64)]),
     "vrc_cube_read_brick": (c_i32, [c_p, c_i64, c_i64, c_p, c_i64]),
     "vrc_cube_free": (c_i32, [c_p, c_i64]),

@@ -255,6 +255,43 @@ __global__ void k_brick_finish(const ScanPartial *__restrict__ part, BrickGeom g
     bnonfinite[b] = r.nonfinite;
 }
 
+// One provided brick ((B+2)^3 floats, x fastest, halo included) in brick
+// storage: row (zr, yr) of P elements with the halo voxel lx = -1 at element
+// O - 1, padding 0; values stored as the upload's pack pass stores them.
+template <int DT>
+__global__ void k_pack_provided(const float *__restrict__ bw, BrickGeom g, float scale, uint8_t *__restrict__ out)
+{
+    const int64_t nrow = (int64_t)g.R * g.R;
+    for (int64_t row = blockIdx.x; row < nrow; row += gridDim.x) {
+        const float *in = bw + row * g.R;
+        for (int e = threadIdx.x; e < g.P; e += blockDim.x) {
+            const int i = e - (g.O - 1);
+            const bool v = i >= 0 && i < g.R;
+            if (DT == VRC_BF16)
+                reinterpret_cast<uint16_t *>(out)[row * g.P + e] =
+                    v ? __bfloat16_as_ushort(__float2bfloat16_rn(in[i])) : (uint16_t)0;
+            else
+                out[row * g.P + e] = v ? fp8_code(in[i], scale) : (uint8_t)0;
+        }
+    }
+}
+
+// Stored values of per-brick extrema measured on provided float32 bricks
+// (rounding is monotone, so the stored extremum is the extremum stored); a
+// brick without finite values keeps its markers, non-finite halo maxima stay.
+template <int DT>
+__global__ void k_stored_extrema(float *mn, float *mx, float *hmx, const float *scales, int64_t n)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const float s = scales[b];
+    if (mn[b] <= mx[b]) {
+        mn[b] = stored_value(mn[b], DT, s);
+        mx[b] = stored_value(mx[b], DT, s);
+    }
+    if (fabsf(hmx[b]) <= FLT_MAX) hmx[b] = stored_value(hmx[b], DT, s);
+}
+
 // 16 bytes of stored elements from 16 / esize source values.
 template <int DT> struct Chunk {
     static constexpr int n = DT == VRC_F32 ? 4 : (DT == VRC_BF16 ? 8 : 16);
@@ -711,6 +748,9 @@ void release_device(vrc_ctx *ctx, Cube *c, bool sync)
     if (c->bmax) dev_free(ctx, c->bmax, g.nbricks * 4);
     if (c->bnonfinite) dev_free(ctx, c->bnonfinite, g.nbricks * 4);
     if (c->bhalo) dev_free(ctx, c->bhalo, g.nbricks * 4);
+    if (c->pack_src) dev_free(ctx, c->pack_src, (size_t)g.R * g.R * g.R * sizeof(float));
+    if (c->pack_out) dev_free(ctx, c->pack_out, (size_t)g.brick_bytes);
+    c->pack_src = c->pack_out = nullptr;
     c->pool = c->ring_pool = nullptr;
     c->scales = c->cellmax = c->bmin = c->bmax = c->bhalo = nullptr;
     c->bnonfinite = nullptr;
@@ -723,6 +763,7 @@ void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
     if (c->host_pool) cudaFreeHost(c->host_pool);
     if (c->host_pinned) cudaHostUnregister((void *)c->host_src);
     if (c->host_packed) cudaFreeHost(c->host_packed);
+    if (c->pack_stream) cudaStreamDestroy(c->pack_stream);
     for (cudaEvent_t e : c->slot_ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -761,21 +802,28 @@ struct BrickMeta {
     int64_t cnt = 0;
 };
 
-// Repack brick `bw` ((B+2)^3 floats, x fastest) into host slot `slot` (rows of
-// P elements, the halo voxel at element O-1) and measure it.
-void pack_host_slot(Cube *c, int64_t slot, const float *bw, BrickMeta *m)
+// Measure provided brick `bw` ((B+2)^3 floats, x fastest): interior extrema,
+// sum and non-finite count, the halo-inclusive maximum, and the largest
+// finite magnitude (halo included: the FP8 scale's absmax).  rows: float32
+// host-slot storage to fill in the same pass (rows of P elements, the halo
+// voxel at element O-1, padding 0), or null.
+void measure_brick(const BrickGeom &g, const float *bw, BrickMeta *m, float *absmax, float *rows)
 {
-    const BrickGeom &g = c->g;
     const int R = g.R;
-    float *dst = reinterpret_cast<float *>((char *)c->host_pool + slot * g.brick_bytes);
+    float am = 0.f;
     for (int zr = 0; zr < R; ++zr)
         for (int yr = 0; yr < R; ++yr) {
-            float *row = dst + ((int64_t)zr * R + yr) * g.P;
             const float *in = bw + ((int64_t)zr * R + yr) * R;
-            std::memset(row, 0, sizeof(float) * g.P);
-            std::memcpy(row + g.O - 1, in, sizeof(float) * R);
+            if (rows) {
+                float *row = rows + ((int64_t)zr * R + yr) * g.P;
+                std::memset(row, 0, sizeof(float) * g.P);
+                std::memcpy(row + g.O - 1, in, sizeof(float) * R);
+            }
             if (!m) continue;
-            for (int x = 0; x < R; ++x) m->hmx = std::fmax(m->hmx, in[x]);   // NaN ignored, +inf kept
+            for (int x = 0; x < R; ++x) {
+                m->hmx = std::fmax(m->hmx, in[x]);   // NaN ignored, +inf kept
+                if (std::fabs(in[x]) <= FLT_MAX) am = std::fmax(am, std::fabs(in[x]));
+            }
             if (zr >= 1 && zr <= g.B && yr >= 1 && yr <= g.B)
                 for (int x = 1; x <= g.B; ++x) {
                     const float v = in[x];
@@ -789,6 +837,41 @@ void pack_host_slot(Cube *c, int64_t slot, const float *bw, BrickMeta *m)
                     }
                 }
         }
+    *absmax = am;
+}
+
+// Store provided brick b (`bw`, (B+2)^3 floats) in host slot `slot` (rows of
+// P elements, the halo voxel at element O-1), measuring it when m is given.
+// float32: copied on the host.  bf16 / fp8: packed on the device as the
+// upload packs (the brick's FP8 scale from the measured absmax when measuring,
+// else the recorded one) and copied back into the slot.
+vrc_status pack_host_slot(vrc_ctx *ctx, Cube *c, int64_t slot, int64_t b, const float *bw, BrickMeta *m)
+{
+    const BrickGeom &g = c->g;
+    const int R = g.R;
+    float absmax = 0.f;
+    char *dst = (char *)c->host_pool + slot * g.brick_bytes;
+    if (g.dtype == VRC_F32) {
+        measure_brick(g, bw, m, &absmax, reinterpret_cast<float *>(dst));
+        return VRC_OK;
+    }
+    if (m) measure_brick(g, bw, m, &absmax, nullptr);
+    if (m) c->h_scales[b] = g.dtype == VRC_FP8E4M3 && absmax > 0.f ? absmax / 448.f : 1.f;
+    const float scale = c->h_scales[b];
+    const size_t nsrc = (size_t)R * R * R * sizeof(float);
+    cudaStream_t ps = c->pack_stream;
+    VRC_CK(ctx, cudaMemcpyAsync(c->pack_src, bw, nsrc, cudaMemcpyHostToDevice, ps));
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)R * R, 4096);
+    if (g.dtype == VRC_BF16)
+        k_pack_provided<VRC_BF16><<<grid, 128, 0, ps>>>((const float *)c->pack_src, g, scale, (uint8_t *)c->pack_out);
+    else
+        k_pack_provided<VRC_FP8E4M3><<<grid, 128, 0, ps>>>((const float *)c->pack_src, g, scale,
+                                                           (uint8_t *)c->pack_out);
+    count_launch(ctx);
+    VRC_CK(ctx, cudaGetLastError());
+    VRC_CK(ctx, cudaMemcpyAsync(dst, c->pack_out, (size_t)g.brick_bytes, cudaMemcpyDeviceToHost, ps));
+    VRC_CK(ctx, cudaStreamSynchronize(ps));
+    return VRC_OK;
 }
 
 // Record brick b's measurements.  For a brick on the cube's far border the
@@ -1078,12 +1161,14 @@ vrc_status vrc_cube_register(vrc_ctx *ctx, const float *src, int64_t nx, int64_t
     return VRC_OK;
 }
 
-vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_t nz, int32_t brick,
-                                    int64_t n_host_bricks, int32_t ring_bricks, int64_t *cube_id)
+namespace {
+
+vrc_status create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_t nz, int32_t storage, int32_t brick,
+                           int64_t n_host_bricks, int32_t ring_bricks, int64_t *cube_id)
 {
     if (!ctx || !cube_id) return VRC_E_INVAL;
     BrickGeom g;
-    if (!make_geom(nx, ny, nz, brick, VRC_F32, &g, 16)) return set_err(ctx, VRC_E_INVAL, "bad dims/brick");
+    if (!make_geom(nx, ny, nz, brick, storage, &g, 16)) return set_err(ctx, VRC_E_INVAL, "bad dims/storage/brick");
     if (n_host_bricks <= 0 || n_host_bricks > g.nbricks) return set_err(ctx, VRC_E_INVAL, "bad n_host_bricks");
     if (ring_bricks < 0 || ring_bricks > 4096) return set_err(ctx, VRC_E_INVAL, "bad ring_bricks");
     if (ring_bricks == 0) ring_bricks = 8;
@@ -1121,11 +1206,19 @@ vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_
     c->h_bhalo_max.assign(g.nbricks, -INFINITY);
     c->h_bsum.assign(g.nbricks, 0.0);
     c->h_bcnt.assign(g.nbricks, 0);
-    std::vector<float> ones(g.nbricks, 1.f);
-    cudaMemcpy(c->scales, ones.data(), g.nbricks * 4, cudaMemcpyHostToDevice);
+    c->h_scales.assign(g.nbricks, 1.f);
+    cudaMemcpy(c->scales, c->h_scales.data(), g.nbricks * 4, cudaMemcpyHostToDevice);
     c->charged = (int64_t)ring_bricks * g.brick_bytes;
     *cube_id = register_cube(ctx, c);
     return VRC_OK;
+}
+
+}  // namespace
+
+vrc_status vrc_cube_create_streamed(vrc_ctx *ctx, int64_t nx, int64_t ny, int64_t nz, int32_t brick,
+                                    int64_t n_host_bricks, int32_t ring_bricks, int64_t *cube_id)
+{
+    return create_streamed(ctx, nx, ny, nz, VRC_F32, brick, n_host_bricks, ring_bricks, cube_id);
 }
 
 vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const float *bw)
@@ -1137,7 +1230,8 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
     if (c->source) return set_err(ctx, VRC_E_UNSUPPORTED, "cube takes its bricks from its provider");
     if (slot < 0 || slot >= c->n_host) return set_err(ctx, VRC_E_INVAL, "slot out of range");
     BrickMeta m;
-    pack_host_slot(c, slot, bw, &m);
+    vrc_status s = pack_host_slot(ctx, c, slot, slot, bw, &m);
+    if (s != VRC_OK) return s;
     if (!c->host_filled[slot]) {
         c->host_filled[slot] = 1;
         ++c->n_filled;
@@ -1149,18 +1243,34 @@ vrc_status vrc_cube_put_brick(vrc_ctx *ctx, int64_t cube_id, int64_t slot, const
 }
 
 vrc_status vrc_cube_upload_streamed(vrc_ctx *ctx, vrc_brick_source_fn source, void *user, int64_t nx, int64_t ny,
-                                    int64_t nz, int32_t brick, int64_t n_host_bricks, int32_t ring_bricks,
-                                    int64_t *cube_id)
+                                    int64_t nz, int32_t storage, int32_t brick, int64_t n_host_bricks,
+                                    int32_t ring_bricks, int64_t *cube_id)
 {
     if (!ctx || !cube_id) return VRC_E_INVAL;
     if (!source) return set_err(ctx, VRC_E_INVAL, "null brick provider");
     int64_t id = 0;
-    vrc_status s = vrc_cube_create_streamed(ctx, nx, ny, nz, brick, n_host_bricks, ring_bricks, &id);
+    vrc_status s = create_streamed(ctx, nx, ny, nz, storage, brick, n_host_bricks, ring_bricks, &id);
     if (s != VRC_OK) return s;
     Cube *c = find_cube(ctx, id);
     c->source = source;
     c->source_user = user;
     const BrickGeom &g = c->g;
+    if (g.dtype != VRC_F32) {
+        // device staging of the packing of provided bricks
+        s = dev_alloc(ctx, &c->pack_src, (size_t)g.R * g.R * g.R * sizeof(float));
+        if (s == VRC_OK) s = dev_alloc(ctx, &c->pack_out, (size_t)g.brick_bytes);
+        if (s == VRC_OK) {
+            const cudaError_t e = cudaStreamCreateWithFlags(&c->pack_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                c->pack_stream = nullptr;
+                s = cuda_err(ctx, e, "packing stream");
+            }
+        }
+        if (s != VRC_OK) {
+            vrc_cube_free(ctx, id);
+            return s;
+        }
+    }
     c->slot_brick.assign(c->n_host, -1);
     c->slot_ev.assign(c->n_host, nullptr);
     c->slot_ev_live.assign(c->n_host, 0);
@@ -1179,13 +1289,45 @@ vrc_status vrc_cube_upload_streamed(vrc_ctx *ctx, vrc_brick_source_fn source, vo
         BrickMeta m;
         s = call_source(ctx, c, b);
         if (s != VRC_OK) break;
-        pack_host_slot(c, slot, c->source_buf.data(), &m);
+        s = pack_host_slot(ctx, c, slot, b, c->source_buf.data(), &m);
+        if (s != VRC_OK) break;
         c->slot_brick[slot] = b;
         set_brick_meta(c, b, m);
     }
     if (s != VRC_OK) {
         vrc_cube_free(ctx, id);
         return s;
+    }
+    if (s == VRC_OK && g.dtype != VRC_F32) {
+        // brick scales to the device; the extrema measured on the provided
+        // float32 bricks become those of the stored values
+        const size_t nb4 = (size_t)g.nbricks * 4;
+        cudaStream_t ps = c->pack_stream;
+        auto ck = [&](cudaError_t e, const char *what) {
+            if (s == VRC_OK && e != cudaSuccess) s = cuda_err(ctx, e, what);
+        };
+        ck(cudaMemcpyAsync(c->scales, c->h_scales.data(), nb4, cudaMemcpyHostToDevice, ps), "brick scales");
+        ck(cudaMemcpyAsync(c->bmin, c->h_bmin.data(), nb4, cudaMemcpyHostToDevice, ps), "brick extrema");
+        ck(cudaMemcpyAsync(c->bmax, c->h_bmax.data(), nb4, cudaMemcpyHostToDevice, ps), "brick extrema");
+        ck(cudaMemcpyAsync(c->bhalo, c->h_bhalo_max.data(), nb4, cudaMemcpyHostToDevice, ps), "brick extrema");
+        if (s == VRC_OK) {
+            const unsigned grid = (unsigned)((g.nbricks + 127) / 128);
+            if (g.dtype == VRC_BF16)
+                k_stored_extrema<VRC_BF16><<<grid, 128, 0, ps>>>(c->bmin, c->bmax, c->bhalo, c->scales, g.nbricks);
+            else
+                k_stored_extrema<VRC_FP8E4M3><<<grid, 128, 0, ps>>>(c->bmin, c->bmax, c->bhalo, c->scales,
+                                                                    g.nbricks);
+            count_launch(ctx);
+            ck(cudaGetLastError(), "stored extrema");
+        }
+        ck(cudaMemcpyAsync(c->h_bmin.data(), c->bmin, nb4, cudaMemcpyDeviceToHost, ps), "brick extrema");
+        ck(cudaMemcpyAsync(c->h_bmax.data(), c->bmax, nb4, cudaMemcpyDeviceToHost, ps), "brick extrema");
+        ck(cudaMemcpyAsync(c->h_bhalo_max.data(), c->bhalo, nb4, cudaMemcpyDeviceToHost, ps), "brick extrema");
+        ck(cudaStreamSynchronize(ps), "brick extrema");
+        if (s != VRC_OK) {
+            vrc_cube_free(ctx, id);
+            return s;
+        }
     }
     c->host_filled.assign(c->n_host, 1);
     c->n_filled = c->n_host;
@@ -1202,12 +1344,20 @@ vrc_status vrc_cube_read_brick(vrc_ctx *ctx, int64_t cube_id, int64_t brick, voi
     CubeUse use;
     vrc_status s = acquire_cube(ctx, cube_id, nullptr, &c, use);
     if (s != VRC_OK) return s;
-    if (c->streamed) return set_err(ctx, VRC_E_UNSUPPORTED, "streamed cube: bricks live in host slots");
     const BrickGeom &g = c->g;
     if (brick < 0 || brick >= g.nbricks) return set_err(ctx, VRC_E_INVAL, "brick %lld out of range", (long long)brick);
     if (dst_bytes < g.brick_bytes)
         return set_err(ctx, VRC_E_INVAL, "dst_bytes %lld < brick bytes %lld", (long long)dst_bytes,
                        (long long)g.brick_bytes);
+    if (c->streamed) {
+        // the brick's host slot (a provider cube provides and packs it again when
+        // the slot holds another brick)
+        if (c->n_filled < c->n_host) return set_err(ctx, VRC_E_INVAL, "streamed cube: host slots not all written");
+        int64_t slot = 0;
+        if ((s = host_brick(ctx, c, brick, &slot)) != VRC_OK) return s;
+        std::memcpy(dst, (const char *)c->host_pool + slot * g.brick_bytes, (size_t)g.brick_bytes);
+        return VRC_OK;
+    }
     VRC_CK(ctx, cudaSetDevice(ctx->device));
     VRC_CK(ctx, cudaDeviceSynchronize());
     VRC_CK(ctx, cudaMemcpy(dst, (const char *)c->pool + brick * g.brick_bytes, (size_t)g.brick_bytes,
@@ -1310,7 +1460,7 @@ vrc_status host_brick(vrc_ctx *ctx, Cube *c, int64_t brick, int64_t *slot)
     c->slot_brick[sl] = -1;
     vrc_status s = call_source(ctx, c, brick);
     if (s != VRC_OK) return s;
-    pack_host_slot(c, sl, c->source_buf.data(), nullptr);
+    if ((s = pack_host_slot(ctx, c, sl, brick, c->source_buf.data(), nullptr)) != VRC_OK) return s;
     c->slot_brick[sl] = brick;
     return VRC_OK;
 }

@@ -1542,7 +1542,7 @@ vrc_status render_streamed(vrc_ctx *ctx, Cube *c, SortLastPlan &plan, const vrc_
     cudaEventRecord(entry, st);             // earlier work on `st` may still use the ring
     cudaStreamWaitEvent(cs, entry, 0);
     vrc_status status = VRC_OK;
-    bricks_fn bf = pick_bricks(mode, rc.sampling, VRC_F32, false);
+    bricks_fn bf = pick_bricks(mode, rc.sampling, c->g.dtype, false);
     size_t made = 0;
     for (size_t i = 0; i < chunks.size() && status == VRC_OK; ++i) {
         const Chunk &ch = chunks[i];

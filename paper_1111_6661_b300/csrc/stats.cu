@@ -305,7 +305,8 @@ struct CodeItems {
     uint32_t Pb, RPb, Ob;
 };
 
-__device__ __forceinline__ CodeItems code_items(const BrickGeom &g)
+// nrun: bricks in the pool (the whole cube, or one run of an out-of-core cube)
+__device__ __forceinline__ CodeItems code_items(const BrickGeom &g, int64_t nrun)
 {
     CodeItems ci;
     ci.logVPR = g.logB - 4;                          // 16 codes per vector
@@ -313,7 +314,7 @@ __device__ __forceinline__ CodeItems code_items(const BrickGeom &g)
     const int logCPB = 2 * g.logB - ci.logRPC;
     ci.lcpi = min(kLogCodeChunks, logCPB);
     ci.ipb = logCPB - ci.lcpi;
-    ci.items = g.nbricks << ci.ipb;
+    ci.items = nrun << ci.ipb;
     ci.Pb = (uint32_t)g.P;
     ci.RPb = (uint32_t)g.R * ci.Pb;
     ci.Ob = (uint32_t)g.O;
@@ -321,18 +322,20 @@ __device__ __forceinline__ CodeItems code_items(const BrickGeom &g)
 }
 
 // Add the codes of item `it` to cnt[256] (interior voxels inside the cube
-// only); returns the item's brick.  Every thread of the block takes part.
+// only); returns the item's brick of the cube (the pool holds bricks brick0 ..).
+// Every thread of the block takes part.
 __device__ __forceinline__ uint32_t count_codes(const uint8_t *__restrict__ pool, const BrickGeom &g,
-                                                const CodeItems &ci, int64_t it, uint32_t *cnt)
+                                                const CodeItems &ci, int64_t it, uint32_t *cnt, int64_t brick0)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t b = (uint32_t)(it >> ci.ipb);
+    const uint32_t pb = (uint32_t)(it >> ci.ipb);              // brick slot in the pool
+    const uint32_t b = pb + (uint32_t)brick0;                  // brick of the cube
     const uint32_t c0 = ((uint32_t)it & ((1u << ci.ipb) - 1)) << ci.lcpi;
     const uint32_t bx = b % (uint32_t)g.nb[0], byz = b / (uint32_t)g.nb[0];
     const uint32_t by = byz % (uint32_t)g.nb[1], bz = byz / (uint32_t)g.nb[1];
     const bool clean = ((int64_t)(bx + 1) << g.logB) <= g.dims[0] && ((int64_t)(by + 1) << g.logB) <= g.dims[1] &&
                        ((int64_t)(bz + 1) << g.logB) <= g.dims[2];
-    const uint8_t *bp = pool + (uint64_t)b * (uint64_t)g.brick_bytes;
+    const uint8_t *bp = pool + (uint64_t)pb * (uint64_t)g.brick_bytes;
     for (uint32_t ch = c0 + warp; ch < c0 + (1u << ci.lcpi); ch += kStatsThreads / 32) {
         const uint32_t lr0 = ch << ci.logRPC;
         uint4 raw[kVecPerLane];
@@ -378,13 +381,13 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_codes(StatsArgs a)
     __shared__ uint32_t cnt[256];
     const BrickGeom &g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const CodeItems ci = code_items(g);
+    const CodeItems ci = code_items(g, a.nrun);
     double s1 = 0.0, s2 = 0.0;
     unsigned long long n = 0, nnf = 0;
     for (int64_t it = blockIdx.x; it < ci.items; it += gridDim.x) {
         cnt[threadIdx.x] = 0;
         __syncthreads();
-        const uint32_t b = count_codes(a.pool, g, ci, it, cnt);
+        const uint32_t b = count_codes(a.pool, g, ci, it, cnt, a.brick0);
         __syncthreads();
         const uint32_t k = cnt[threadIdx.x];
         if (k) {
@@ -421,7 +424,15 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_codes(StatsArgs a)
             r.n += wp[w].n;
             r.nnf += wp[w].nnf;
         }
-        a.partials[blockIdx.x] = r;
+        if (a.accumulate) {
+            StatPartial &p = a.partials[blockIdx.x];
+            p.s1 += r.s1;
+            p.s2 += r.s2;
+            p.n += r.n;
+            p.nnf += r.nnf;
+        } else {
+            a.partials[blockIdx.x] = r;
+        }
     }
 }
 
@@ -665,14 +676,15 @@ __global__ void __launch_bounds__(kStatsThreads) k_select_keys(const uint32_t *_
 // FP8 median, step 1: table[b * 256 + q] = number of interior voxels of brick
 // b stored with code q (zeroed by the caller).
 __global__ void __launch_bounds__(kStatsThreads) k_code_table(const uint8_t *__restrict__ pool, BrickGeom g,
-                                                             uint32_t *__restrict__ table)
+                                                             uint32_t *__restrict__ table, int64_t brick0,
+                                                             int64_t nrun)
 {
     __shared__ uint32_t cnt[256];
-    const CodeItems ci = code_items(g);
+    const CodeItems ci = code_items(g, nrun);
     for (int64_t it = blockIdx.x; it < ci.items; it += gridDim.x) {
         cnt[threadIdx.x] = 0;
         __syncthreads();
-        const uint32_t b = count_codes(pool, g, ci, it, cnt);
+        const uint32_t b = count_codes(pool, g, ci, it, cnt, brick0);
         __syncthreads();
         if (cnt[threadIdx.x]) atomicAdd(&table[(int64_t)b * 256 + threadIdx.x], cnt[threadIdx.x]);
         __syncthreads();
@@ -938,8 +950,20 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
     uint32_t *table = reinterpret_cast<uint32_t *>(dh + kSelMaxBins);
     if (codes) {
         VRC_CK(ctx, cudaMemsetAsync(table, 0, nentries * sizeof(uint32_t), st));
-        k_code_table<<<stats_grid(ctx), kStatsThreads, 0, st>>>((const uint8_t *)c->pool, c->g, table);
-        count_launch(ctx);
+        if (c->streamed) {
+            // out-of-core: the counts are taken run by run through the ring
+            const vrc_status sr = for_ring_runs(ctx, c, st, [&](const uint8_t *pool, int64_t b0, int64_t n) {
+                k_code_table<<<stats_grid(ctx), kStatsThreads, 0, st>>>(pool, c->g, table, b0, n);
+                count_launch(ctx);
+                const cudaError_t e = cudaGetLastError();
+                return e == cudaSuccess ? VRC_OK : cuda_err(ctx, e, "code table run");
+            });
+            if (sr != VRC_OK) return sr;
+        } else {
+            k_code_table<<<stats_grid(ctx), kStatsThreads, 0, st>>>((const uint8_t *)c->pool, c->g, table, 0,
+                                                                    c->g.nbricks);
+            count_launch(ctx);
+        }
         VRC_CK(ctx, cudaGetLastError());
     }
     std::vector<unsigned long long> h(kSelMaxBins);
@@ -1025,14 +1049,19 @@ vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *str
                 table, c->scales, nentries, a);
             count_launch(ctx);
         } else if (c->streamed) {
-            // out-of-core (float32): the pass runs over the cube run by run through the ring
+            // out-of-core: the pass runs over the cube run by run through the ring
             s = for_ring_runs(ctx, c, st, [&](const uint8_t *pool, int64_t b0, int64_t n) {
                 SelArgs r = a;
                 r.pool = pool;
                 r.brick0 = b0;
                 r.nrun = n;
-                if (pass == 0) k_select_hist<VRC_F32, true><<<grid, kStatsThreads, 0, st>>>(r);
-                else k_select_hist<VRC_F32, false><<<grid, kStatsThreads, 0, st>>>(r);
+                if (c->g.dtype == VRC_F32) {
+                    if (pass == 0) k_select_hist<VRC_F32, true><<<grid, kStatsThreads, 0, st>>>(r);
+                    else k_select_hist<VRC_F32, false><<<grid, kStatsThreads, 0, st>>>(r);
+                } else {
+                    if (pass == 0) k_select_hist<VRC_BF16, true><<<grid, kStatsThreads, 0, st>>>(r);
+                    else k_select_hist<VRC_BF16, false><<<grid, kStatsThreads, 0, st>>>(r);
+                }
                 count_launch(ctx);
                 const cudaError_t e = cudaGetLastError();
                 return e == cudaSuccess ? VRC_OK : cuda_err(ctx, e, "median run");

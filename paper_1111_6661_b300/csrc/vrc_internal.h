@@ -88,6 +88,11 @@ struct Cube {
     std::vector<cudaEvent_t> slot_ev;
     std::vector<uint8_t> slot_ev_live;
     std::vector<float> source_buf;      // (B+2)^3 floats handed to the provider
+    // bf16 / fp8 provider cubes: a provided brick is packed on the device
+    // (pack_src: its (B+2)^3 floats, pack_out: the stored brick) on pack_stream
+    // and copied back into its host slot; brick scales in h_scales
+    void *pack_src = nullptr, *pack_out = nullptr;
+    cudaStream_t pack_stream = nullptr;
     uint64_t source_calls = 0;          // provider calls since creation
     std::vector<double> h_bsum;         // per brick: sum and count of its finite interior values
     std::vector<int64_t> h_bcnt;

@@ -187,8 +187,8 @@ def test_read_brick_errors(ctx):
         ctx.cube_read_brick(cid, 0)               # freed id
     sid = ctx.cube_create_streamed((32, 32, 32), 16, 8)
     try:
-        with pytest.raises(vrc.VrcError, match="UNSUPPORTED"):
-            ctx.cube_read_brick(sid, 0)           # a streamed cube's bricks live in host slots
+        with pytest.raises(vrc.VrcError, match="INVAL"):
+            ctx.cube_read_brick(sid, 0)           # host slots not written yet
     finally:
         ctx.cube_free(sid)
 

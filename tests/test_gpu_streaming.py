@@ -344,3 +344,54 @@ def test_stats_of_caller_filled_streamed_cube(ctx, cube128):
     assert ctx.cube_median(sid) == ctx.cube_median(rid)
     ctx.cube_free(sid)
     ctx.cube_free(rid)
+
+
+def _voxels(brick_array, B):
+    """Logical (B+2)^3 stored elements of a brick as read by cube_read_brick
+    (the row padding dropped: resident and out-of-core cubes pad rows
+    differently)."""
+    R, P = B + 2, brick_array.shape[2]
+    O = (P - B) // 2
+    return brick_array[:, :, O - 1:O - 1 + R]
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+@pytest.mark.parametrize("n_host", [None, 3])
+def test_provider_cube_bf16_fp8_matches_resident(ctx, cube128, dtype, n_host):
+    """Out-of-core cube kept as bf16 / fp8 (the provider hands float32 bricks;
+    each is packed on the device and its stored form kept in the host cache):
+    every stored brick (bf16 bits, e4m3 codes and the brick scales behind
+    them), the TF range, sort-last renders, statistics, histogram and median
+    equal those of the same cube uploaded with that storage.  With 3 host slots
+    bricks are provided and packed again during renders and passes."""
+    import paper_1111_6661_b300 as vrc
+    v = cube128[:64, :48, :80].copy()
+    v[40, 10, 70] = np.nan                   # non-finite voxels in border bricks
+    v[3, 47, 2] = np.inf
+    dims = (80, 48, 64)
+    source, calls = _provider(v, 16)
+    nb_total = 5 * 3 * 4
+    sid = ctx.cube_upload_streamed(dims, 16, source, n_host or nb_total, 4, storage=dtype)
+    assert sorted(calls) == list(range(nb_total))
+    rid = ctx.cube_upload(v, dtype, brick=16)
+    si, ri = ctx.cube_info(sid), ctx.cube_info(rid)
+    assert si["storage"] == dtype and (si["vmin"], si["vmax"]) == (ri["vmin"], ri["vmax"])
+    for b in range(nb_total):
+        assert np.array_equal(_voxels(ctx.cube_read_brick(sid, b), 16), _voxels(ctx.cube_read_brick(rid, b), 16)), b
+    cams = cubegen.orbit_cameras(dims, 2) + [cubegen.ortho_z_camera(dims)]
+    rc, rs = vrc.raycfg(40, 32, 0.5), vrc.raycfg(40, 32, 0.5, path="sortlast")
+    assert torch.equal(ctx.render_mip(sid, cams, rc).cpu(), ctx.render_mip(rid, cams, rs).cpu())
+    tf = cubegen.tf_dense()
+    assert torch.equal(ctx.render_dvr(sid, cams, rc, tf).cpu(), ctx.render_dvr(rid, cams, rs, tf).cpu())
+    assert ctx.last_render_path() == "sortlast"
+    s, h = ctx.cube_stats(sid, 300)
+    sr, hr = ctx.cube_stats(rid, 300)
+    _check_stats_equal(s, sr, h, hr)
+    assert s["n_nonfinite"] == 2
+    assert ctx.cube_median(sid) == ctx.cube_median(rid)
+    if n_host is None:
+        # every brick cached: the zero-copy path reads the packed slots in place
+        z = ctx.render_mip(sid, cams, vrc.raycfg(40, 32, 0.5, path="zerocopy")).cpu()
+        assert torch.equal(z, ctx.render_mip(sid, cams, rc).cpu())
+    ctx.cube_free(sid)
+    ctx.cube_free(rid)
