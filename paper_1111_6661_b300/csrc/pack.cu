@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <type_traits>
 
 #include "vrc_internal.h"
@@ -764,6 +765,7 @@ void release_cube(vrc_ctx *ctx, Cube *c, bool sync)
     if (c->host_pinned) cudaHostUnregister((void *)c->host_src);
     if (c->host_packed) cudaFreeHost(c->host_packed);
     if (c->pack_stream) cudaStreamDestroy(c->pack_stream);
+    if (c->source_pinned) cudaHostUnregister(c->source_buf.data());
     for (cudaEvent_t e : c->slot_ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -802,16 +804,21 @@ struct BrickMeta {
     int64_t cnt = 0;
 };
 
-// Measure provided brick `bw` ((B+2)^3 floats, x fastest): interior extrema,
-// sum and non-finite count, the halo-inclusive maximum, and the largest
-// finite magnitude (halo included: the FP8 scale's absmax).  rows: float32
-// host-slot storage to fill in the same pass (rows of P elements, the halo
-// voxel at element O-1, padding 0), or null.
-void measure_brick(const BrickGeom &g, const float *bw, BrickMeta *m, float *absmax, float *rows)
+// Measure z-planes [z0, z1) of provided brick `bw` ((B+2)^3 floats, x
+// fastest): interior extrema, sum (per row in binary32, rows in binary64: it
+// only centres the statistics) and non-finite count, the halo-inclusive
+// maximum (NaN ignored, +inf kept) and the largest finite magnitude (halo
+// included: the FP8 scale's absmax).  rows: float32 host-slot storage to fill
+// in the same pass (rows of P elements, the halo voxel at element O-1,
+// padding 0), or null.
+void measure_planes(const BrickGeom &g, const float *bw, int z0, int z1, BrickMeta *m, float *absmax, float *rows)
 {
-    const int R = g.R;
-    float am = 0.f;
-    for (int zr = 0; zr < R; ++zr)
+    const int R = g.R, B = g.B;
+    float hmx = -INFINITY, am = 0.f, mn = FLT_MAX, mx = -FLT_MAX;
+    int32_t nnf = 0;
+    int64_t cnt = 0;
+    double sum = 0.0;
+    for (int zr = z0; zr < z1; ++zr)
         for (int yr = 0; yr < R; ++yr) {
             const float *in = bw + ((int64_t)zr * R + yr) * R;
             if (rows) {
@@ -821,23 +828,69 @@ void measure_brick(const BrickGeom &g, const float *bw, BrickMeta *m, float *abs
             }
             if (!m) continue;
             for (int x = 0; x < R; ++x) {
-                m->hmx = std::fmax(m->hmx, in[x]);   // NaN ignored, +inf kept
-                if (std::fabs(in[x]) <= FLT_MAX) am = std::fmax(am, std::fabs(in[x]));
+                const float v = in[x], a = std::fabs(v);
+                hmx = v > hmx ? v : hmx;
+                am = a <= FLT_MAX && a > am ? a : am;
             }
-            if (zr >= 1 && zr <= g.B && yr >= 1 && yr <= g.B)
-                for (int x = 1; x <= g.B; ++x) {
+            if (zr >= 1 && zr <= B && yr >= 1 && yr <= B) {
+                float rs = 0.f;
+                int rc = 0;
+                for (int x = 1; x <= B; ++x) {
                     const float v = in[x];
-                    if (std::isfinite(v)) {
-                        m->mn = std::fmin(m->mn, v);
-                        m->mx = std::fmax(m->mx, v);
-                        m->sum += v;
-                        ++m->cnt;
-                    } else {
-                        ++m->nnf;
-                    }
+                    const bool fin = std::fabs(v) <= FLT_MAX;
+                    mn = fin && v < mn ? v : mn;
+                    mx = fin && v > mx ? v : mx;
+                    rs += fin ? v : 0.f;
+                    rc += fin;
                 }
+                sum += rs;
+                cnt += rc;
+                nnf += B - rc;
+            }
         }
+    if (!m) return;
+    m->hmx = hmx;
+    m->mn = mn;
+    m->mx = mx;
+    m->nnf = nnf;
+    m->cnt = cnt;
+    m->sum = sum;
     *absmax = am;
+}
+
+// measure_planes over the whole brick, split by z-planes over host threads
+// for large bricks (merged in plane order: the result does not depend on
+// timing).
+void measure_brick(const BrickGeom &g, const float *bw, BrickMeta *m, float *absmax, float *rows)
+{
+    const int R = g.R;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int64_t)R * R * R < (1 << 20) ? 1 : (int)std::min<unsigned>(hw, 16u);
+    if (nt == 1) {
+        measure_planes(g, bw, 0, R, m, absmax, rows);
+        return;
+    }
+    std::vector<BrickMeta> part(nt);
+    std::vector<float> am(nt, 0.f);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back(measure_planes, std::cref(g), bw, R * t / nt, R * (t + 1) / nt, m ? &part[t] : nullptr,
+                        &am[t], rows);
+    for (std::thread &x : th) x.join();
+    if (!m) return;
+    BrickMeta r;
+    float a = 0.f;
+    for (int t = 0; t < nt; ++t) {
+        r.hmx = part[t].hmx > r.hmx ? part[t].hmx : r.hmx;
+        r.mn = std::min(r.mn, part[t].mn);
+        r.mx = std::max(r.mx, part[t].mx);
+        r.nnf += part[t].nnf;
+        r.cnt += part[t].cnt;
+        r.sum += part[t].sum;
+        a = std::max(a, am[t]);
+    }
+    *m = r;
+    *absmax = a;
 }
 
 // Store provided brick b (`bw`, (B+2)^3 floats) in host slot `slot` (rows of
@@ -1275,6 +1328,14 @@ vrc_status vrc_cube_upload_streamed(vrc_ctx *ctx, vrc_brick_source_fn source, vo
     c->slot_ev.assign(c->n_host, nullptr);
     c->slot_ev_live.assign(c->n_host, 0);
     c->source_buf.resize((size_t)g.R * g.R * g.R);
+    // bf16 / fp8: provided bricks are copied to the device for packing, from page-locked memory
+    if (g.dtype != VRC_F32) {
+        if (cudaHostRegister(c->source_buf.data(), c->source_buf.size() * sizeof(float), cudaHostRegisterPortable) ==
+            cudaSuccess)
+            c->source_pinned = true;
+        else
+            cudaGetLastError();
+    }
     for (int64_t sl = 0; sl < c->n_host && s == VRC_OK; ++sl) {
         const cudaError_t e = cudaEventCreateWithFlags(&c->slot_ev[sl], cudaEventDisableTiming);
         if (e != cudaSuccess) {

@@ -93,6 +93,7 @@ struct Cube {
     // and copied back into its host slot; brick scales in h_scales
     void *pack_src = nullptr, *pack_out = nullptr;
     cudaStream_t pack_stream = nullptr;
+    bool source_pinned = false;         // source_buf page-locked (unlocked at release)
     uint64_t source_calls = 0;          // provider calls since creation
     std::vector<double> h_bsum;         // per brick: sum and count of its finite interior values
     std::vector<int64_t> h_bcnt;
