@@ -1164,7 +1164,7 @@ def main():
     ap.add_argument("--no-view-latency", action="store_true")
     ap.add_argument("--no-mip-native", action="store_true")
     ap.add_argument("--storage", default=None, choices=["f32", "bf16", "fp8"],
-                    help="storage type of the cube (default workload: fp32; mip_native: fp32)")
+                    help="storage type of the cube (default workload, mip_native, ooc provider cube: fp32)")
     ap.add_argument("--path", default="fused", choices=["fused", "slab", "sortlast"],
                     help="render path of the timed step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
