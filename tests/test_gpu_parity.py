@@ -706,6 +706,14 @@ def test_row_group_nearest_mip(ctx, dtype):
     dims = (60, 48, 40)
     B = 16
     v = cubegen.generate(dims, 6, 67)
+    # special columns: all values <= 0 with -0 and +0 (a zero maximum: the
+    # per-ray loop decides), a NaN, an infinity (fp8 stores it as NaN)
+    v[:, 5, 7] = -np.abs(v[:, 5, 7]) - 1.0
+    v[3, 5, 7], v[9, 5, 7] = 0.0, -0.0
+    v[:, 6, 9] = -np.abs(v[:, 6, 9]) - 1.0
+    v[4, 6, 9] = -0.0
+    v[10, 6, 8] = np.nan
+    v[11, 7, 9] = np.inf
     cid = ctx.cube_upload(v, dtype, brick=B)
     nx, ny, nz = dims
     c = (nx / 2, ny / 2, nz / 2)
