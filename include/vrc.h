@@ -410,7 +410,16 @@ vrc_status vrc_cube_stats_noalloc(vrc_ctx *ctx, int64_t cube_id, int32_t nbins, 
  * (brick, code) entries weighted by their counts (a stored fp8 value depends
  * only on its brick's scale and its code).  bf16 keys have 16 significant
  * bits, so two passes fix them.  Out-of-core cubes stream their bricks
- * through the device ring once per pass.  *out is HOST memory; waits for
+ * through the device ring once per pass.
+ * Resident float32 / bf16 cubes of at least 2^22 voxels first bracket the
+ * median.  A first-digit pass over every 61st chunk of rows (1.6% of the cube)
+ * bounds the first-digit bins the median falls in.  One pass over the cube then
+ * counts the finite values and those below the bounded bins, and keeps the
+ * keys of those bins in a device buffer (allocated for the call when they
+ * number at most 2^26 and the budget allows).  The digits are selected among
+ * the kept keys.  When the median's rank falls outside them (a sample unlike
+ * the cube), or a buffer cannot be had, the radix passes above run; the result
+ * is the same exact value either way.  *out is HOST memory; waits for
  * `stream`.  Errors: VRC_E_BADID, VRC_E_NONFINITE, VRC_E_SOURCE.
  */
 vrc_status vrc_cube_median(vrc_ctx *ctx, int64_t cube_id, double *out, void *stream);

@@ -151,6 +151,40 @@ def test_median_candidates_kept_or_not(ctx):
     ctx.cube_free(cid)
 
 
+def sampled_rows_mask(shape, B, esize, stride=61):
+    """Voxels of a cube (dims multiples of B, esize bytes per stored value)
+    that the median's sample reads: chunks of 256 16-byte vectors, i.e.
+    4096 / (esize B) consecutive rows (z_local, y_local) of one brick, every
+    stride-th chunk in brick order."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    b = ((z // B) * (ny // B) + y // B) * (nx // B) + x // B
+    rows_per_chunk = 4096 // (esize * B)
+    chunk = b * (B * B // rows_per_chunk) + ((z % B) * B + y % B) // rows_per_chunk
+    return chunk % stride == 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_median_bracket(ctx, dtype):
+    """Cubes of at least 2^22 voxels: a sample of the rows bounds the median's
+    leading digit, and one pass over the cube keeps the keys of the bounded
+    bins.  A generated cube (the bracket holds the median), a cube with many
+    ties, and a cube whose sampled rows hold values far above the rest (the
+    bracket misses; the passes read the cube) give the oracle's lower median."""
+    v = cubegen.generate((256, 256, 128), 40, 7)
+    rng = np.random.default_rng(12)
+    ties = np.round(rng.standard_normal((128, 256, 256)) * 4).astype(np.float32)
+    skew = rng.standard_normal((128, 256, 256)).astype(np.float32)
+    m = sampled_rows_mask(skew.shape, 64, 4 if dtype == "f32" else 2)
+    assert 0.01 < m.mean() < 0.02
+    skew[m] = 1000.0 + rng.random(int(m.sum())).astype(np.float32)
+    for w in (v, ties, skew):
+        cid = ctx.cube_upload(w, dtype, brick=64)
+        assert ctx.cube_median(cid) == oracle.median(stored(w, dtype, 64))
+        assert ctx.cube_median(cid) == oracle.median(stored(w, dtype, 64))   # the call again
+        ctx.cube_free(cid)
+
+
 # ------------------------------------------------------------------ rendering
 def render_check_mip(ctx, v, cid, cams, W, H, step, sampling, dtype="f32", B=0, path="fused"):
     vrc = vrcmod()
