@@ -329,8 +329,8 @@ def run_gpu(args, w):
     stats_bytes = info["dims"][0] * info["dims"][1] * info["dims"][2] * {"f32": 4, "bf16": 2, "fp8": 1}[w["storage"]]
     stats_gbs = stats_bytes / (stats_ms / 1e3) / 1e9
 
-    # exact median of the same cube (radix selection: two passes over the cube, the third over the
-    # candidates the second kept; not part of the step)
+    # exact median of the same cube (radix selection bracketed by a sampled first digit: one pass
+    # over the cube keeps the keys of the bounded bins, the digits come from those; not part of the step)
     ctx.cube_median(cid)
     t_med = time.perf_counter()
     for _ in range(3):
