@@ -1,5 +1,5 @@
 // Fused global statistics over resident bricks (min/max, mean, std, histogram)
-// and exact median by three-pass radix selection.
+// and exact median by radix selection (bracketed by a sampled first digit on resident cubes).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <float.h>
